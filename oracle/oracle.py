@@ -1,0 +1,298 @@
+"""ctypes/numpy marshalling for the C oracle (``zeus_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  No arithmetic of the
+method lives here: every number is computed by the C file, this module
+builds it with gcc, converts arguments and allocates result arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import tempfile
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "zeus_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD_DIR, "libzeus_oracle.so")
+
+# Section V-B test functions; QUADRATIC is a test objective 0.5*sum (i+1) x_i^2.
+OBJECTIVES = {"rosenbrock": 0, "rastrigin": 1, "ackley": 2,
+              "goldstein_price": 3, "quadratic": 100}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, no FMA contraction, OpenMP)."""
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_BUILD_DIR)
+    os.close(fd)
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("objective", C.c_int32), ("dim", C.c_int32),
+        ("lower", C.c_double), ("upper", C.c_double),
+        ("n_starts", C.c_int64),
+        ("pso_iters", C.c_int32), ("bfgs_max_iters", C.c_int32),
+        ("ls_max_iters", C.c_int32), ("required_converged", C.c_int32),
+        ("grad_tol", C.c_double),
+        ("w", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
+        ("armijo_c", C.c_double), ("backtrack", C.c_double),
+        ("target_f", C.c_double),
+        ("seed", C.c_uint64),
+        ("start_from_pbest", C.c_int32), ("n_threads", C.c_int32),
+    ]
+
+
+class _Result(C.Structure):
+    _fields_ = [("f", C.c_double), ("gnorm", C.c_double), ("margin", C.c_double),
+                ("iters", C.c_int32), ("status", C.c_int32),
+                ("n_feval", C.c_int32), ("pad", C.c_int32)]
+
+
+@dataclass
+class Problem:
+    """Arguments of the parallel Zeus procedure (Alg. 7).  Defaults: the
+    2-D Rosenbrock workload (128 particles, 5 PSO iterations, w=0.7,
+    c1=c2=1.5, Armijo c=1e-4, backtracking 0.5, 20 trials, 100 BFGS
+    iterations, ||g|| < 1e-8)."""
+    objective: str | int = "rosenbrock"
+    dim: int = 2
+    lower: float = -5.0
+    upper: float = 5.0
+    n_starts: int = 128
+    pso_iters: int = 5
+    bfgs_max_iters: int = 100
+    ls_max_iters: int = 20
+    required_converged: int = 0
+    grad_tol: float = 1e-8
+    w: float = 0.7
+    c1: float = 1.5
+    c2: float = 1.5
+    armijo_c: float = 1e-4
+    backtrack: float = 0.5
+    target_f: float = float("nan")
+    seed: int = 0
+    start_from_pbest: int = 0
+    n_threads: int = 0
+
+    def obj_id(self) -> int:
+        o = self.objective
+        return OBJECTIVES[o] if isinstance(o, str) else int(o)
+
+    def c(self) -> _Problem:
+        return _Problem(self.obj_id(), self.dim, self.lower, self.upper,
+                        self.n_starts, self.pso_iters, self.bfgs_max_iters,
+                        self.ls_max_iters, self.required_converged,
+                        self.grad_tol, self.w, self.c1, self.c2,
+                        self.armijo_c, self.backtrack, self.target_f,
+                        self.seed & (2**64 - 1), self.start_from_pbest,
+                        self.n_threads)
+
+
+_lib = None
+_D = C.POINTER(C.c_double)
+_U64 = C.POINTER(C.c_uint64)
+_I64 = C.POINTER(C.c_int64)
+_I32 = C.POINTER(C.c_int)
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    L = C.CDLL(build())
+    L.zo_philox4x64_10.argtypes = [_U64, _U64, _U64]
+    L.zo_uniform.argtypes = [C.c_uint64] * 5
+    L.zo_uniform.restype = C.c_double
+    L.zo_dual_op.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
+                             C.c_double, _D, _D]
+    L.zo_f.argtypes = [C.c_int, C.c_int, _D]
+    L.zo_f.restype = C.c_double
+    L.zo_grad_forward.argtypes = [C.c_int, C.c_int, _D, _D, _D]
+    L.zo_argmin.argtypes = [_D, C.c_int64]
+    L.zo_argmin.restype = C.c_int64
+    L.zo_pso.argtypes = [C.POINTER(_Problem), _D, _D, _D, _D, _D, _D, _I64]
+    L.zo_line_search.argtypes = [C.c_int, C.c_int, _D, _D, C.c_double,
+                                 C.c_double, C.c_double, C.c_double, C.c_int,
+                                 _D, _I32, _I32, _D]
+    L.zo_line_search.restype = C.c_double
+    L.zo_bfgs_update.argtypes = [C.c_int, _D, _D, _D]
+    L.zo_bfgs_update.restype = C.c_int
+    L.zo_bfgs.argtypes = [C.POINTER(_Problem), _D, _D, C.POINTER(_Result),
+                          C.c_void_p, C.c_void_p]
+    L.zo_bfgs_many.argtypes = [C.POINTER(_Problem), C.c_int64, _D, _D,
+                               C.POINTER(_Result)]
+    L.zo_solve.argtypes = [C.POINTER(_Problem), _D, _D, _D, _D, _D, _D,
+                           C.POINTER(_Result)]
+    L.zo_solve.restype = C.c_int64
+    L.zo_bfgs_quadratic_exact.argtypes = [C.c_int, _D, _D, C.c_int,
+                                          C.c_double, _D, _D]
+    L.zo_bfgs_quadratic_exact.restype = C.c_int
+    L.zo_max_threads.restype = C.c_int
+    assert L.zo_sizeof_problem() == C.sizeof(_Problem)
+    assert L.zo_sizeof_result() == C.sizeof(_Result)
+    _lib = L
+    return L
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def max_threads() -> int:
+    return int(lib().zo_max_threads())
+
+
+def philox4x64_10(ctr, key) -> np.ndarray:
+    """Philox4x64-10 block function (Salmon et al., SC'11)."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint64))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint64))
+    out = np.zeros(4, dtype=np.uint64)
+    lib().zo_philox4x64_10(c.ctypes.data_as(_U64), k.ctypes.data_as(_U64),
+                           out.ctypes.data_as(_U64))
+    return out
+
+
+def uniform(seed: int, problem: int, phase: int, particle: int, j: int) -> float:
+    """The uniform draw of (phase, particle, dimension j) (Section IV-A reading)."""
+    return float(lib().zo_uniform(seed & (2**64 - 1), problem, phase, particle, j))
+
+
+def dual_op(op: str, a1, b1, a2=0.0, b2=0.0):
+    """One dual-number operation (Section III-C): returns (value, tangent)."""
+    code = ["add", "sub", "mul", "div", "sin", "cos", "exp", "sqrt"].index(op)
+    ra, rb = C.c_double(), C.c_double()
+    lib().zo_dual_op(code, a1, b1, a2, b2, C.byref(ra), C.byref(rb))
+    return ra.value, rb.value
+
+
+def _obj(o) -> int:
+    return OBJECTIVES[o] if isinstance(o, str) else int(o)
+
+
+def f(objective, x) -> float:
+    """Objective value (Section V-B)."""
+    x = _f64(x)
+    return float(lib().zo_f(_obj(objective), x.size, _dp(x)))
+
+
+def grad_forward(objective, x):
+    """Forward-mode gradient by d dual passes (Alg. 5); returns (f, g)."""
+    x = _f64(x)
+    g = np.zeros_like(x)
+    fv = C.c_double()
+    lib().zo_grad_forward(_obj(objective), x.size, _dp(x), C.byref(fv), _dp(g))
+    return fv.value, g
+
+
+def argmin(fv) -> int:
+    """Best-of-swarm reduction (Alg. 7): NaN as +inf, ties to the lowest index."""
+    fv = _f64(fv)
+    return int(lib().zo_argmin(_dp(fv), fv.size))
+
+
+def pso(p: Problem) -> dict:
+    """PSO phase (Alg. 2 then Alg. 3 pso_iters times, synchronous gbest)."""
+    n, d = p.n_starts, p.dim
+    x = np.zeros((n, d)); v = np.zeros((n, d)); px = np.zeros((n, d))
+    pf = np.zeros(n); gx = np.zeros(d); gf = C.c_double(); gi = C.c_int64()
+    pc = p.c()
+    lib().zo_pso(C.byref(pc), _dp(x), _dp(v), _dp(px), _dp(pf), _dp(gx),
+                 C.byref(gf), C.byref(gi))
+    return dict(x=x, v=v, px=px, pf=pf, gx=gx, gf=gf.value, gidx=gi.value)
+
+
+def line_search(objective, x, p, f0, ddir, c=1e-4, beta=0.5, L=20):
+    """Backtracking Armijo line search (Alg. 6): returns (alpha, accepted, n_feval)."""
+    x = _f64(x); p = _f64(p)
+    xt = np.zeros_like(x)
+    acc = C.c_int(); nf = C.c_int(0); mg = C.c_double(math.inf)
+    a = lib().zo_line_search(_obj(objective), x.size, _dp(x), _dp(p), f0, ddir,
+                             c, beta, L, _dp(xt), C.byref(acc), C.byref(nf),
+                             C.byref(mg))
+    return float(a), bool(acc.value), int(nf.value)
+
+
+def bfgs_update(H, s, y):
+    """Inverse-Hessian rank-two update of Alg. 4; returns (H_new, applied)."""
+    H = _f64(H).copy(); s = _f64(s); y = _f64(y)
+    ok = lib().zo_bfgs_update(s.size, _dp(H), _dp(s), _dp(y))
+    return H, bool(ok)
+
+
+def _results(res, n):
+    return dict(
+        f=np.array([res[i].f for i in range(n)]),
+        gnorm=np.array([res[i].gnorm for i in range(n)]),
+        margin=np.array([res[i].margin for i in range(n)]),
+        iters=np.array([res[i].iters for i in range(n)], dtype=np.int32),
+        status=np.array([res[i].status for i in range(n)], dtype=np.int32),
+        n_feval=np.array([res[i].n_feval for i in range(n)], dtype=np.int32))
+
+
+def bfgs(p: Problem, x0):
+    """One BFGS run from x0 (Alg. 4); returns dict with x and the result."""
+    x0 = _f64(x0)
+    xo = np.zeros_like(x0)
+    r = _Result()
+    pc = p.c()
+    lib().zo_bfgs(C.byref(pc), _dp(x0), _dp(xo), C.byref(r), None, None)
+    out = _results([r], 1)
+    out = {k: v[0] for k, v in out.items()}
+    out["x"] = xo
+    return out
+
+
+def bfgs_many(p: Problem, x0):
+    """BFGS from each row of x0 ([n, d]); OpenMP over starts."""
+    x0 = _f64(x0)
+    n = x0.shape[0]
+    xo = np.zeros_like(x0)
+    res = (_Result * max(n, 1))()
+    pc = p.c()
+    lib().zo_bfgs_many(C.byref(pc), n, _dp(x0), _dp(xo), res)
+    out = _results(res, n)
+    out["x"] = xo
+    return out
+
+
+def solve(p: Problem) -> dict:
+    """Whole method (Alg. 7): PSO, BFGS from every particle, argmin."""
+    n, d = p.n_starts, p.dim
+    x = np.zeros((n, d)); v = np.zeros((n, d)); px = np.zeros((n, d))
+    pf = np.zeros(n); gx = np.zeros(d); xo = np.zeros((n, d))
+    res = (_Result * max(n, 1))()
+    pc = p.c()
+    b = lib().zo_solve(C.byref(pc), _dp(x), _dp(v), _dp(px), _dp(pf), _dp(gx),
+                       _dp(xo), res)
+    out = _results(res, n)
+    out.update(x=xo, swarm=x, v=v, px=px, pf=pf, gx=gx, best=int(b))
+    return out
+
+
+def bfgs_quadratic_exact(A, x0, max_iters=100, tol=1e-10):
+    """Test-only BFGS with exact steps on 0.5 x^T A x; returns (iters, x, H)."""
+    A = _f64(A); x0 = _f64(x0)
+    d = x0.size
+    xo = np.zeros(d); H = np.zeros((d, d))
+    k = lib().zo_bfgs_quadratic_exact(d, _dp(A), _dp(x0), max_iters, tol,
+                                      _dp(xo), _dp(H))
+    return int(k), xo, H

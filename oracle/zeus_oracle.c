@@ -1,0 +1,655 @@
+/*
+ * zeus_oracle.c -- plain, slow, obviously-correct FP64 CPU reference of the
+ * Zeus method (PSO seeding, then one BFGS run per start with forward-mode
+ * dual-number gradients, backtracking Armijo line search and the dense
+ * inverse-Hessian rank-two update, then a best-of-swarm argmin).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA path is
+ * checked against.  Only tests/, __graft_entry__.smoke() and bench.py's CPU
+ * baseline leg may load it.  It shares no code, header, table or constant
+ * generator with the CUDA library; it has its own Philox, its own dual
+ * numbers and its own objectives.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -fPIC -shared -lm
+ * (no FMA contraction, so every product and sum below is rounded exactly
+ * once in the order written).
+ *
+ * Each function names the part of the paper it follows (Zeus, arXiv
+ * 2603.28770).  Readings of points the paper leaves open are marked
+ * "Reading:".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Problem description (the oracle's own copy; not shared with the library) */
+/* ------------------------------------------------------------------------ */
+
+enum {
+    ZO_ROSENBROCK = 0,      /* Section V-B, Rosenbrock */
+    ZO_RASTRIGIN = 1,       /* Section V-B, Rastrigin (A = 10) */
+    ZO_ACKLEY = 2,          /* Section V-B, Ackley (a=20, b=0.2, c=2*pi) */
+    ZO_GOLDSTEIN_PRICE = 3, /* Section V-B, Goldstein-Price (d = 2) */
+    ZO_QUADRATIC = 100      /* test objective: 0.5 * sum (i+1) x_i^2 */
+};
+
+typedef struct {
+    int32_t objective;
+    int32_t dim;
+    double lower, upper;
+    int64_t n_starts;
+    int32_t pso_iters;
+    int32_t bfgs_max_iters;
+    int32_t ls_max_iters;
+    int32_t required_converged; /* 0 = off */
+    double grad_tol;
+    double w, c1, c2;
+    double armijo_c, backtrack;
+    double target_f;            /* NaN = off */
+    uint64_t seed;
+    int32_t start_from_pbest;   /* 0 = current swarm positions (Alg. 10) */
+    int32_t n_threads;          /* OpenMP threads for the per-start loops */
+} zo_problem;
+
+/* per-start result of one BFGS run (Alg. 4) */
+typedef struct {
+    double f;          /* f at the final x */
+    double gnorm;      /* ||g|| at the final x */
+    double margin;     /* smallest relative margin of any branch decision */
+    int32_t iters;     /* completed iterations k */
+    int32_t status;    /* 0 max-iter, 1 converged, 2 stopped, 3 non-finite */
+    int32_t n_feval;   /* line-search objective evaluations */
+    int32_t pad;
+} zo_result;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As  */
+/* Easy as 1, 2, 3", SC'11), written from its published definition.         */
+/* Replaces the paper's cuRAND seeding of Section IV-A.                      */
+/* ------------------------------------------------------------------------ */
+
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void zo_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2],
+                      uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint64_t k[2] = {key_in[0], key_in[1]};
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k[0] += W0; k[1] += W1; }
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(M0, c[0], &hi0, &lo0);
+        mulhilo64(M1, c[2], &hi1, &lo1);
+        uint64_t n0 = hi1 ^ c[1] ^ k[0];
+        uint64_t n2 = hi0 ^ c[3] ^ k[1];
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* Reading of Section IV-A: one uniform double per (phase, particle, dim).
+ * Counter = (j / 4, particle i, problem, phase), key = (seed, 0); the
+ * draw is word j % 4 of the block, mapped to [0,1) with 53 bits.
+ * Phases: 0 = initial position, 1 = initial velocity, 2+2t = r1 and
+ * 3+2t = r2 of PSO iteration t. */
+double zo_uniform(uint64_t seed, uint64_t problem, uint64_t phase,
+                  uint64_t particle, uint64_t j)
+{
+    uint64_t ctr[4] = {j / 4, particle, problem, phase};
+    uint64_t key[2] = {seed, 0};
+    uint64_t out[4];
+    zo_philox4x64_10(ctr, key, out);
+    return (double)(out[j % 4] >> 11) * 0x1.0p-53;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dual numbers a + b*eps with eps^2 = 0 (Section III-C).                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { double a, b; } zo_dual;
+
+static zo_dual dconst(double a) { zo_dual r = {a, 0.0}; return r; }
+static zo_dual dadd(zo_dual x, zo_dual y) { zo_dual r = {x.a + y.a, x.b + y.b}; return r; }
+static zo_dual dsub(zo_dual x, zo_dual y) { zo_dual r = {x.a - y.a, x.b - y.b}; return r; }
+/* (a1 + b1 e)(a2 + b2 e) = a1 a2 + (a1 b2 + b1 a2) e */
+static zo_dual dmul(zo_dual x, zo_dual y)
+{
+    zo_dual r = {x.a * y.a, x.a * y.b + x.b * y.a};
+    return r;
+}
+/* (a1 + b1 e)/(a2 + b2 e) = a1/a2 + (b1 a2 - a1 b2)/a2^2 e */
+static zo_dual ddiv(zo_dual x, zo_dual y)
+{
+    zo_dual r = {x.a / y.a, (x.b * y.a - x.a * y.b) / (y.a * y.a)};
+    return r;
+}
+static zo_dual dscale(double s, zo_dual x) { zo_dual r = {s * x.a, s * x.b}; return r; }
+/* g(a + b e) = g(a) + g'(a) b e */
+static zo_dual dsin(zo_dual x) { zo_dual r = {sin(x.a), cos(x.a) * x.b}; return r; }
+static zo_dual dcos(zo_dual x) { zo_dual r = {cos(x.a), -sin(x.a) * x.b}; return r; }
+static zo_dual dexp(zo_dual x) { double e = exp(x.a); zo_dual r = {e, e * x.b}; return r; }
+/* Reading: d/du sqrt(u) at u = 0 is taken as 0 (Ackley's kink at the
+ * origin, Section V-B, where the derivative is undefined). */
+static zo_dual dsqrt(zo_dual x)
+{
+    double s = sqrt(x.a);
+    zo_dual r = {s, s > 0.0 ? x.b / (2.0 * s) : 0.0};
+    return r;
+}
+
+/* exported for the dual-algebra pins */
+void zo_dual_op(int op, double a1, double b1, double a2, double b2,
+                double *ra, double *rb)
+{
+    zo_dual x = {a1, b1}, y = {a2, b2}, r;
+    switch (op) {
+    case 0: r = dadd(x, y); break;
+    case 1: r = dsub(x, y); break;
+    case 2: r = dmul(x, y); break;
+    case 3: r = ddiv(x, y); break;
+    case 4: r = dsin(x); break;
+    case 5: r = dcos(x); break;
+    case 6: r = dexp(x); break;
+    case 7: r = dsqrt(x); break;
+    default: r = dconst(NAN); break;
+    }
+    *ra = r.a;
+    *rb = r.b;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Objectives (Section V-B), on doubles and on duals.                        */
+/* ------------------------------------------------------------------------ */
+
+static const double ZO_PI = 3.14159265358979323846;
+static const double ZO_E = 2.71828182845904523536;
+
+double zo_f(int obj, int d, const double *x)
+{
+    double s = 0.0;
+    switch (obj) {
+    case ZO_ROSENBROCK:
+        /* Reading: the chain sum runs over i = 1..d-1 (the printed upper
+         * limit n would need x_{n+1}). */
+        for (int i = 0; i + 1 < d; ++i) {
+            double a = 1.0 - x[i];
+            double b = x[i + 1] - x[i] * x[i];
+            s = s + (a * a + 100.0 * (b * b));
+        }
+        return s;
+    case ZO_RASTRIGIN:
+        s = 10.0 * (double)d;
+        for (int i = 0; i < d; ++i)
+            s = s + (x[i] * x[i] - 10.0 * cos(2.0 * ZO_PI * x[i]));
+        return s;
+    case ZO_ACKLEY: {
+        double s1 = 0.0, s2 = 0.0;
+        for (int i = 0; i < d; ++i) {
+            s1 = s1 + x[i] * x[i];
+            s2 = s2 + cos(2.0 * ZO_PI * x[i]);
+        }
+        double t1 = -20.0 * exp(-0.2 * sqrt(s1 / (double)d));
+        double t2 = exp(s2 / (double)d);
+        return (t1 - t2) + (20.0 + ZO_E);
+    }
+    case ZO_GOLDSTEIN_PRICE: {
+        double x1 = x[0], x2 = x[1];
+        double t = (x1 + x2) + 1.0;
+        double pa = 19.0 - 14.0 * x1 + 3.0 * (x1 * x1) - 14.0 * x2
+                    + 6.0 * (x1 * x2) + 3.0 * (x2 * x2);
+        double a = 1.0 + (t * t) * pa;
+        double u = 2.0 * x1 - 3.0 * x2;
+        double pb = 18.0 - 32.0 * x1 + 12.0 * (x1 * x1) + 48.0 * x2
+                    - 36.0 * (x1 * x2) + 27.0 * (x2 * x2);
+        double b = 30.0 + (u * u) * pb;
+        return a * b;
+    }
+    case ZO_QUADRATIC:
+        for (int i = 0; i < d; ++i)
+            s = s + 0.5 * (double)(i + 1) * (x[i] * x[i]);
+        return s;
+    default:
+        return NAN;
+    }
+}
+
+/* The same objectives written over dual numbers (Alg. 5 evaluates f on
+ * xDual).  Operation order mirrors zo_f, so the value part equals zo_f. */
+static zo_dual zo_f_dual(int obj, int d, const zo_dual *x)
+{
+    zo_dual s = dconst(0.0);
+    switch (obj) {
+    case ZO_ROSENBROCK:
+        for (int i = 0; i + 1 < d; ++i) {
+            zo_dual a = dsub(dconst(1.0), x[i]);
+            zo_dual b = dsub(x[i + 1], dmul(x[i], x[i]));
+            s = dadd(s, dadd(dmul(a, a), dscale(100.0, dmul(b, b))));
+        }
+        return s;
+    case ZO_RASTRIGIN:
+        s = dconst(10.0 * (double)d);
+        for (int i = 0; i < d; ++i)
+            s = dadd(s, dsub(dmul(x[i], x[i]),
+                             dscale(10.0, dcos(dscale(2.0 * ZO_PI, x[i])))));
+        return s;
+    case ZO_ACKLEY: {
+        zo_dual s1 = dconst(0.0), s2 = dconst(0.0);
+        for (int i = 0; i < d; ++i) {
+            s1 = dadd(s1, dmul(x[i], x[i]));
+            s2 = dadd(s2, dcos(dscale(2.0 * ZO_PI, x[i])));
+        }
+        zo_dual t1 = dscale(-20.0, dexp(dscale(-0.2, dsqrt(ddiv(s1, dconst((double)d))))));
+        zo_dual t2 = dexp(ddiv(s2, dconst((double)d)));
+        return dadd(dsub(t1, t2), dconst(20.0 + ZO_E));
+    }
+    case ZO_GOLDSTEIN_PRICE: {
+        /* same left-to-right order as zo_f */
+        zo_dual x1 = x[0], x2 = x[1];
+        zo_dual t = dadd(dadd(x1, x2), dconst(1.0));
+        zo_dual pa = dconst(19.0);
+        pa = dsub(pa, dscale(14.0, x1));
+        pa = dadd(pa, dscale(3.0, dmul(x1, x1)));
+        pa = dsub(pa, dscale(14.0, x2));
+        pa = dadd(pa, dscale(6.0, dmul(x1, x2)));
+        pa = dadd(pa, dscale(3.0, dmul(x2, x2)));
+        zo_dual a = dadd(dconst(1.0), dmul(dmul(t, t), pa));
+        zo_dual u = dsub(dscale(2.0, x1), dscale(3.0, x2));
+        zo_dual pb = dconst(18.0);
+        pb = dsub(pb, dscale(32.0, x1));
+        pb = dadd(pb, dscale(12.0, dmul(x1, x1)));
+        pb = dadd(pb, dscale(48.0, x2));
+        pb = dsub(pb, dscale(36.0, dmul(x1, x2)));
+        pb = dadd(pb, dscale(27.0, dmul(x2, x2)));
+        zo_dual b = dadd(dconst(30.0), dmul(dmul(u, u), pb));
+        return dmul(a, b);
+    }
+    case ZO_QUADRATIC:
+        for (int i = 0; i < d; ++i)
+            s = dadd(s, dscale(0.5 * (double)(i + 1), dmul(x[i], x[i])));
+        return s;
+    default:
+        return dconst(NAN);
+    }
+}
+
+/* Alg. 5 (forwardAD): d passes; pass i seeds the tangent of x_i with 1,
+ * evaluates f on duals and reads the tangent as df/dx_i.  The value part
+ * of the first pass is returned as f(x) (reading: the line search's f0 is
+ * this value). */
+void zo_grad_forward(int obj, int d, const double *x, double *f, double *g)
+{
+    zo_dual *xd = (zo_dual *)malloc(sizeof(zo_dual) * (size_t)(d > 0 ? d : 1));
+    for (int i = 0; i < d; ++i) { xd[i].a = x[i]; xd[i].b = 0.0; }
+    double fval = NAN;
+    for (int i = 0; i < d; ++i) {
+        xd[i].b = 1.0;
+        zo_dual r = zo_f_dual(obj, d, xd);
+        g[i] = r.b;
+        if (i == 0) fval = r.a;
+        xd[i].b = 0.0;
+    }
+    if (d == 0) fval = zo_f(obj, d, x);
+    *f = fval;
+    free(xd);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Argmin (Alg. 7 ParallelReduction).  Reading: NaN counts as +inf, ties go  */
+/* to the lowest index.                                                      */
+/* ------------------------------------------------------------------------ */
+
+int64_t zo_argmin(const double *f, int64_t n)
+{
+    int64_t best = -1;
+    double bf = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        double v = isnan(f[i]) ? INFINITY : f[i];
+        if (best < 0 || v < bf) { best = i; bf = v; }
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* PSO (Alg. 2 InitSwarm, Alg. 3 UpdateSwarm).                               */
+/* Reading: the global best is refreshed once per iteration from the         */
+/* personal bests (synchronous), r1 and r2 are drawn per dimension, no       */
+/* clamping is applied, and exactly pso_iters updates are made.              */
+/* ------------------------------------------------------------------------ */
+
+static double fmin_nan(double v) { return isnan(v) ? INFINITY : v; }
+
+void zo_pso(const zo_problem *pr, double *x, double *v, double *px,
+            double *pf, double *gx, double *gf, int64_t *gidx)
+{
+    const int d = pr->dim;
+    const int64_t n = pr->n_starts;
+    const double lo = pr->lower, hi = pr->upper;
+    const double vr = hi - lo;          /* Alg. 2: vel_range = upper - lower */
+    const double vlo = -vr, vhi = vr;
+#ifdef _OPENMP
+    if (pr->n_threads > 0) omp_set_num_threads(pr->n_threads);
+#endif
+    /* Alg. 2 */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int j = 0; j < d; ++j) {
+            double ux = zo_uniform(pr->seed, 0, 0, (uint64_t)i, (uint64_t)j);
+            double uv = zo_uniform(pr->seed, 0, 1, (uint64_t)i, (uint64_t)j);
+            x[i * d + j] = lo + (hi - lo) * ux;
+            v[i * d + j] = vlo + (vhi - vlo) * uv;
+            px[i * d + j] = x[i * d + j];
+        }
+        pf[i] = zo_f(pr->objective, d, x + i * d);
+    }
+    int64_t b = zo_argmin(pf, n);
+    *gidx = b;
+    *gf = fmin_nan(pf[b]);
+    for (int j = 0; j < d; ++j) gx[j] = px[b * d + j];
+
+    /* Alg. 3, pso_iters times */
+    for (int t = 0; t < pr->pso_iters; ++t) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            double *xi = x + i * d, *vi = v + i * d, *pi = px + i * d;
+            for (int j = 0; j < d; ++j) {
+                double r1 = zo_uniform(pr->seed, 0, 2 + 2 * (uint64_t)t, (uint64_t)i, (uint64_t)j);
+                double r2 = zo_uniform(pr->seed, 0, 3 + 2 * (uint64_t)t, (uint64_t)i, (uint64_t)j);
+                double vn = pr->w * vi[j] + (pr->c1 * r1) * (pi[j] - xi[j])
+                            + (pr->c2 * r2) * (gx[j] - xi[j]);
+                vi[j] = vn;
+                xi[j] = xi[j] + vn;
+            }
+            double fv = zo_f(pr->objective, d, xi);
+            if (fv < pf[i]) {
+                pf[i] = fv;
+                for (int j = 0; j < d; ++j) pi[j] = xi[j];
+            }
+        }
+        b = zo_argmin(pf, n);
+        *gidx = b;
+        *gf = fmin_nan(pf[b]);
+        for (int j = 0; j < d; ++j) gx[j] = px[b * d + j];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Backtracking Armijo line search (Alg. 6).                                 */
+/* Returns alpha; *accepted = 1 if the Armijo test held for some trial.      */
+/* Reading: trials m = 0..L-1; if none is accepted the returned alpha is     */
+/* the value after the last halving (beta^L), as in the printed loop.        */
+/* ------------------------------------------------------------------------ */
+
+static double track_margin(double margin, double lhs, double rhs, double scale)
+{
+    double m = fabs(lhs - rhs) / (fabs(scale) > 1.0 ? fabs(scale) : 1.0);
+    return m < margin ? m : margin;
+}
+
+double zo_line_search(int obj, int d, const double *x, const double *p,
+                      double f0, double ddir, double c, double beta, int L,
+                      double *xt, int *accepted, int *n_feval, double *margin)
+{
+    double alpha = 1.0;
+    *accepted = 0;
+    for (int m = 0; m < L; ++m) {
+        for (int j = 0; j < d; ++j) xt[j] = x[j] + alpha * p[j];
+        double ft = zo_f(obj, d, xt);
+        (*n_feval)++;
+        double rhs = f0 + c * alpha * ddir;
+        if (margin) *margin = track_margin(*margin, ft, rhs, f0);
+        if (ft <= rhs) { *accepted = 1; break; }
+        alpha = beta * alpha;
+    }
+    return alpha;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Inverse-Hessian rank-two update (the update formula of Alg. 4).           */
+/* The printed product form (I - rho s y^T) H (I - rho y s^T) + rho s s^T    */
+/* expands, for symmetric H, to                                              */
+/*   H - rho (Hy s^T + s (Hy)^T) + (rho^2 y^T H y + rho) s s^T.              */
+/* Returns 1 if applied.  Reading: skipped when y^T s <= 1e-12 |s| |y|.      */
+/* ------------------------------------------------------------------------ */
+
+int zo_bfgs_update(int d, double *H, const double *s, const double *y)
+{
+    double sy = 0.0, ss = 0.0, yy = 0.0;
+    for (int i = 0; i < d; ++i) {
+        sy = sy + y[i] * s[i];
+        ss = ss + s[i] * s[i];
+        yy = yy + y[i] * y[i];
+    }
+    if (!(sy > 1e-12 * sqrt(ss) * sqrt(yy))) return 0;
+    double rho = 1.0 / sy;
+    double *Hy = (double *)malloc(sizeof(double) * (size_t)d);
+    double yHy = 0.0;
+    for (int r = 0; r < d; ++r) {
+        double a = 0.0;
+        for (int c = 0; c < d; ++c) a = a + H[r * d + c] * y[c];
+        Hy[r] = a;
+    }
+    for (int r = 0; r < d; ++r) yHy = yHy + y[r] * Hy[r];
+    double beta = rho * rho * yHy + rho;
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c)
+            H[r * d + c] = H[r * d + c] - rho * (Hy[r] * s[c] + s[r] * Hy[c])
+                           + beta * (s[r] * s[c]);
+    free(Hy);
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One BFGS run (Alg. 4, with the per-thread body of Alg. 10).               */
+/* Readings: the gradient at x_new is reused as the next iteration's         */
+/* gradient; a non-descent direction resets H to I and uses p = -g; the      */
+/* convergence test ||g|| < tol is made at the top of each iteration only;   */
+/* status 3 marks a non-finite f or g.  stop (may be NULL) is the shared     */
+/* stop flag of Alg. 10.                                                     */
+/* ------------------------------------------------------------------------ */
+
+static int finite_vec(int d, const double *v)
+{
+    for (int i = 0; i < d; ++i)
+        if (!isfinite(v[i])) return 0;
+    return 1;
+}
+
+void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
+             zo_result *res, volatile int *stop, volatile int64_t *n_conv)
+{
+    const int d = pr->dim, obj = pr->objective;
+    size_t nb = sizeof(double) * (size_t)(d > 0 ? d : 1);
+    double *H = (double *)malloc(nb * (size_t)(d > 0 ? d : 1));
+    double *x = (double *)malloc(nb), *g = (double *)malloc(nb);
+    double *p = (double *)malloc(nb), *xn = (double *)malloc(nb);
+    double *gn = (double *)malloc(nb), *s = (double *)malloc(nb);
+    double *y = (double *)malloc(nb);
+    for (int i = 0; i < d; ++i) x[i] = x0[i];
+    for (int i = 0; i < d * d; ++i) H[i] = 0.0;
+    for (int i = 0; i < d; ++i) H[i * d + i] = 1.0;
+    double f0;
+    zo_grad_forward(obj, d, x, &f0, g);
+    double margin = INFINITY;
+    int k = 0, status = 0, n_feval = 0;
+    double gnorm = NAN;
+    for (;;) {
+        double gg = 0.0;
+        for (int i = 0; i < d; ++i) gg = gg + g[i] * g[i];
+        gnorm = sqrt(gg);
+        if (k >= pr->bfgs_max_iters) { status = 0; break; }
+        if (stop && *stop) { status = 2; break; }
+        if (!isfinite(f0) || !finite_vec(d, g)) { status = 3; break; }
+        margin = track_margin(margin, gnorm, pr->grad_tol, pr->grad_tol);
+        if (gnorm < pr->grad_tol) {
+            status = 1;
+            if (n_conv) {
+                int64_t c;
+#pragma omp atomic capture
+                c = ++(*n_conv);
+                if (stop && pr->required_converged > 0 && c >= pr->required_converged)
+                    *stop = 1;
+            }
+            break;
+        }
+        if (!isnan(pr->target_f) && f0 <= pr->target_f) {
+            status = 1;
+            if (stop) *stop = 1;
+            break;
+        }
+        /* p = -H g, ddir = g^T p */
+        double ddir = 0.0;
+        for (int r = 0; r < d; ++r) {
+            double a = 0.0;
+            for (int c = 0; c < d; ++c) a = a + H[r * d + c] * g[c];
+            p[r] = -a;
+        }
+        for (int r = 0; r < d; ++r) ddir = ddir + g[r] * p[r];
+        if (!(ddir < 0.0)) {
+            /* Reading: non-descent direction -> restart from H = I */
+            for (int i = 0; i < d * d; ++i) H[i] = 0.0;
+            for (int i = 0; i < d; ++i) H[i * d + i] = 1.0;
+            for (int r = 0; r < d; ++r) p[r] = -g[r];
+            ddir = 0.0;
+            for (int r = 0; r < d; ++r) ddir = ddir + g[r] * p[r];
+        }
+        int accepted = 0;
+        double alpha = zo_line_search(obj, d, x, p, f0, ddir, pr->armijo_c,
+                                      pr->backtrack, pr->ls_max_iters, xn,
+                                      &accepted, &n_feval, &margin);
+        for (int j = 0; j < d; ++j) xn[j] = x[j] + alpha * p[j];
+        double fn;
+        zo_grad_forward(obj, d, xn, &fn, gn);
+        for (int j = 0; j < d; ++j) {
+            s[j] = xn[j] - x[j];
+            y[j] = gn[j] - g[j];
+        }
+        zo_bfgs_update(d, H, s, y);
+        for (int j = 0; j < d; ++j) { x[j] = xn[j]; g[j] = gn[j]; }
+        f0 = fn;
+        ++k;
+    }
+    for (int j = 0; j < d; ++j) x_out[j] = x[j];
+    res->f = f0;
+    res->gnorm = gnorm;
+    res->margin = margin;
+    res->iters = k;
+    res->status = status;
+    res->n_feval = n_feval;
+    res->pad = 0;
+    free(H); free(x); free(g); free(p); free(xn); free(gn); free(s); free(y);
+}
+
+/* BFGS from n given starts (x0 row-major [n][d]); OpenMP over starts. */
+void zo_bfgs_many(const zo_problem *pr, int64_t n, const double *x0,
+                  double *x_out, zo_result *res)
+{
+    volatile int stop = 0;
+    volatile int64_t n_conv = 0;
+    const int use_stop = pr->required_converged > 0 || !isnan(pr->target_f);
+#ifdef _OPENMP
+    if (pr->n_threads > 0) omp_set_num_threads(pr->n_threads);
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; ++i)
+        zo_bfgs(pr, x0 + i * pr->dim, x_out + i * pr->dim, res + i,
+                use_stop ? &stop : NULL, use_stop ? &n_conv : NULL);
+}
+
+/* Whole method (Alg. 7): PSO, then BFGS from every particle's current
+ * position (or personal best), then argmin of the BFGS final values. */
+int64_t zo_solve(const zo_problem *pr, double *x, double *v, double *px,
+                 double *pf, double *gx, double *x_out, zo_result *res)
+{
+    double gf;
+    int64_t gi;
+    zo_pso(pr, x, v, px, pf, gx, &gf, &gi);
+    const double *starts = pr->start_from_pbest ? px : x;
+    zo_bfgs_many(pr, pr->n_starts, starts, x_out, res);
+    double *fo = (double *)malloc(sizeof(double) * (size_t)pr->n_starts);
+    for (int64_t i = 0; i < pr->n_starts; ++i) fo[i] = res[i].f;
+    int64_t b = zo_argmin(fo, pr->n_starts);
+    free(fo);
+    return b;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Test-only: BFGS on f = 0.5 x^T A x (A dense SPD, row-major) with the      */
+/* exact line search alpha = -g^T p / (p^T A p).  Used to pin the update:    */
+/* with exact steps BFGS terminates on a quadratic in at most d iterations   */
+/* and H_d = A^{-1} (Nocedal & Wright, Numerical Optimization, Thm. 6.4 /    */
+/* the quadratic-termination property of the Broyden class).  Uses the same  */
+/* zo_bfgs_update as the main path.  Returns the iterations taken; H is      */
+/* left in H_out.                                                            */
+/* ------------------------------------------------------------------------ */
+
+int zo_bfgs_quadratic_exact(int d, const double *A, const double *x0,
+                            int max_iters, double tol, double *x_out,
+                            double *H_out)
+{
+    size_t nb = sizeof(double) * (size_t)d;
+    double *x = (double *)malloc(nb), *g = (double *)malloc(nb);
+    double *p = (double *)malloc(nb), *Ap = (double *)malloc(nb);
+    double *s = (double *)malloc(nb), *y = (double *)malloc(nb);
+    double *H = H_out;
+    for (int i = 0; i < d; ++i) x[i] = x0[i];
+    for (int i = 0; i < d * d; ++i) H[i] = 0.0;
+    for (int i = 0; i < d; ++i) H[i * d + i] = 1.0;
+    int k = 0;
+    for (;;) {
+        double gg = 0.0;
+        for (int r = 0; r < d; ++r) {
+            double a = 0.0;
+            for (int c = 0; c < d; ++c) a = a + A[r * d + c] * x[c];
+            g[r] = a;
+            gg = gg + a * a;
+        }
+        if (sqrt(gg) < tol || k >= max_iters) break;
+        double gp = 0.0, pAp = 0.0;
+        for (int r = 0; r < d; ++r) {
+            double a = 0.0;
+            for (int c = 0; c < d; ++c) a = a + H[r * d + c] * g[c];
+            p[r] = -a;
+        }
+        for (int r = 0; r < d; ++r) {
+            double a = 0.0;
+            for (int c = 0; c < d; ++c) a = a + A[r * d + c] * p[c];
+            Ap[r] = a;
+            gp = gp + g[r] * p[r];
+        }
+        for (int r = 0; r < d; ++r) pAp = pAp + p[r] * Ap[r];
+        double alpha = -gp / pAp;
+        for (int r = 0; r < d; ++r) {
+            s[r] = alpha * p[r];
+            x[r] = x[r] + s[r];
+            y[r] = alpha * Ap[r];     /* y = A s */
+        }
+        zo_bfgs_update(d, H, s, y);
+        ++k;
+    }
+    for (int i = 0; i < d; ++i) x_out[i] = x[i];
+    free(x); free(g); free(p); free(Ap); free(s); free(y);
+    return k;
+}
+
+int zo_sizeof_problem(void) { return (int)sizeof(zo_problem); }
+int zo_sizeof_result(void) { return (int)sizeof(zo_result); }
+int zo_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
