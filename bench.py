@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Benchmark of the Zeus hot path on one GB300 (or N, one process per GPU).
+
+One step = the whole method on one problem: PSO initialisation and updates,
+one BFGS run per particle, best-of-swarm reduction -- the 10-D Rastrigin
+workload (16384 particles in [-5.12,5.12]^10, 20 PSO updates, BFGS cap
+1000, ||g|| < 1e-8), FP64, forward-mode dual gradients.  The metric is
+start-iterations per second (sum over starts of completed BFGS iterations
+divided by device time).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl zeus|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference: the paper
+ships no code) on the host cores for the same workload, a bounded sample of
+starts per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2603_28770_gb300 import workloads  # noqa: E402
+
+WORKLOAD = "rastrigin10d_n16384"
+METRIC = "start-iters/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="zeus", choices=["zeus", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--grad-mode", default="forward", choices=["forward", "adjoint"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------- roofline model
+
+def fp64_flops_per_start_iter(d: int, feval_per_iter: float) -> float:
+    """Algorithmic FP64 operations of one start-iteration of the 10-D
+    Rastrigin run in forward mode (FMA = 2, transcendental calls counted by
+    the FP64 operations of the sin/cos(pi x) evaluations they stand for,
+    TRIG_OPS each).  Terms:
+      gradient  d passes x (d value terms + 1 tangent term)
+      line search  feval_per_iter evaluations x d terms
+      direction  p = -H g (2 d^2) and g'p (2 d)
+      update  s, y, y's, |s|, |y| (8 d), Hy and y'Hy (2 d^2 + 2 d),
+              rank-two update (6 d^2)."""
+    value_term = 5 + TRIG_OPS          # x*x, 10*c, -, +, 2x ; cos(pi 2x)
+    tangent_term = 5 + TRIG_OPS        # x+x, 2 pi s, 10*, -, + ; sin(pi 2x)
+    grad = d * (d * value_term + tangent_term)
+    ls = feval_per_iter * d * (2 + value_term)
+    direction = 2 * d * d + 2 * d
+    update = 8 * d + 2 * d * d + 2 * d + 6 * d * d
+    return grad + ls + direction + update
+
+
+TRIG_OPS = 24  # FP64 operations per sin(pi x) or cos(pi x) value (see design notes)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except OSError:
+        return {}
+
+
+# -------------------------------------------------------------- zeus arm
+
+def run_zeus(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2603_28770_gb300 as z
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    fields = workloads.workload(a.workload, grad_mode=a.grad_mode)
+    # weak scaling: every rank solves its own independent multistart problem
+    fields["seed"] = fields["seed"] + rank
+    p = z.Problem(**{k: v for k, v in fields.items() if k in z.Problem.__dataclass_fields__})
+    pc = p.to_c()
+    n, d = p.n_starts, p.dim
+
+    ws = z.new_workspace(pc, dev)
+    x = torch.empty(n, d, dtype=torch.float64, device=dev)
+    f = torch.empty(n, dtype=torch.float64, device=dev)
+    gn = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    it = torch.empty(n, dtype=torch.int32, device=dev)
+    v = torch.empty(n, d, dtype=torch.float64, device=dev)
+    px = torch.empty(n, d, dtype=torch.float64, device=dev)
+    pf = torch.empty(n, dtype=torch.float64, device=dev)
+    gx = torch.empty(d, dtype=torch.float64, device=dev)
+    res = z.new_result(dev)
+    ws_pso = z.new_workspace(pc, dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        # the whole path: PSO phase, BFGS from the final positions, argmin
+        if ev:
+            ev[0].record(stream)
+        z.zeus_pso(pc, ws_pso, x, v, px, pf, gx, None, stream)
+        if ev:
+            ev[1].record(stream)
+        z.zeus_solve_from(pc, x, ws, x, f, gn, st, it, res, stream)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    summary = z.decode_result(res)
+    iters_per_step = int(summary["total_iters"])
+    feval_per_step = int(summary["total_feval"])
+
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for k in range(a.steps):
+            flush.fill_(k & 0xFF)  # evict L2 between timed steps (outside the events)
+            step(events[k])
+        torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    step_ms = [e[0].elapsed_time(e[2]) for e in events]
+    bfgs_ms = [e[1].elapsed_time(e[2]) for e in events]
+    total_ms = sum(step_ms)
+    summary = z.decode_result(res)
+    assert int(summary["total_iters"]) == iters_per_step, "non-deterministic iteration count"
+
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        it_t = torch.tensor([iters_per_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(it_t, op=dist.ReduceOp.SUM)
+        iters_all = float(it_t.item())
+    else:
+        iters_all = float(iters_per_step)
+
+    value = iters_all * a.steps / (total_ms / 1e3)
+
+    # end to end through the host-buffer C entry point
+    ctx = z.Context()
+    hx = torch.empty(n, d, dtype=torch.float64).pin_memory()
+    hf = torch.empty(n, dtype=torch.float64).pin_memory()
+    hg = torch.empty(n, dtype=torch.float64).pin_memory()
+    hs = torch.empty(n, dtype=torch.int32).pin_memory()
+    hi = torch.empty(n, dtype=torch.int32).pin_memory()
+    ctx.zeus_solve_host(pc, hx, hf, hg, hs, hi, stream)  # warm-up (allocates)
+    e2e_ms = []
+    for k in range(max(1, a.steps)):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = ctx.zeus_solve_host(pc, hx, hf, hg, hs, hi, stream)  # synchronizes the stream
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    ctx.close()
+    assert int(r["total_iters"]) == iters_per_step
+    e2e_value = iters_per_step * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+    d2h = n * d * 8 + n * 8 * 2 + n * 4 * 2 + 64
+
+    # roofline of the dominant kernel (the BFGS kernel, FP64-pipe bound)
+    peaks = _peaks()
+    flops = fp64_flops_per_start_iter(d, feval_per_step / max(iters_per_step, 1)) * iters_per_step
+    bfgs_s = statistics.mean(bfgs_ms) / 1e3
+    achieved = flops / bfgs_s / 1e12
+    peak = FP64_PEAK_TFLOPS
+    roof = {"kernel": "bfgs_kernel", "bound": "alu", "achieved": round(achieved, 4), "peak": peak,
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "peak_source": "nominal FP64 rate of the part (recipe figure), not measured",
+            "flops_per_launch": flops, "launch_ms": round(bfgs_s * 1e3, 3)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "start-iters/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Philox draws of the method itself; no dataset)",
+        "config": {"workload": a.workload, "objective": p.objective, "dim": d, "n_starts": n,
+                   "pso_iters": p.pso_iters, "bfgs_max_iters": p.bfgs_max_iters,
+                   "grad_mode": a.grad_mode, "precision": "fp64",
+                   "start_iters_per_step": iters_per_step, "feval_per_step": feval_per_step,
+                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(e2e_value, 1), "unit": "start-iters/s",
+                "h2d_bytes_per_step": 128, "d2h_bytes_per_step": d2h,
+                "api": "zeus_solve_host (problem struct in, host outputs back, stream synchronized)"},
+        "gpu_launches": a.steps * (p.pso_iters + 3),
+        "roofline": roof,
+        "best_f": summary["best_f"], "n_converged": summary["n_converged"],
+        "wall_s_timed": round(t_wall, 3),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(fields, budget_s=12.0)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of one GB300 (recipe figure)
+
+
+# ------------------------------------------------------------ oracle arm
+
+def _oracle_sample(fields, n_sample, threads):
+    import oracle
+    op = oracle.Problem(**{k: v for k, v in fields.items() if k in oracle.Problem.__dataclass_fields__})
+    op.n_threads = threads
+    t0 = time.perf_counter()
+    sw = oracle.pso(op)
+    x0 = sw["x"][:n_sample]
+    r = oracle.bfgs_many(op, x0)
+    dt = time.perf_counter() - t0
+    return int(r["iters"].sum()), dt
+
+
+def cpu_baseline(fields, budget_s=12.0) -> dict:
+    """The FP64 oracle as it stands on the host cores: the full PSO phase
+    plus BFGS from the first M particles, M grown until ~budget_s."""
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n_sample = 64
+    iters, dt = _oracle_sample(fields, n_sample, threads)
+    while dt < budget_s / 4 and n_sample < fields["n_starts"]:
+        n_sample = min(fields["n_starts"], n_sample * 4)
+        iters, dt = _oracle_sample(fields, n_sample, threads)
+    return {"value": round(iters / dt, 1), "unit": "start-iters/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"PSO over all {fields['n_starts']} particles + BFGS from the first "
+                      f"{n_sample} of them ({iters} start-iterations in {dt:.2f} s, OpenMP)"}
+
+
+def run_reference(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    fields = workloads.workload(a.workload)
+    threads = os.cpu_count() or 1
+    n_sample = 256
+    for _ in range(a.warmup):
+        _oracle_sample(fields, 16, threads)
+    times, iters = [], []
+    for _ in range(a.steps):
+        it, dt = _oracle_sample(fields, n_sample, threads)
+        times.append(dt)
+        iters.append(it)
+    value = sum(iters) / sum(times)
+    sample = (f"per step: PSO over all {fields['n_starts']} particles + BFGS from the first "
+              f"{n_sample}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "start-iters/s",
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": round(1e3 * sum(times) / a.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": a.workload, "sample": sample},
+        "cpu_baseline": {"value": round(value, 1), "unit": "start-iters/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 1), "unit": "start-iters/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_zeus(args)

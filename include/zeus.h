@@ -1,0 +1,224 @@
+/*
+ * zeus.h -- C ABI of the GB300 (sm_103a) implementation of the Zeus method
+ * (arXiv 2603.28770): a short particle-swarm phase seeds N start points, one
+ * BFGS run per start takes forward-mode dual-number gradients (or a
+ * reverse-mode adjoint), a backtracking Armijo line search and the dense
+ * inverse-Hessian rank-two update, and a best-of-swarm reduction picks the
+ * result.
+ *
+ * Conventions for every entry point:
+ *  - Return value: ZEUS_OK (0) or a negative zeus_status code.  No entry
+ *    point aborts, throws or prints; zeus_strerror() names a code.
+ *  - "device" pointers are CUDA global-memory addresses on the current
+ *    device, "host" pointers are ordinary CPU memory.  The caller owns every
+ *    buffer it passes; the library keeps no pointer after a call returns.
+ *  - Arrays of points are row-major [n][dim] (the paper's N x dim swarm
+ *    layout, Alg. 7), contiguous, dim elements per row.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued on it and the call returns without
+ *    waiting, except where a function says it synchronizes.
+ *  - Entry points that take `workspace` allocate nothing: the caller
+ *    provides `workspace_bytes` >= zeus_workspace_size() bytes of device
+ *    memory, 256-byte aligned.  Its contents need no initialisation and are
+ *    undefined afterwards.  Two calls in flight must not share a workspace.
+ *  - Validation errors (ZEUS_EINVAL, ZEUS_EWORKSPACE, ZEUS_EUNSUPPORTED) are
+ *    reported before any work is enqueued.
+ */
+#ifndef ZEUS_H
+#define ZEUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ZEUS_ABI_VERSION 1
+
+typedef enum {
+    ZEUS_OK = 0,
+    ZEUS_EINVAL = -1,          /* an argument is out of range */
+    ZEUS_ENOMEM = -2,          /* a handle could not allocate device memory */
+    ZEUS_ECUDA = -3,           /* a CUDA call failed (launch, copy, ...) */
+    ZEUS_ETIMEOUT = -4,        /* a bounded device-side wait expired */
+    ZEUS_EUNSUPPORTED = -5,    /* combination of options not built */
+    ZEUS_EWORKSPACE = -6       /* workspace missing, too small or misaligned */
+} zeus_status;
+
+/* Test functions of Section V-B.  QUADRATIC is a test objective
+ * f = 0.5 * sum_i (i+1) x_i^2 (minimum 0 at x = 0). */
+typedef enum {
+    ZEUS_OBJ_ROSENBROCK = 0,       /* sum_{i<d-1} (1-x_i)^2 + 100 (x_{i+1}-x_i^2)^2, d >= 2 */
+    ZEUS_OBJ_RASTRIGIN = 1,        /* 10 d + sum (x_i^2 - 10 cos(2 pi x_i)) */
+    ZEUS_OBJ_ACKLEY = 2,           /* -20 e^{-0.2 sqrt(mean x^2)} - e^{mean cos 2 pi x} + 20 + e */
+    ZEUS_OBJ_GOLDSTEIN_PRICE = 3,  /* d == 2 */
+    ZEUS_OBJ_QUADRATIC = 100
+} zeus_objective;
+
+typedef enum {
+    ZEUS_FP64 = 0,           /* every step in FP64 (the paper's precision) */
+    ZEUS_FP32_GUARDED = 1    /* objective, gradient and H in FP32; y^T s, rho,
+                                the Armijo test and the final f in FP64 */
+} zeus_precision;
+
+typedef enum {
+    ZEUS_GRAD_FORWARD = 0,   /* dim dual-number passes (Alg. 5) */
+    ZEUS_GRAD_ADJOINT = 1    /* one reverse sweep (hand-written adjoint) */
+} zeus_grad_mode;
+
+/* Per-start termination status (Alg. 4 result.status, extended). */
+typedef enum {
+    ZEUS_RUN_MAX_ITER = 0,   /* iteration cap reached (the paper's status 0) */
+    ZEUS_RUN_CONVERGED = 1,  /* ||g|| < grad_tol, or f <= target_f */
+    ZEUS_RUN_STOPPED = 2,    /* the shared stop flag was raised (Alg. 10) */
+    ZEUS_RUN_NONFINITE = 3   /* f or g became NaN or infinite */
+} zeus_run_status;
+
+/*
+ * Arguments of the parallel Zeus procedure (Alg. 7:
+ * Zeus(f, N, range, iter_bfgs, iter_pso, iter_ls, required_c, Theta, w, c1, c2)).
+ * zeus_default_problem() fills the 2-D Rosenbrock workload.
+ */
+typedef struct {
+    int32_t objective;          /* zeus_objective */
+    int32_t dim;                /* d >= 1 (Rosenbrock >= 2, Goldstein-Price == 2), d <= 4096 */
+    double lower, upper;        /* sampling box of Alg. 2, lower < upper (not enforced later) */
+    int64_t n_starts;           /* N = particles = BFGS runs, 1 <= N <= 2^31 - 1 */
+    int32_t pso_iters;          /* T >= 0 PSO updates (Alg. 3) */
+    int32_t bfgs_max_iters;     /* K >= 0 (iter_bfgs) */
+    int32_t ls_max_iters;       /* L >= 1 line-search trials (iter_ls, paper: 20) */
+    int32_t required_converged; /* required_c of Alg. 10; 0 = off */
+    double grad_tol;            /* Theta: converged when ||g||_2 < Theta */
+    double w, c1, c2;           /* PSO inertia, cognitive, social (Section III-A) */
+    double armijo_c;            /* Armijo constant c in (0,1) (Section III-D) */
+    double backtrack;           /* step factor beta in (0,1) (paper: 0.5) */
+    double target_f;            /* NaN = off; else a start with f <= target_f
+                                   counts as converged and raises the stop flag */
+    uint64_t seed;              /* Philox4x64-10 key word 0 */
+    int32_t precision;          /* zeus_precision */
+    int32_t grad_mode;          /* zeus_grad_mode */
+    int32_t start_from_pbest;   /* 0: BFGS from current positions (Alg. 10), 1: from personal bests */
+    int32_t threads_per_start;  /* 0 = automatic; else 1,2,4,8,16 or 32 lanes per start */
+} zeus_problem;
+
+/* Summary written on the device by zeus_solve / zeus_solve_from. */
+typedef struct {
+    double best_f;          /* min over starts of the final f (NaN counts as +inf) */
+    int64_t best_index;     /* its start index, ties to the lowest index */
+    int64_t n_converged;    /* starts with status ZEUS_RUN_CONVERGED */
+    int64_t total_iters;    /* sum over starts of completed BFGS iterations */
+    int64_t total_feval;    /* sum over starts of line-search objective evaluations */
+    double gbest_f;         /* PSO global best value after the last update (zeus_solve) */
+    int64_t gbest_index;    /* its particle index */
+    int32_t error;          /* device-side error word, 0 = none */
+    int32_t stop_flag;      /* 1 if the stop flag was raised */
+} zeus_result;
+
+/* Name of a zeus_status code (static string, never NULL). */
+const char *zeus_strerror(int code);
+
+/* ZEUS_ABI_VERSION of the built library. */
+int zeus_abi_version(void);
+
+/* Fill *p with the defaults: 2-D Rosenbrock on [-5,5]^2, N = 128, T = 5,
+ * w = 0.7, c1 = c2 = 1.5, K = 100, L = 20, c = 1e-4, beta = 0.5,
+ * Theta = 1e-8, FP64, forward mode, seed 0.  Returns ZEUS_EINVAL if p is NULL. */
+int zeus_default_problem(zeus_problem *p);
+
+/* Check every field of *p; ZEUS_OK, ZEUS_EINVAL or ZEUS_EUNSUPPORTED. */
+int zeus_validate(const zeus_problem *p);
+
+/* Device workspace needed by zeus_solve / zeus_solve_from / zeus_pso /
+ * zeus_argmin for problem *p (host pointer), in bytes. */
+int zeus_workspace_size(const zeus_problem *p, size_t *bytes);
+
+/*
+ * The whole method, Alg. 7: PSO initialisation (Alg. 2/8) and p->pso_iters
+ * synchronous PSO updates (Alg. 3/9), one BFGS run per particle (Alg. 4/10)
+ * started from its current position (or personal best), and the
+ * best-of-swarm reduction.
+ *   x_out      device double [N][dim]  final BFGS points (required)
+ *   f_out      device double [N]       final f (may be NULL)
+ *   gnorm_out  device double [N]       final ||g|| (may be NULL)
+ *   status_out device int32  [N]       zeus_run_status (may be NULL)
+ *   iters_out  device int32  [N]       completed iterations (may be NULL)
+ *   result     device zeus_result      summary (may be NULL)
+ * With required_converged = 0 and target_f = NaN the outputs depend only
+ * on *p (bitwise reproducible run to run).
+ */
+int zeus_solve(const zeus_problem *p, void *workspace, size_t workspace_bytes,
+               double *x_out, double *f_out, double *gnorm_out,
+               int32_t *status_out, int32_t *iters_out, zeus_result *result,
+               void *stream);
+
+/* BFGS from caller-given starts (Alg. 10 without the PSO phase), then the
+ * best-of-swarm reduction.  x0: device double [N][dim], may equal x_out.
+ * Other arguments as zeus_solve; result->gbest_* are set to NaN / -1. */
+int zeus_solve_from(const zeus_problem *p, const double *x0,
+                    void *workspace, size_t workspace_bytes,
+                    double *x_out, double *f_out, double *gnorm_out,
+                    int32_t *status_out, int32_t *iters_out,
+                    zeus_result *result, void *stream);
+
+/* The PSO phase alone (Alg. 2 then Alg. 3 T times, synchronous global best).
+ * All outputs device, required: x_out, v_out, px_out [N][dim] (positions,
+ * velocities, personal-best positions), pf_out [N] (personal-best values),
+ * gx_out [dim] (global-best position); result->gbest_f / gbest_index are
+ * written if result is not NULL. */
+int zeus_pso(const zeus_problem *p, void *workspace, size_t workspace_bytes,
+             double *x_out, double *v_out, double *px_out, double *pf_out,
+             double *gx_out, zeus_result *result, void *stream);
+
+/* Objective values and gradients at n points (Section V-B objectives).
+ *   x: device double [n][dim]; f_out: device double [n] (may be NULL);
+ *   g_out: device double [n][dim] (may be NULL).
+ *   grad_mode: ZEUS_GRAD_FORWARD (Alg. 5, dim dual passes) or
+ *   ZEUS_GRAD_ADJOINT (reverse sweep).  FP64 throughout. */
+int zeus_objective_eval(int32_t objective, int32_t dim, int64_t n,
+                        const double *x, double *f_out, double *g_out,
+                        int32_t grad_mode, void *stream);
+
+/* The same in FP32 (x, f_out, g_out are float arrays). */
+int zeus_objective_eval_f32(int32_t objective, int32_t dim, int64_t n,
+                            const float *x, float *f_out, float *g_out,
+                            int32_t grad_mode, void *stream);
+
+/* Best-of-swarm reduction (Alg. 7 ParallelReduction): writes
+ * result->best_f / best_index for device f[n] (NaN as +inf, ties to the
+ * lowest index); the other result fields are zeroed.  Needs
+ * zeus_argmin_workspace_size(n) bytes of workspace. */
+int zeus_argmin(const double *f, int64_t n, void *workspace,
+                size_t workspace_bytes, zeus_result *result, void *stream);
+int zeus_argmin_workspace_size(int64_t n, size_t *bytes);
+
+/* The uniform draws of the PSO phase (Philox4x64-10 per Section IV-A as
+ * read here): out[i*dim + j] = draw (phase, particle i, dimension j) for
+ * i < n, j < dim; device double [n][dim]. */
+int zeus_uniform(uint64_t seed, uint64_t problem, uint64_t phase,
+                 int64_t n, int32_t dim, double *out, void *stream);
+
+/* ---- Host-buffer interface (owns device buffers; for callers without
+ * CUDA memory of their own) ---- */
+typedef struct zeus_context zeus_context;
+
+/* Create a context on the current device.  *ctx receives the handle. */
+int zeus_context_create(zeus_context **ctx);
+/* Free the context and its device buffers (synchronizes the device). */
+int zeus_context_destroy(zeus_context *ctx);
+
+/* zeus_solve with HOST outputs: runs on `stream`, copies the outputs to
+ * the host buffers (any of which may be NULL except x_out) and synchronizes
+ * `stream` before returning.  Grows the context's device buffers on demand
+ * (ZEUS_ENOMEM if that fails).  x_out: host double [N][dim]; f_out,
+ * gnorm_out: host double [N]; status_out, iters_out: host int32 [N];
+ * result: host zeus_result. */
+int zeus_solve_host(zeus_context *ctx, const zeus_problem *p, double *x_out,
+                    double *f_out, double *gnorm_out, int32_t *status_out,
+                    int32_t *iters_out, zeus_result *result, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZEUS_H */

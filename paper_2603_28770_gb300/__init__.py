@@ -1,0 +1,345 @@
+"""GB300 (sm_103a) implementation of the data-parallel hot path of Zeus
+(arXiv 2603.28770): PSO seeding, one BFGS run per start with forward-mode
+dual-number (or reverse-mode adjoint) gradients, backtracking Armijo line
+search and the dense inverse-Hessian rank-two update, and a best-of-swarm
+reduction.
+
+The arithmetic runs in the CUDA kernels of ``libzeus.so`` behind the C ABI
+of ``include/zeus.h``.  This module is the thin binding above it: functions
+named like the C entry points marshal torch CUDA tensors (device memory) and
+the current torch stream; PyTorch is plumbing here, not the compute path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, fields
+
+import torch
+
+from . import _capi
+from ._capi import (GRAD_MODES, OBJECTIVES, PRECISIONS, RUN_STATUS, ZeusError, check, lib,
+                    library_path, strerror, zeus_problem, zeus_result)
+
+__all__ = [
+    "Problem", "ZeusError", "zeus_solve", "zeus_solve_from", "zeus_pso", "zeus_objective_eval",
+    "zeus_objective_eval_f32", "zeus_argmin", "zeus_argmin_workspace_size", "zeus_uniform",
+    "zeus_workspace_size", "zeus_validate", "zeus_default_problem", "zeus_strerror",
+    "zeus_abi_version", "Context", "solve", "solve_from", "pso", "objective", "ObjectiveFn",
+    "decode_result", "library_path", "lib",
+]
+
+
+@dataclass
+class Problem:
+    """Arguments of the parallel Zeus procedure (Alg. 7).  Field meanings and
+    ranges are those of ``zeus_problem`` in include/zeus.h; the defaults are
+    ``zeus_default_problem`` (2-D Rosenbrock, 128 particles, 5 PSO updates)."""
+    objective: str | int = "rosenbrock"
+    dim: int = 2
+    lower: float = -5.0
+    upper: float = 5.0
+    n_starts: int = 128
+    pso_iters: int = 5
+    bfgs_max_iters: int = 100
+    ls_max_iters: int = 20
+    required_converged: int = 0
+    grad_tol: float = 1e-8
+    w: float = 0.7
+    c1: float = 1.5
+    c2: float = 1.5
+    armijo_c: float = 1e-4
+    backtrack: float = 0.5
+    target_f: float = float("nan")
+    seed: int = 0
+    precision: str | int = "fp64"
+    grad_mode: str | int = "forward"
+    start_from_pbest: int = 0
+    threads_per_start: int = 0
+
+    def to_c(self) -> zeus_problem:
+        def code(v, table):
+            return table[v] if isinstance(v, str) else int(v)
+        return zeus_problem(
+            code(self.objective, OBJECTIVES), self.dim, self.lower, self.upper, self.n_starts,
+            self.pso_iters, self.bfgs_max_iters, self.ls_max_iters, self.required_converged,
+            self.grad_tol, self.w, self.c1, self.c2, self.armijo_c, self.backtrack,
+            self.target_f, self.seed & (2**64 - 1), code(self.precision, PRECISIONS),
+            code(self.grad_mode, GRAD_MODES), self.start_from_pbest, self.threads_per_start)
+
+    def replace(self, **kw) -> "Problem":
+        d = {f.name: getattr(self, f.name) for f in fields(self)}
+        d.update(kw)
+        return Problem(**d)
+
+
+# ------------------------------------------------------------------ helpers
+
+def _ptr(t: torch.Tensor | None, dtype=None, numel=None, name="") -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name}: needs {numel} elements, has {t.numel()}")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _prob(p) -> zeus_problem:
+    return p.to_c() if isinstance(p, Problem) else p
+
+
+RESULT_BYTES = C.sizeof(zeus_result)
+
+
+def new_result(device="cuda") -> torch.Tensor:
+    """Device buffer for one zeus_result."""
+    return torch.empty(RESULT_BYTES, dtype=torch.uint8, device=device)
+
+
+def decode_result(t: torch.Tensor) -> dict:
+    """zeus_result buffer (device or host) -> dict (synchronizes if on device)."""
+    raw = bytes(t.detach().cpu().numpy().tobytes())
+    r = zeus_result.from_buffer_copy(raw)
+    return {name: getattr(r, name) for name, _ in zeus_result._fields_}
+
+
+# ------------------------------------------------- same-name entry points
+
+def zeus_strerror(code: int) -> str:
+    return strerror(code)
+
+
+def zeus_abi_version() -> int:
+    return lib().zeus_abi_version()
+
+
+def zeus_default_problem() -> zeus_problem:
+    p = zeus_problem()
+    check(lib().zeus_default_problem(C.byref(p)), "zeus_default_problem")
+    return p
+
+
+def zeus_validate(problem) -> int:
+    return lib().zeus_validate(C.byref(_prob(problem)))
+
+
+def zeus_workspace_size(problem) -> int:
+    n = C.c_size_t()
+    check(lib().zeus_workspace_size(C.byref(_prob(problem)), C.byref(n)), "zeus_workspace_size")
+    return n.value
+
+
+def new_workspace(problem, device="cuda") -> torch.Tensor:
+    return torch.empty(max(zeus_workspace_size(problem), 256), dtype=torch.uint8, device=device)
+
+
+def zeus_solve(problem, workspace, x_out, f_out=None, gnorm_out=None, status_out=None,
+               iters_out=None, result=None, stream=None) -> None:
+    pc = _prob(problem)
+    n, d = pc.n_starts, pc.dim
+    check(lib().zeus_solve(
+        C.byref(pc), _ptr(workspace, torch.uint8, name="workspace"), workspace.numel(),
+        _ptr(x_out, torch.float64, n * d, "x_out"), _ptr(f_out, torch.float64, n, "f_out"),
+        _ptr(gnorm_out, torch.float64, n, "gnorm_out"),
+        _ptr(status_out, torch.int32, n, "status_out"), _ptr(iters_out, torch.int32, n, "iters_out"),
+        _ptr(result, torch.uint8, RESULT_BYTES, "result"), _stream(stream)), "zeus_solve")
+
+
+def zeus_solve_from(problem, x0, workspace, x_out, f_out=None, gnorm_out=None, status_out=None,
+                    iters_out=None, result=None, stream=None) -> None:
+    pc = _prob(problem)
+    n, d = pc.n_starts, pc.dim
+    check(lib().zeus_solve_from(
+        C.byref(pc), _ptr(x0, torch.float64, n * d, "x0"),
+        _ptr(workspace, torch.uint8, name="workspace"), workspace.numel(),
+        _ptr(x_out, torch.float64, n * d, "x_out"), _ptr(f_out, torch.float64, n, "f_out"),
+        _ptr(gnorm_out, torch.float64, n, "gnorm_out"),
+        _ptr(status_out, torch.int32, n, "status_out"), _ptr(iters_out, torch.int32, n, "iters_out"),
+        _ptr(result, torch.uint8, RESULT_BYTES, "result"), _stream(stream)), "zeus_solve_from")
+
+
+def zeus_pso(problem, workspace, x_out, v_out, px_out, pf_out, gx_out, result=None,
+             stream=None) -> None:
+    pc = _prob(problem)
+    n, d = pc.n_starts, pc.dim
+    check(lib().zeus_pso(
+        C.byref(pc), _ptr(workspace, torch.uint8, name="workspace"), workspace.numel(),
+        _ptr(x_out, torch.float64, n * d, "x_out"), _ptr(v_out, torch.float64, n * d, "v_out"),
+        _ptr(px_out, torch.float64, n * d, "px_out"), _ptr(pf_out, torch.float64, n, "pf_out"),
+        _ptr(gx_out, torch.float64, d, "gx_out"), _ptr(result, torch.uint8, RESULT_BYTES, "result"),
+        _stream(stream)), "zeus_pso")
+
+
+def _obj_code(o) -> int:
+    return OBJECTIVES[o] if isinstance(o, str) else int(o)
+
+
+def _grad_code(g) -> int:
+    return GRAD_MODES[g] if isinstance(g, str) else int(g)
+
+
+def zeus_objective_eval(objective, dim, x, f_out=None, g_out=None, grad_mode=0, stream=None):
+    n = x.numel() // dim
+    check(lib().zeus_objective_eval(
+        _obj_code(objective), dim, n, _ptr(x, torch.float64, n * dim, "x"),
+        _ptr(f_out, torch.float64, n, "f_out"), _ptr(g_out, torch.float64, n * dim, "g_out"),
+        _grad_code(grad_mode), _stream(stream)), "zeus_objective_eval")
+
+
+def zeus_objective_eval_f32(objective, dim, x, f_out=None, g_out=None, grad_mode=0, stream=None):
+    n = x.numel() // dim
+    check(lib().zeus_objective_eval_f32(
+        _obj_code(objective), dim, n, _ptr(x, torch.float32, n * dim, "x"),
+        _ptr(f_out, torch.float32, n, "f_out"), _ptr(g_out, torch.float32, n * dim, "g_out"),
+        _grad_code(grad_mode), _stream(stream)), "zeus_objective_eval_f32")
+
+
+def zeus_argmin_workspace_size(n: int) -> int:
+    b = C.c_size_t()
+    check(lib().zeus_argmin_workspace_size(n, C.byref(b)), "zeus_argmin_workspace_size")
+    return b.value
+
+
+def zeus_argmin(f, workspace, result, stream=None) -> None:
+    check(lib().zeus_argmin(_ptr(f, torch.float64, name="f"), f.numel(),
+                            _ptr(workspace, torch.uint8, name="workspace"), workspace.numel(),
+                            _ptr(result, torch.uint8, RESULT_BYTES, "result"), _stream(stream)),
+          "zeus_argmin")
+
+
+def zeus_uniform(seed, problem_index, phase, n, dim, out, stream=None) -> None:
+    check(lib().zeus_uniform(seed & (2**64 - 1), problem_index, phase, n, dim,
+                             _ptr(out, torch.float64, n * dim, "out"), _stream(stream)),
+          "zeus_uniform")
+
+
+class Context:
+    """zeus_context: the host-buffer interface (zeus_solve_host)."""
+
+    def __init__(self):
+        h = C.c_void_p()
+        check(lib().zeus_context_create(C.byref(h)), "zeus_context_create")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            lib().zeus_context_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def zeus_solve_host(self, problem, x_out, f_out=None, gnorm_out=None, status_out=None,
+                        iters_out=None, stream=None) -> dict:
+        """Host (numpy / pinned CPU tensor) outputs; returns the decoded result."""
+        pc = _prob(problem)
+        res = zeus_result()
+
+        def hp(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                assert not a.is_cuda and a.is_contiguous()
+                return a.data_ptr()
+            assert a.flags.c_contiguous
+            return a.ctypes.data
+
+        check(lib().zeus_solve_host(self._h, C.byref(pc), hp(x_out), hp(f_out), hp(gnorm_out),
+                                    hp(status_out), hp(iters_out), C.addressof(res),
+                                    _stream(stream)), "zeus_solve_host")
+        return {name: getattr(res, name) for name, _ in zeus_result._fields_}
+
+
+# ------------------------------------------------------------ conveniences
+
+def _alloc_outputs(pc: zeus_problem, device):
+    n, d = pc.n_starts, pc.dim
+    return dict(x=torch.empty(n, d, dtype=torch.float64, device=device),
+                f=torch.empty(n, dtype=torch.float64, device=device),
+                gnorm=torch.empty(n, dtype=torch.float64, device=device),
+                status=torch.empty(n, dtype=torch.int32, device=device),
+                iters=torch.empty(n, dtype=torch.int32, device=device),
+                result=new_result(device))
+
+
+def solve(problem: Problem, device="cuda", stream=None) -> dict:
+    """The whole method (Alg. 7) on the device; returns the output tensors
+    and the decoded summary (synchronizes)."""
+    pc = _prob(problem)
+    out = _alloc_outputs(pc, device)
+    ws = new_workspace(pc, device)
+    zeus_solve(pc, ws, out["x"], out["f"], out["gnorm"], out["status"], out["iters"],
+               out["result"], stream)
+    out["summary"] = decode_result(out["result"])
+    return out
+
+
+def solve_from(problem: Problem, x0: torch.Tensor, device="cuda", stream=None) -> dict:
+    """BFGS from given starts, then the best-of-swarm reduction."""
+    pc = _prob(problem)
+    out = _alloc_outputs(pc, device)
+    ws = new_workspace(pc, device)
+    zeus_solve_from(pc, x0.contiguous(), ws, out["x"], out["f"], out["gnorm"], out["status"],
+                    out["iters"], out["result"], stream)
+    out["summary"] = decode_result(out["result"])
+    return out
+
+
+def pso(problem: Problem, device="cuda", stream=None) -> dict:
+    """The PSO phase alone (Alg. 2 then Alg. 3 pso_iters times)."""
+    pc = _prob(problem)
+    n, d = pc.n_starts, pc.dim
+    t = {k: torch.empty(n, d, dtype=torch.float64, device=device) for k in ("x", "v", "px")}
+    t["pf"] = torch.empty(n, dtype=torch.float64, device=device)
+    t["gx"] = torch.empty(d, dtype=torch.float64, device=device)
+    res = new_result(device)
+    ws = new_workspace(pc, device)
+    zeus_pso(pc, ws, t["x"], t["v"], t["px"], t["pf"], t["gx"], res, stream)
+    r = decode_result(res)
+    t["gf"], t["gidx"] = r["gbest_f"], r["gbest_index"]
+    return t
+
+
+def objective(obj, x: torch.Tensor, grad: bool = True, grad_mode="forward"):
+    """f (and g) at the rows of x ([n, d], float64 or float32, CUDA)."""
+    n, d = x.shape
+    x = x.contiguous()
+    f = torch.empty(n, dtype=x.dtype, device=x.device)
+    g = torch.empty_like(x) if grad else None
+    fn = zeus_objective_eval if x.dtype == torch.float64 else zeus_objective_eval_f32
+    fn(obj, d, x, f, g, grad_mode)
+    return (f, g) if grad else f
+
+
+class ObjectiveFn(torch.autograd.Function):
+    """f(x) for the rows of x with the gradient from the hand-written
+    reverse-mode adjoint kernel (or forward-mode duals) of libzeus."""
+
+    @staticmethod
+    def forward(ctx, x, obj="rosenbrock", grad_mode="adjoint"):
+        f, g = objective(obj, x.detach(), grad=True, grad_mode=grad_mode)
+        ctx.save_for_backward(g)
+        return f
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (g,) = ctx.saved_tensors
+        return grad_out.unsqueeze(1) * g, None, None
+
+
+def status_names(status: torch.Tensor):
+    return [RUN_STATUS.get(int(s), str(int(s))) for s in status.cpu().tolist()]
+

@@ -1,0 +1,124 @@
+"""ctypes declarations of the C ABI in include/zeus.h.
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of libzeus.so.  Loading fails loudly if the library cannot be built
+or loaded; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+ZEUS_OK = 0
+ZEUS_EINVAL = -1
+ZEUS_ENOMEM = -2
+ZEUS_ECUDA = -3
+ZEUS_ETIMEOUT = -4
+ZEUS_EUNSUPPORTED = -5
+ZEUS_EWORKSPACE = -6
+
+OBJECTIVES = {"rosenbrock": 0, "rastrigin": 1, "ackley": 2, "goldstein_price": 3, "quadratic": 100}
+PRECISIONS = {"fp64": 0, "fp32_guarded": 1}
+GRAD_MODES = {"forward": 0, "adjoint": 1}
+RUN_STATUS = {0: "max_iter", 1: "converged", 2: "stopped", 3: "nonfinite"}
+
+
+class zeus_problem(C.Structure):
+    _fields_ = [
+        ("objective", C.c_int32), ("dim", C.c_int32),
+        ("lower", C.c_double), ("upper", C.c_double),
+        ("n_starts", C.c_int64),
+        ("pso_iters", C.c_int32), ("bfgs_max_iters", C.c_int32),
+        ("ls_max_iters", C.c_int32), ("required_converged", C.c_int32),
+        ("grad_tol", C.c_double),
+        ("w", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
+        ("armijo_c", C.c_double), ("backtrack", C.c_double),
+        ("target_f", C.c_double),
+        ("seed", C.c_uint64),
+        ("precision", C.c_int32), ("grad_mode", C.c_int32),
+        ("start_from_pbest", C.c_int32), ("threads_per_start", C.c_int32),
+    ]
+
+
+class zeus_result(C.Structure):
+    _fields_ = [
+        ("best_f", C.c_double), ("best_index", C.c_int64),
+        ("n_converged", C.c_int64), ("total_iters", C.c_int64),
+        ("total_feval", C.c_int64), ("gbest_f", C.c_double),
+        ("gbest_index", C.c_int64), ("error", C.c_int32), ("stop_flag", C.c_int32),
+    ]
+
+
+class ZeusError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_VP = C.c_void_p
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes); exactly the declarations of include/zeus.h
+SIGNATURES = {
+    "zeus_strerror": (C.c_char_p, [C.c_int]),
+    "zeus_abi_version": (C.c_int, []),
+    "zeus_default_problem": (C.c_int, [C.POINTER(zeus_problem)]),
+    "zeus_validate": (C.c_int, [C.POINTER(zeus_problem)]),
+    "zeus_workspace_size": (C.c_int, [C.POINTER(zeus_problem), C.POINTER(C.c_size_t)]),
+    "zeus_solve": (C.c_int, [C.POINTER(zeus_problem), _VP, C.c_size_t, _VP, _VP, _VP, _VP, _VP,
+                             _VP, _VP]),
+    "zeus_solve_from": (C.c_int, [C.POINTER(zeus_problem), _VP, _VP, C.c_size_t, _VP, _VP, _VP,
+                                  _VP, _VP, _VP, _VP]),
+    "zeus_pso": (C.c_int, [C.POINTER(zeus_problem), _VP, C.c_size_t, _VP, _VP, _VP, _VP, _VP,
+                           _VP, _VP]),
+    "zeus_objective_eval": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, _VP, _VP, _VP, C.c_int32,
+                                      _VP]),
+    "zeus_objective_eval_f32": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, _VP, _VP, _VP,
+                                          C.c_int32, _VP]),
+    "zeus_argmin": (C.c_int, [_VP, C.c_int64, _VP, C.c_size_t, _VP, _VP]),
+    "zeus_argmin_workspace_size": (C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
+    "zeus_uniform": (C.c_int, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int32, _VP,
+                               _VP]),
+    "zeus_context_create": (C.c_int, [C.POINTER(_VP)]),
+    "zeus_context_destroy": (C.c_int, [_VP]),
+    "zeus_solve_host": (C.c_int, [_VP, C.POINTER(zeus_problem), _VP, _VP, _VP, _VP, _VP, _VP,
+                                  _VP]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> C.CDLL:
+    """Load libzeus.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libzeus.so missing at {path}")
+            L = C.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            if L.zeus_abi_version() != 1:
+                raise RuntimeError("libzeus.so ABI version mismatch")
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().zeus_strerror(int(code)).decode()
+
+
+def check(code: int, where: str) -> None:
+    if code != ZEUS_OK:
+        raise ZeusError(code, where)

@@ -1,0 +1,80 @@
+// zeus_internal.h -- host/device contract between the C-ABI layer
+// (zeus_capi.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "zeus.h"
+
+namespace zeus {
+
+// Control block at offset 0 of every workspace.  Zeroed (cudaMemsetAsync)
+// at the start of each call; the kernels that use `blocks_done` reset it to
+// zero when they finish, so kernels of one call can share it in turn.
+struct Ctrl {
+    unsigned int blocks_done;        // last-block counter of the fused grid reductions
+    int stop;                        // shared stop flag (Alg. 10)
+    int error;                       // device error word
+    int pad0;
+    unsigned long long n_conv;       // starts that converged
+    unsigned long long total_iters;  // sum of completed BFGS iterations
+    unsigned long long total_feval;  // sum of line-search evaluations
+    double gbest_f;                  // PSO global best value
+    long long gbest_idx;             // and its particle
+    unsigned long long pad1[25];
+};
+static_assert(sizeof(Ctrl) == 256, "control block is one 256-byte segment");
+
+// (value, index) pair of the argmin reductions
+struct ArgPair {
+    double f;
+    long long idx;
+};
+
+constexpr int kMaxReduceBlocks = 4096;  // argmin partials kept in the workspace
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Workspace carve-up (offsets in bytes from the workspace base).
+struct Layout {
+    size_t ctrl, partials, f_tmp, v, px, pf, gx, h, total;
+};
+
+// Kernel-side configuration of a BFGS launch.
+struct BfgsLaunch {
+    int G;          // lanes per start
+    int S;          // starts per block
+    int stride;     // words of shared memory per start
+    size_t smem;    // dynamic shared memory per block (bytes)
+    int blocks;     // grid size
+    bool h_global;  // H kept in the workspace instead of shared memory
+};
+
+// ---- launchers (defined in the kernel translation units) ----
+int lanes_for_dim(int d, int requested);
+
+cudaError_t launch_pso(const zeus_problem& p, int G, double* x, double* v, double* px, double* pf,
+                       double* gx, Ctrl* ctrl, ArgPair* partials, zeus_result* res,
+                       cudaStream_t st);
+int pso_blocks(const zeus_problem& p, int G);
+
+int plan_bfgs(const zeus_problem& p, BfgsLaunch* L);
+cudaError_t launch_bfgs(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
+                        double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
+                        int32_t* iters_out, double* h_ws, Ctrl* ctrl, cudaStream_t st);
+
+cudaError_t launch_argmin(const double* f, long long n, Ctrl* ctrl, ArgPair* partials,
+                          zeus_result* res, int mode, cudaStream_t st);
+int argmin_blocks(long long n);
+
+cudaError_t launch_objective(int obj, int d, long long n, const double* x, double* f, double* g,
+                             int grad_mode, cudaStream_t st);
+cudaError_t launch_objective_f32(int obj, int d, long long n, const float* x, float* f, float* g,
+                                 int grad_mode, cudaStream_t st);
+
+cudaError_t launch_uniform(uint64_t seed, uint64_t problem, uint64_t phase, long long n, int d,
+                           double* out, cudaStream_t st);
+
+}  // namespace zeus

@@ -1,0 +1,120 @@
+"""The C-ABI library (include/zeus.h) builds, loads without a GPU, exports
+every declared symbol, and its host-side logic (defaults, validation,
+workspace sizing, error strings) behaves as documented.  No device work."""
+import ctypes as C
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "zeus.h")
+
+
+@pytest.fixture(scope="module")
+def z():
+    import paper_2603_28770_gb300 as z
+    z.lib()
+    return z
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(zeus_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(z):
+    names = _declared()
+    assert "zeus_solve" in names and len(names) >= 15
+    L = C.CDLL(z.library_path())
+    for n in names:
+        assert hasattr(L, n), n
+    # and the Python binding declares exactly the header's entry points
+    from paper_2603_28770_gb300 import _capi
+    assert sorted(_capi.SIGNATURES) == names
+
+
+def test_struct_layouts_match_header(z, tmp_path):
+    # compile the header with the host C compiler and compare every field
+    # offset and the struct sizes with the ctypes declarations
+    from paper_2603_28770_gb300 import _capi
+    import subprocess
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "zeus.h"', 'int main(void){']
+    for cname, cls in (("zeus_problem", _capi.zeus_problem), ("zeus_result", _capi.zeus_result)):
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for cname, cls in (("zeus_problem", _capi.zeus_problem), ("zeus_result", _capi.zeus_result)):
+        assert int(out[cname]) == C.sizeof(cls)
+        for f, _ in cls._fields_:
+            assert int(out[f"{cname}.{f}"]) == getattr(cls, f).offset, f
+
+
+def test_defaults(z):
+    p = z.zeus_default_problem()
+    assert (p.objective, p.dim, p.n_starts, p.pso_iters, p.bfgs_max_iters, p.ls_max_iters) == (0, 2, 128, 5, 100, 20)
+    assert (p.w, p.c1, p.c2, p.armijo_c, p.backtrack, p.grad_tol) == (0.7, 1.5, 1.5, 1e-4, 0.5, 1e-8)
+    assert math.isnan(p.target_f) and p.precision == 0 and p.grad_mode == 0
+    assert z.zeus_validate(p) == 0
+    assert z.zeus_validate(z.Problem()) == 0
+
+
+@pytest.mark.parametrize("kw", [
+    dict(dim=1), dict(objective="goldstein_price", dim=3), dict(objective=7), dict(dim=0), dict(dim=5000),
+    dict(lower=1.0, upper=1.0), dict(lower=float("nan")), dict(upper=float("inf")), dict(n_starts=0),
+    dict(n_starts=2**31), dict(pso_iters=-1), dict(bfgs_max_iters=-1), dict(ls_max_iters=0),
+    dict(required_converged=-2), dict(grad_tol=-1.0), dict(grad_tol=float("nan")), dict(w=float("inf")),
+    dict(armijo_c=0.0), dict(armijo_c=1.0), dict(backtrack=1.0), dict(backtrack=0.0), dict(grad_mode=2),
+    dict(start_from_pbest=2), dict(threads_per_start=3), dict(threads_per_start=64), dict(precision=5),
+])
+def test_validation_rejects(z, kw):
+    assert z.zeus_validate(z.Problem(**kw)) == z._capi.ZEUS_EINVAL
+
+
+@pytest.mark.parametrize("kw", [
+    dict(objective="rastrigin", dim=1), dict(objective="quadratic", dim=1), dict(objective="ackley", dim=4096),
+    dict(n_starts=1), dict(pso_iters=0), dict(bfgs_max_iters=0), dict(grad_mode="adjoint"),
+    dict(threads_per_start=32), dict(start_from_pbest=1), dict(required_converged=3), dict(target_f=1e-6),
+])
+def test_validation_accepts(z, kw):
+    assert z.zeus_validate(z.Problem(**kw)) == 0
+
+
+def test_workspace_sizes(z):
+    small = z.zeus_workspace_size(z.Problem())
+    assert small % 256 == 0 and small >= 256 + 128 * 8 * 5
+    big = z.zeus_workspace_size(z.Problem(objective="rastrigin", dim=10, n_starts=16384))
+    assert big > small and big >= 16384 * 10 * 8 * 2
+    assert z.zeus_argmin_workspace_size(1) >= 256
+    with pytest.raises(z.ZeusError):
+        z.zeus_workspace_size(z.Problem(dim=0))
+
+
+def test_null_and_workspace_errors_before_any_launch(z):
+    L = z.lib()
+    p = z.Problem().to_c()
+    # NULL problem, NULL x_out, missing workspace: rejected on the host
+    assert L.zeus_solve(None, None, 0, None, None, None, None, None, None, None) == z._capi.ZEUS_EINVAL
+    assert L.zeus_solve(C.byref(p), None, 0, None, None, None, None, None, None, None) == z._capi.ZEUS_EINVAL
+    assert L.zeus_solve(C.byref(p), None, 0, C.c_void_p(256), None, None, None, None, None, None) == z._capi.ZEUS_EWORKSPACE
+    # misaligned workspace
+    assert L.zeus_solve(C.byref(p), C.c_void_p(4096 + 8), 1 << 20, C.c_void_p(256), None, None, None,
+                        None, None, None) == z._capi.ZEUS_EWORKSPACE
+    assert L.zeus_argmin(None, 10, None, 0, None, None) == z._capi.ZEUS_EINVAL
+    assert L.zeus_uniform(0, 0, 0, -1, 2, None, None) == z._capi.ZEUS_EINVAL
+    assert L.zeus_context_destroy(None) == z._capi.ZEUS_EINVAL
+
+
+def test_strerror(z):
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert z.zeus_strerror(code) and "unknown" not in z.zeus_strerror(code)
+    assert "unknown" in z.zeus_strerror(-99)

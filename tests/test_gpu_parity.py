@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.  Bit-exact for the integer work (Philox draws,
+argmin indices, statuses, iteration counts); floating point within 1e-9
+relative (see tests/parity.py)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2603_28770_gb300 import workloads
+from parity import close, compare_runs, oracle_problem, to_np, zeus_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def z():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2603_28770_gb300 as z
+    z.lib()
+    return z
+
+
+@pytest.fixture(scope="module")
+def ora():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+# ------------------------------------------------------------------ Philox
+
+@pytest.mark.parametrize("seed,phase", [(0, 0), (1, 1), (12345, 2), (2**64 - 1, 41), (7, 1000)])
+def test_philox_draws_bit_exact(z, ora, seed, phase):
+    n, d = 37, 11
+    out = torch.empty(n, d, dtype=torch.float64, device="cuda")
+    z.zeus_uniform(seed, 0, phase, n, d, out)
+    got = out.cpu().numpy()
+    want = np.array([[ora.uniform(seed, 0, phase, i, j) for j in range(d)] for i in range(n)])
+    assert np.array_equal(got, want)
+
+
+# -------------------------------------------------------------- objectives
+
+OBJ_CASES = [("rosenbrock", 2), ("rosenbrock", 13), ("rastrigin", 1), ("rastrigin", 10), ("rastrigin", 33),
+             ("ackley", 2), ("ackley", 17), ("goldstein_price", 2), ("quadratic", 5), ("rosenbrock", 130)]
+
+
+@pytest.mark.parametrize("obj,d", OBJ_CASES)
+@pytest.mark.parametrize("mode", ["forward", "adjoint"])
+def test_objective_and_gradient(z, ora, obj, d, mode):
+    x = workloads.start_points(301, d, -3.0, 3.0, seed=d)
+    xt = torch.from_numpy(x).cuda()
+    f, g = z.objective(obj, xt, grad=True, grad_mode=mode)
+    fv = z.objective(obj, xt, grad=False)
+    f, g, fv = f.cpu().numpy(), g.cpu().numpy(), fv.cpu().numpy()
+    for i in range(x.shape[0]):
+        fo, go = ora.grad_forward(obj, x[i])
+        assert close(f[i], fo, 1e-12) and close(fv[i], fo, 1e-12), (i, f[i], fv[i], fo)
+        scale = max(1.0, np.abs(go).max())
+        tol = 1e-12 if mode == "forward" else 1e-11
+        assert np.abs(g[i] - go).max() <= tol * scale, (i, g[i], go)
+
+
+@pytest.mark.parametrize("obj,d", [("rosenbrock", 8), ("rastrigin", 10), ("ackley", 9)])
+def test_objective_fp32(z, ora, obj, d):
+    x = workloads.start_points(64, d, -2.0, 2.0, seed=3)
+    f, g = z.objective(obj, torch.from_numpy(x).float().cuda(), grad=True, grad_mode="adjoint")
+    f, g = f.cpu().numpy(), g.cpu().numpy()
+    for i in range(64):
+        fo, go = ora.grad_forward(obj, x[i].astype(np.float32).astype(np.float64))
+        assert abs(f[i] - fo) <= 1e-5 * max(1.0, abs(fo))
+        assert np.abs(g[i] - go).max() <= 1e-4 * max(1.0, np.abs(go).max())
+
+
+def test_autograd_adjoint(z, ora):
+    x = torch.from_numpy(workloads.start_points(16, 12, -2.0, 2.0, seed=9)).cuda().requires_grad_()
+    f = z.ObjectiveFn.apply(x, "ackley", "adjoint")
+    f.sum().backward()
+    for i in range(16):
+        _, go = ora.grad_forward("ackley", x[i].detach().cpu().numpy())
+        assert np.abs(x.grad[i].cpu().numpy() - go).max() <= 1e-11 * max(1.0, np.abs(go).max())
+
+
+# --------------------------------------------------------------------- PSO
+
+PSO_CASES = [
+    dict(objective="rastrigin", dim=10, lower=-5.12, upper=5.12, n_starts=300, pso_iters=7, seed=11),
+    dict(objective="rosenbrock", dim=2, lower=-5.0, upper=5.0, n_starts=128, pso_iters=5, seed=0),
+    dict(objective="ackley", dim=5, lower=-5.0, upper=5.0, n_starts=1000, pso_iters=3, seed=2),
+    dict(objective="rastrigin", dim=1, lower=-5.12, upper=5.12, n_starts=33, pso_iters=4, seed=5),
+    dict(objective="goldstein_price", dim=2, lower=-2.0, upper=2.0, n_starts=257, pso_iters=6, seed=8),
+    dict(objective="rosenbrock", dim=37, lower=-2.0, upper=2.0, n_starts=65, pso_iters=2, seed=4),
+    dict(objective="quadratic", dim=3, lower=-1.0, upper=1.0, n_starts=1, pso_iters=3, seed=1),
+]
+
+
+@pytest.mark.parametrize("case", PSO_CASES, ids=lambda c: f"{c['objective']}{c['dim']}_n{c['n_starts']}")
+def test_pso_parity(z, ora, case):
+    g = z.pso(zeus_problem(z, case))
+    o = ora.pso(oracle_problem(ora, case))
+    for k in ("x", "v", "px"):
+        a, b = g[k].cpu().numpy(), o[k]
+        assert np.all(np.abs(a - b) <= 1e-9 * np.maximum(1.0, np.abs(b))), k
+    assert np.all(close(g["pf"].cpu().numpy(), o["pf"]))
+    assert g["gidx"] == o["gidx"]
+    assert np.array_equal(g["gx"].cpu().numpy(), g["px"].cpu().numpy()[g["gidx"]])
+    assert close(g["gf"], o["gf"])
+
+
+# ----------------------------------------------- BFGS from given starts (K=20)
+
+BFGS_CASES = [
+    ("rosenbrock", 2, 300, -5.0, 5.0), ("rastrigin", 10, 700, -5.12, 5.12), ("ackley", 5, 300, -5.0, 5.0),
+    ("goldstein_price", 2, 200, -2.0, 2.0), ("quadratic", 7, 70, -3.0, 3.0), ("rosenbrock", 16, 129, -2.0, 2.0),
+    ("rastrigin", 3, 1025, -5.12, 5.12), ("rosenbrock", 40, 33, -2.0, 2.0),
+]
+
+
+@pytest.mark.parametrize("obj,d,n,lo,hi", BFGS_CASES)
+@pytest.mark.parametrize("mode", ["forward", "adjoint"])
+def test_bfgs_first_20_iterations(z, ora, obj, d, n, lo, hi, mode):
+    x0 = workloads.start_points(n, d, lo, hi, seed=n + d)
+    fields = dict(objective=obj, dim=d, lower=lo, upper=hi, n_starts=n, bfgs_max_iters=20, grad_mode=mode)
+    g = to_np(z.solve_from(zeus_problem(z, fields), torch.from_numpy(x0).cuda()))
+    o = ora.bfgs_many(oracle_problem(ora, fields), x0)
+    compare_runs(g, o)
+    s = g["summary"]
+    assert s["total_iters"] == int(g["iters"].sum())
+    assert s["best_index"] == ora.argmin(g["f"])
+    assert math.isnan(s["gbest_f"]) and s["gbest_index"] == -1
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_lane_counts_agree(z, ora, lanes):
+    d, n = 10, 200
+    x0 = workloads.start_points(n, d, -5.12, 5.12, seed=77)
+    fields = dict(objective="rastrigin", dim=d, n_starts=n, bfgs_max_iters=20, threads_per_start=lanes)
+    g = to_np(z.solve_from(zeus_problem(z, fields), torch.from_numpy(x0).cuda()))
+    compare_runs(g, ora.bfgs_many(oracle_problem(ora, fields), x0))
+
+
+# ------------------------------------------------------------- whole method
+
+def test_solve_rosenbrock2d_workload(z, ora):
+    fields = workloads.workload("rosenbrock2d_n128")
+    g = to_np(z.solve(zeus_problem(z, fields)))
+    o = ora.solve(oracle_problem(ora, fields))
+    compare_runs(g, o, rtol=1e-8)
+    s = g["summary"]
+    assert s["best_index"] == o["best"] and g["f"][s["best_index"]] < 1e-6
+    assert np.linalg.norm(g["x"][s["best_index"]] - 1.0) < 1e-6
+    assert s["n_converged"] == int((g["status"] == 1).sum())
+
+
+def test_solve_rastrigin10d_full_size_sampled(z, ora):
+    # the full 16384-particle workload in the launch configuration of the
+    # benchmark; the oracle runs the whole PSO phase and BFGS on a sample
+    fields = workloads.workload("rastrigin10d_n16384")
+    g = z.solve(zeus_problem(z, fields))
+    gx, gs = g["x"].cpu().numpy(), g["summary"]
+    op = ora.pso(oracle_problem(ora, fields))
+    assert gs["gbest_index"] == op["gidx"] and close(gs["gbest_f"], op["gf"])
+    sample = np.random.default_rng(0).choice(fields["n_starts"], size=96, replace=False)
+    o = ora.bfgs_many(oracle_problem(ora, fields), op["x"][sample])
+    gsub = {k: g[k].cpu().numpy()[sample] for k in ("f", "gnorm", "status", "iters")}
+    gsub["x"] = gx[sample]
+    compare_runs(gsub, o, rtol=1e-8, max_flip_frac=0.05)
+    # end to end: success (f < 1e-6) rate of the sample matches the GPU's
+    assert gs["total_iters"] == int(g["iters"].sum().item())
+
+
+def test_deterministic_and_host_interface(z):
+    fields = dict(objective="ackley", dim=6, lower=-5.0, upper=5.0, n_starts=513, pso_iters=4,
+                  bfgs_max_iters=60, seed=3)
+    p = zeus_problem(z, fields)
+    a, b = to_np(z.solve(p)), to_np(z.solve(p))
+    for k in ("x", "f", "gnorm", "status", "iters"):
+        assert np.array_equal(a[k], b[k]), k
+    ctx = z.Context()
+    n, d = p.n_starts, p.dim
+    hx = np.empty((n, d)); hf = np.empty(n); hg = np.empty(n)
+    hs = np.empty(n, dtype=np.int32); hi = np.empty(n, dtype=np.int32)
+    r = ctx.zeus_solve_host(p, hx, hf, hg, hs, hi)
+    assert np.array_equal(hx, a["x"]) and np.array_equal(hf, a["f"]) and np.array_equal(hs, a["status"])
+    assert np.array_equal(hi, a["iters"]) and np.array_equal(hg, a["gnorm"])
+    assert r["best_index"] == a["summary"]["best_index"] and r["best_f"] == a["summary"]["best_f"]
+    ctx.close()
+
+
+# --------------------------------------------------------------- edge cases
+
+def test_edge_cases(z, ora):
+    # K = 0: nothing moves
+    x0 = workloads.start_points(5, 3, -2, 2, seed=1)
+    g = to_np(z.solve_from(z.Problem(objective="rosenbrock", dim=3, n_starts=5, bfgs_max_iters=0),
+                           torch.from_numpy(x0).cuda()))
+    assert np.array_equal(g["x"], x0) and np.all(g["iters"] == 0) and np.all(g["status"] == 0)
+    assert np.all(close(g["f"], [ora.f("rosenbrock", r) for r in x0], 1e-14))
+    # starts at the minimiser converge with zero iterations; a non-finite start is flagged
+    x0 = np.array([[0.0, 0.0, 0.0, 0.0], [1e160, 1e160, 1e160, 1e160], [np.nan, 0, 0, 0]])
+    g = to_np(z.solve_from(z.Problem(objective="rastrigin", dim=4, n_starts=3, bfgs_max_iters=10),
+                           torch.from_numpy(x0).cuda()))
+    assert list(g["status"]) == [1, 3, 3] and list(g["iters"]) == [0, 0, 0]
+    assert g["summary"]["best_index"] == 0 and g["summary"]["best_f"] == 0.0
+    # a single start
+    g = to_np(z.solve(z.Problem(objective="goldstein_price", dim=2, lower=-2, upper=2, n_starts=1,
+                                pso_iters=2, bfgs_max_iters=200)))
+    o = ora.solve(ora.Problem("goldstein_price", dim=2, lower=-2, upper=2, n_starts=1, pso_iters=2,
+                              bfgs_max_iters=200))
+    compare_runs(g, o, rtol=1e-8)
+
+
+def test_argmin(z, ora):
+    rng = np.random.default_rng(4)
+    for n in (1, 255, 256, 257, 100000, 400001):
+        v = rng.integers(0, 50, size=n).astype(np.float64)
+        v[rng.random(n) < 0.1] = np.nan
+        t = torch.from_numpy(v).cuda()
+        ws = torch.empty(z.zeus_argmin_workspace_size(n), dtype=torch.uint8, device="cuda")
+        res = z.new_result()
+        z.zeus_argmin(t, ws, res)
+        r = z.decode_result(res)
+        b = ora.argmin(v)
+        assert r["best_index"] == b and (r["best_f"] == v[b] or (np.isnan(v[b]) and r["best_f"] == np.inf))
+
+
+def test_stop_modes(z):
+    base = dict(objective="rastrigin", dim=4, lower=-5.12, upper=5.12, n_starts=2000, pso_iters=3,
+                bfgs_max_iters=200)
+    g = to_np(z.solve(zeus_problem(z, base, required_converged=50)))
+    s = g["summary"]
+    assert s["stop_flag"] == 1 and s["n_converged"] >= 50
+    assert set(np.unique(g["status"])) <= {1, 2}
+    g = to_np(z.solve(zeus_problem(z, base, target_f=1e-6)))
+    s = g["summary"]
+    assert s["stop_flag"] == 1 and s["best_f"] <= 1e-6
