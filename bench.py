@@ -44,6 +44,7 @@ def _args():
     ap.add_argument("--impl", default="zeus", choices=["zeus", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--grad-mode", default="forward", choices=["forward", "adjoint"])
+    ap.add_argument("--lanes", type=int, default=0, help="threads per start (0 = automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -154,7 +155,7 @@ def run_zeus(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    fields = workloads.workload(a.workload, grad_mode=a.grad_mode)
+    fields = workloads.workload(a.workload, grad_mode=a.grad_mode, threads_per_start=a.lanes)
     # weak scaling: every rank solves its own independent multistart problem
     fields["seed"] = fields["seed"] + rank
     p = z.Problem(**{k: v for k, v in fields.items() if k in z.Problem.__dataclass_fields__})

@@ -99,7 +99,10 @@ typedef struct {
     int32_t precision;          /* zeus_precision */
     int32_t grad_mode;          /* zeus_grad_mode */
     int32_t start_from_pbest;   /* 0: BFGS from current positions (Alg. 10), 1: from personal bests */
-    int32_t threads_per_start;  /* 0 = automatic; else 1,2,4,8,16 or 32 lanes per start */
+    int32_t threads_per_start;  /* 0 = automatic: one lane per start for small d, with the
+                                   long-running starts handed to one 128-thread block
+                                   each; 1 = one lane per start throughout;
+                                   128 = one 128-thread block per start throughout */
 } zeus_problem;
 
 /* Summary written on the device by zeus_solve / zeus_solve_from. */
@@ -197,6 +200,16 @@ int zeus_argmin_workspace_size(int64_t n, size_t *bytes);
  * i < n, j < dim; device double [n][dim]. */
 int zeus_uniform(uint64_t seed, uint64_t problem, uint64_t phase,
                  int64_t n, int32_t dim, double *out, void *stream);
+
+/* The FP64 elementary functions the objectives use, for validation:
+ *   fn 0: y0 = sin(2 pi x), y1 = cos(2 pi x)  (the library's own method)
+ *   fn 1: y0 = e^x                             (the library's own method)
+ *   fn 2: y0, y1 = CUDA sincospi(2x)           (CUDA math library)
+ *   fn 3: y0 = CUDA exp(x)                     (CUDA math library)
+ * x, y0: device double [n]; y1: device double [n] for fn 0 and 2, else
+ * ignored (may be NULL). */
+int zeus_math_eval(int32_t fn, int64_t n, const double *x, double *y0, double *y1,
+                   void *stream);
 
 /* ---- Host-buffer interface (owns device buffers; for callers without
  * CUDA memory of their own) ---- */

@@ -119,6 +119,9 @@ def lib():
     L.zo_uniform.restype = C.c_double
     L.zo_dual_op.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
                              C.c_double, _D, _D]
+    L.zo_sincos2pi.argtypes = [C.c_double, _D, _D]
+    L.zo_exp.argtypes = [C.c_double]
+    L.zo_exp.restype = C.c_double
     L.zo_f.argtypes = [C.c_int, C.c_int, _D]
     L.zo_f.restype = C.c_double
     L.zo_grad_forward.argtypes = [C.c_int, C.c_int, _D, _D, _D]
@@ -176,9 +179,21 @@ def uniform(seed: int, problem: int, phase: int, particle: int, j: int) -> float
     return float(lib().zo_uniform(seed & (2**64 - 1), problem, phase, particle, j))
 
 
+def sincos2pi(x: float):
+    """(sin 2 pi x, cos 2 pi x) by the oracle's own exact-reduction Taylor method."""
+    sv, cv = C.c_double(), C.c_double()
+    lib().zo_sincos2pi(float(x), C.byref(sv), C.byref(cv))
+    return sv.value, cv.value
+
+
+def exp(x: float) -> float:
+    """e^x by the oracle's own Cody-Waite / Taylor method."""
+    return float(lib().zo_exp(float(x)))
+
+
 def dual_op(op: str, a1, b1, a2=0.0, b2=0.0):
     """One dual-number operation (Section III-C): returns (value, tangent)."""
-    code = ["add", "sub", "mul", "div", "sin", "cos", "exp", "sqrt"].index(op)
+    code = ["add", "sub", "mul", "div", "sin", "cos", "exp", "sqrt", "cos2pi"].index(op)
     ra, rb = C.c_double(), C.c_double()
     lib().zo_dual_op(code, a1, b1, a2, b2, C.byref(ra), C.byref(rb))
     return ra.value, rb.value

@@ -115,10 +115,89 @@ double zo_uniform(uint64_t seed, uint64_t problem, uint64_t phase,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Elementary functions of the objectives, FP64, written from published      */
+/* methods so that the reference fixes every bit (the CUDA library          */
+/* implements the same methods independently).                              */
+/* ------------------------------------------------------------------------ */
+
+/* Taylor coefficients of sin(2 pi s) = sum_k S_k s^(2k+1) and
+ * cos(2 pi s) = sum_k C_k s^(2k): S_k = (-1)^k (2 pi)^(2k+1) / (2k+1)!,
+ * C_k = (-1)^k (2 pi)^(2k) / (2k)!, rounded to double. */
+static const double ZO_S2PI[9] = {
+    0x1.921fb54442d18p+2, -0x1.4abbce625be53p+5, 0x1.466bc6775aae2p+6,
+    -0x1.32d2cce62bd86p+6, 0x1.50783487ee782p+5, -0x1.e3074fde8871fp+3,
+    0x1.e8f434d018d63p+1, -0x1.6fadb9f155744p-1, 0x1.aaec32af93359p-4};
+static const double ZO_C2PI[9] = {
+    0x1.0000000000000p+0, -0x1.3bd3cc9be45dep+4, 0x1.03c1f081b5ac4p+6,
+    -0x1.55d3c7e3cbffap+6, 0x1.e1f506891babbp+5, -0x1.a6d1f2a204a8cp+4,
+    0x1.f9d38a3763cc3p+2, -0x1.b6e24f44b128fp+0, 0x1.20c62c2f2d7f5p-2};
+
+/* sin(2 pi x) and cos(2 pi x).  Exact argument reduction: r = x - rint(x)
+ * (|r| <= 1/2), q = rint(4 r), s = r - q/4 (|s| <= 1/8), each step exact in
+ * binary floating point; then the Taylor series above through s^17 and s^16
+ * (truncation below 3e-18 on |s| <= 1/8) in Horner form with fused
+ * multiply-adds in s^2, and the quarter-turn identities for q. */
+void zo_sincos2pi(double x, double *sp, double *cp)
+{
+    double n = rint(x);
+    double r = x - n;
+    double qf = rint(4.0 * r);
+    double s = r - 0.25 * qf;
+    int q = ((int)qf) & 3;
+    double z = s * s;
+    double ps = ZO_S2PI[8], pc = ZO_C2PI[8];
+    for (int k = 7; k >= 0; --k) {
+        ps = fma(ps, z, ZO_S2PI[k]);
+        pc = fma(pc, z, ZO_C2PI[k]);
+    }
+    ps = ps * s;
+    switch (q) {
+    case 0: *sp = ps; *cp = pc; break;
+    case 1: *sp = pc; *cp = -ps; break;
+    case 2: *sp = -ps; *cp = -pc; break;
+    default: *sp = -pc; *cp = ps; break;
+    }
+}
+
+static double zo_cos2pi(double x)
+{
+    double s, c;
+    zo_sincos2pi(x, &s, &c);
+    return c;
+}
+
+/* e^x.  Cody & Waite reduction x = k ln2 + r with k = rint(x / ln2) and
+ * ln2 = L1 + L2, L1 holding 32 significant bits so that k L1 is exact;
+ * e^r by its Taylor series through r^13 (|r| <= 0.35, truncation below
+ * 5e-18) in Horner form with fused multiply-adds; exact scaling by 2^k. */
+static const double ZO_EXPC[14] = {
+    0x1.0000000000000p+0, 0x1.0000000000000p+0, 0x1.0000000000000p-1,
+    0x1.5555555555555p-3, 0x1.5555555555555p-5, 0x1.1111111111111p-7,
+    0x1.6c16c16c16c17p-10, 0x1.a01a01a01a01ap-13, 0x1.a01a01a01a01ap-16,
+    0x1.71de3a556c734p-19, 0x1.27e4fb7789f5cp-22, 0x1.ae64567f544e4p-26,
+    0x1.1eed8eff8d898p-29, 0x1.6124613a86d09p-33};  /* 1/k! */
+
+double zo_exp(double x)
+{
+    const double INV_LN2 = 0x1.71547652b82fep+0;
+    const double L1 = 0x1.62e42fee00000p-1, L2 = 0x1.a39ef35793c76p-33;
+    if (isnan(x)) return x;
+    if (x > 709.78) return INFINITY;
+    if (x < -745.2) return 0.0;
+    double k = rint(x * INV_LN2);
+    double r = (x - k * L1) - k * L2;
+    double p = ZO_EXPC[13];
+    for (int i = 12; i >= 0; --i) p = fma(p, r, ZO_EXPC[i]);
+    return ldexp(p, (int)k);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Dual numbers a + b*eps with eps^2 = 0 (Section III-C).                    */
 /* ------------------------------------------------------------------------ */
 
 typedef struct { double a, b; } zo_dual;
+
+static const double ZO_PI_ = 3.14159265358979323846;
 
 static zo_dual dconst(double a) { zo_dual r = {a, 0.0}; return r; }
 static zo_dual dadd(zo_dual x, zo_dual y) { zo_dual r = {x.a + y.a, x.b + y.b}; return r; }
@@ -139,7 +218,15 @@ static zo_dual dscale(double s, zo_dual x) { zo_dual r = {s * x.a, s * x.b}; ret
 /* g(a + b e) = g(a) + g'(a) b e */
 static zo_dual dsin(zo_dual x) { zo_dual r = {sin(x.a), cos(x.a) * x.b}; return r; }
 static zo_dual dcos(zo_dual x) { zo_dual r = {cos(x.a), -sin(x.a) * x.b}; return r; }
-static zo_dual dexp(zo_dual x) { double e = exp(x.a); zo_dual r = {e, e * x.b}; return r; }
+static zo_dual dexp(zo_dual x) { double e = zo_exp(x.a); zo_dual r = {e, e * x.b}; return r; }
+/* cos(2 pi x) as one primitive: (cos 2 pi a, -sin(2 pi a) (2 pi b)) */
+static zo_dual dcos2pi(zo_dual x)
+{
+    double s, c;
+    zo_sincos2pi(x.a, &s, &c);
+    zo_dual r = {c, -s * (2.0 * ZO_PI_ * x.b)};
+    return r;
+}
 /* Reading: d/du sqrt(u) at u = 0 is taken as 0 (Ackley's kink at the
  * origin, Section V-B, where the derivative is undefined). */
 static zo_dual dsqrt(zo_dual x)
@@ -163,6 +250,7 @@ void zo_dual_op(int op, double a1, double b1, double a2, double b2,
     case 5: r = dcos(x); break;
     case 6: r = dexp(x); break;
     case 7: r = dsqrt(x); break;
+    case 8: r = dcos2pi(x); break;
     default: r = dconst(NAN); break;
     }
     *ra = r.a;
@@ -173,7 +261,6 @@ void zo_dual_op(int op, double a1, double b1, double a2, double b2,
 /* Objectives (Section V-B), on doubles and on duals.                        */
 /* ------------------------------------------------------------------------ */
 
-static const double ZO_PI = 3.14159265358979323846;
 static const double ZO_E = 2.71828182845904523536;
 
 double zo_f(int obj, int d, const double *x)
@@ -192,16 +279,16 @@ double zo_f(int obj, int d, const double *x)
     case ZO_RASTRIGIN:
         s = 10.0 * (double)d;
         for (int i = 0; i < d; ++i)
-            s = s + (x[i] * x[i] - 10.0 * cos(2.0 * ZO_PI * x[i]));
+            s = s + (x[i] * x[i] - 10.0 * zo_cos2pi(x[i]));
         return s;
     case ZO_ACKLEY: {
         double s1 = 0.0, s2 = 0.0;
         for (int i = 0; i < d; ++i) {
             s1 = s1 + x[i] * x[i];
-            s2 = s2 + cos(2.0 * ZO_PI * x[i]);
+            s2 = s2 + zo_cos2pi(x[i]);
         }
-        double t1 = -20.0 * exp(-0.2 * sqrt(s1 / (double)d));
-        double t2 = exp(s2 / (double)d);
+        double t1 = -20.0 * zo_exp(-0.2 * sqrt(s1 / (double)d));
+        double t2 = zo_exp(s2 / (double)d);
         return (t1 - t2) + (20.0 + ZO_E);
     }
     case ZO_GOLDSTEIN_PRICE: {
@@ -241,14 +328,13 @@ static zo_dual zo_f_dual(int obj, int d, const zo_dual *x)
     case ZO_RASTRIGIN:
         s = dconst(10.0 * (double)d);
         for (int i = 0; i < d; ++i)
-            s = dadd(s, dsub(dmul(x[i], x[i]),
-                             dscale(10.0, dcos(dscale(2.0 * ZO_PI, x[i])))));
+            s = dadd(s, dsub(dmul(x[i], x[i]), dscale(10.0, dcos2pi(x[i]))));
         return s;
     case ZO_ACKLEY: {
         zo_dual s1 = dconst(0.0), s2 = dconst(0.0);
         for (int i = 0; i < d; ++i) {
             s1 = dadd(s1, dmul(x[i], x[i]));
-            s2 = dadd(s2, dcos(dscale(2.0 * ZO_PI, x[i])));
+            s2 = dadd(s2, dcos2pi(x[i]));
         }
         zo_dual t1 = dscale(-20.0, dexp(dscale(-0.2, dsqrt(ddiv(s1, dconst((double)d))))));
         zo_dual t2 = dexp(ddiv(s2, dconst((double)d)));
@@ -391,9 +477,13 @@ void zo_pso(const zo_problem *pr, double *x, double *v, double *px,
 /* the value after the last halving (beta^L), as in the printed loop.        */
 /* ------------------------------------------------------------------------ */
 
-static double track_margin(double margin, double lhs, double rhs, double scale)
+/* Relative margin of the comparison lhs <= rhs (or lhs < rhs), scaled by
+ * the magnitudes compared: below ~1e-12 a last-bit difference in either
+ * side could take the other branch. */
+static double track_margin(double margin, double lhs, double rhs)
 {
-    double m = fabs(lhs - rhs) / (fabs(scale) > 1.0 ? fabs(scale) : 1.0);
+    double s = fabs(lhs) > fabs(rhs) ? fabs(lhs) : fabs(rhs);
+    double m = fabs(lhs - rhs) / (s > 1e-300 ? s : 1e-300);
     return m < margin ? m : margin;
 }
 
@@ -408,7 +498,7 @@ double zo_line_search(int obj, int d, const double *x, const double *p,
         double ft = zo_f(obj, d, xt);
         (*n_feval)++;
         double rhs = f0 + c * alpha * ddir;
-        if (margin) *margin = track_margin(*margin, ft, rhs, f0);
+        if (margin) *margin = track_margin(*margin, ft, rhs);
         if (ft <= rhs) { *accepted = 1; break; }
         alpha = beta * alpha;
     }
@@ -491,7 +581,7 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
         if (k >= pr->bfgs_max_iters) { status = 0; break; }
         if (stop && *stop) { status = 2; break; }
         if (!isfinite(f0) || !finite_vec(d, g)) { status = 3; break; }
-        margin = track_margin(margin, gnorm, pr->grad_tol, pr->grad_tol);
+        margin = track_margin(margin, gnorm, pr->grad_tol);
         if (gnorm < pr->grad_tol) {
             status = 1;
             if (n_conv) {

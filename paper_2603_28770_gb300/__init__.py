@@ -24,7 +24,7 @@ __all__ = [
     "Problem", "ZeusError", "zeus_solve", "zeus_solve_from", "zeus_pso", "zeus_objective_eval",
     "zeus_objective_eval_f32", "zeus_argmin", "zeus_argmin_workspace_size", "zeus_uniform",
     "zeus_workspace_size", "zeus_validate", "zeus_default_problem", "zeus_strerror",
-    "zeus_abi_version", "Context", "solve", "solve_from", "pso", "objective", "ObjectiveFn",
+    "zeus_abi_version", "zeus_math_eval", "Context", "solve", "solve_from", "pso", "objective", "ObjectiveFn",
     "decode_result", "library_path", "lib",
 ]
 
@@ -221,6 +221,13 @@ def zeus_uniform(seed, problem_index, phase, n, dim, out, stream=None) -> None:
     check(lib().zeus_uniform(seed & (2**64 - 1), problem_index, phase, n, dim,
                              _ptr(out, torch.float64, n * dim, "out"), _stream(stream)),
           "zeus_uniform")
+
+
+def zeus_math_eval(fn: int, x, y0, y1=None, stream=None) -> None:
+    check(lib().zeus_math_eval(fn, x.numel(), _ptr(x, torch.float64, name="x"),
+                               _ptr(y0, torch.float64, x.numel(), "y0"),
+                               _ptr(y1, torch.float64, x.numel(), "y1"), _stream(stream)),
+          "zeus_math_eval")
 
 
 class Context:

@@ -31,7 +31,9 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    # --fmad=false: every product and sum is rounded on its own, as in the
+    # FP64 oracle, so rational-operation objectives reproduce it bit for bit
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
                    "-I", INCLUDE, "-I", CSRC, *extra]
 
 

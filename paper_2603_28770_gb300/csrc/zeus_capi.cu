@@ -16,7 +16,7 @@ namespace {
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-bool is_pow2_lanes(int g) { return g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32; }
+bool valid_lanes(int g) { return g == 0 || g == 1 || g == kWideThreads; }
 
 int validate(const zeus_problem* p) {
     if (!p) return ZEUS_EINVAL;
@@ -48,7 +48,7 @@ int validate(const zeus_problem* p) {
     if (!(p->backtrack > 0.0 && p->backtrack < 1.0)) return ZEUS_EINVAL;
     if (p->grad_mode != ZEUS_GRAD_FORWARD && p->grad_mode != ZEUS_GRAD_ADJOINT) return ZEUS_EINVAL;
     if (p->start_from_pbest != 0 && p->start_from_pbest != 1) return ZEUS_EINVAL;
-    if (!is_pow2_lanes(p->threads_per_start)) return ZEUS_EINVAL;
+    if (!valid_lanes(p->threads_per_start)) return ZEUS_EINVAL;
     if (p->precision == ZEUS_FP32_GUARDED) return ZEUS_EUNSUPPORTED;
     if (p->precision != ZEUS_FP64) return ZEUS_EINVAL;
     return ZEUS_OK;
@@ -56,10 +56,10 @@ int validate(const zeus_problem* p) {
 
 Layout layout_for(const zeus_problem& p, const BfgsLaunch& L) {
     const size_t n = (size_t)p.n_starts, d = (size_t)p.dim;
-    const int G = lanes_for_dim(p.dim, p.threads_per_start);
-    size_t nparts = (size_t)pso_blocks(p, G);
+    size_t nparts = (size_t)pso_blocks(p, lanes_for_dim(p.dim));
     const size_t na = (size_t)argmin_blocks(p.n_starts);
     if (na > nparts) nparts = na;
+    const size_t qc = (size_t)L.q_cap;
     Layout lay;
     size_t off = 0;
     lay.ctrl = off;
@@ -76,8 +76,14 @@ Layout layout_for(const zeus_problem& p, const BfgsLaunch& L) {
     off += align256(n * sizeof(double));
     lay.gx = off;
     off += align256(d * sizeof(double));
-    lay.h = off;
-    if (L.h_global) off += align256(n * d * d * sizeof(double));
+    lay.q_start = off;
+    off += align256(qc * sizeof(int));
+    lay.q_k = off;
+    off += align256(qc * sizeof(int));
+    lay.q_feval = off;
+    off += align256(qc * sizeof(int));
+    lay.q_h = off;
+    off += align256(qc * d * d * sizeof(double));
     lay.total = off;
     return lay;
 }
@@ -95,6 +101,16 @@ T* at(void* ws, size_t off) {
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? ZEUS_OK : ZEUS_ECUDA; }
+
+Queue queue_for(void* ws, const Layout& lay, const BfgsLaunch& L) {
+    Queue q;
+    q.start = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + lay.q_start);
+    q.k = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + lay.q_k);
+    q.feval = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + lay.q_feval);
+    q.H = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + lay.q_h);
+    q.cap = L.q_cap;
+    return q;
+}
 
 // Best-of-swarm reduction over the final f, with the run's counters.
 int finish_with_argmin(const zeus_problem& p, void* ws, const Layout& lay, const double* f,
@@ -193,12 +209,11 @@ int zeus_solve(const zeus_problem* p, void* workspace, size_t workspace_bytes, d
     double* f = f_out ? f_out : at<double>(workspace, lay.f_tmp);
     cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
     if (e != cudaSuccess) return ZEUS_ECUDA;
-    const int G = lanes_for_dim(p->dim, p->threads_per_start);
-    e = launch_pso(*p, G, x_out, vv, px, pf, gx, ctrl, parts, result, st);
+    e = launch_pso(*p, lanes_for_dim(p->dim), x_out, vv, px, pf, gx, ctrl, parts, result, st);
     if (e != cudaSuccess) return ZEUS_ECUDA;
     const double* x0 = p->start_from_pbest ? px : x_out;
-    e = launch_bfgs(*p, L, x0, x_out, f, gnorm_out, status_out, iters_out,
-                    at<double>(workspace, lay.h), ctrl, st);
+    e = launch_bfgs(*p, L, x0, x_out, f, gnorm_out, status_out, iters_out, ctrl,
+                    queue_for(workspace, lay, L), st);
     if (e != cudaSuccess) return ZEUS_ECUDA;
     return finish_with_argmin(*p, workspace, lay, f, result, true, st);
 }
@@ -220,8 +235,8 @@ int zeus_solve_from(const zeus_problem* p, const double* x0, void* workspace,
     double* f = f_out ? f_out : at<double>(workspace, lay.f_tmp);
     cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
     if (e != cudaSuccess) return ZEUS_ECUDA;
-    e = launch_bfgs(*p, L, x0, x_out, f, gnorm_out, status_out, iters_out,
-                    at<double>(workspace, lay.h), ctrl, st);
+    e = launch_bfgs(*p, L, x0, x_out, f, gnorm_out, status_out, iters_out, ctrl,
+                    queue_for(workspace, lay, L), st);
     if (e != cudaSuccess) return ZEUS_ECUDA;
     return finish_with_argmin(*p, workspace, lay, f, result, false, st);
 }
@@ -243,8 +258,7 @@ int zeus_pso(const zeus_problem* p, void* workspace, size_t workspace_bytes, dou
     Ctrl* ctrl = at<Ctrl>(workspace, lay.ctrl);
     cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
     if (e != cudaSuccess) return ZEUS_ECUDA;
-    const int G = lanes_for_dim(p->dim, p->threads_per_start);
-    e = launch_pso(*p, G, x_out, v_out, px_out, pf_out, gx_out, ctrl,
+    e = launch_pso(*p, lanes_for_dim(p->dim), x_out, v_out, px_out, pf_out, gx_out, ctrl,
                    at<ArgPair>(workspace, lay.partials), result, st);
     return cuda_status(e);
 }
@@ -303,6 +317,12 @@ int zeus_uniform(uint64_t seed, uint64_t problem, uint64_t phase, int64_t n, int
                  double* out, void* stream) {
     if (n < 0 || dim < 1 || (n > 0 && !out)) return ZEUS_EINVAL;
     return cuda_status(launch_uniform(seed, problem, phase, n, dim, out, as_stream(stream)));
+}
+
+int zeus_math_eval(int32_t fn, int64_t n, const double* x, double* y0, double* y1, void* stream) {
+    if (fn < 0 || fn > 3 || n < 0) return ZEUS_EINVAL;
+    if (n > 0 && (!x || !y0 || ((fn == 0 || fn == 2) && !y1))) return ZEUS_EINVAL;
+    return cuda_status(launch_math(fn, n, x, y0, y1, as_stream(stream)));
 }
 
 // ---------------------------------------------------------------------------

@@ -104,12 +104,97 @@ __device__ __forceinline__ Dual<T> operator*(Dual<T> x, Dual<T> y) {
 template <class T>
 __device__ __forceinline__ Dual<T> operator*(T s, Dual<T> x) { return dmk(s * x.a, s * x.b); }
 
-// sin(pi x), cos(pi x) in the working precision
-__device__ __forceinline__ void sc_pi(double x, double* s, double* c) { sincospi(x, s, c); }
-__device__ __forceinline__ void sc_pi(float x, float* s, float* c) { sincospif(x, s, c); }
-__device__ __forceinline__ double c_pi(double x) { return cospi(x); }
-__device__ __forceinline__ float c_pi(float x) { return cospif(x); }
-__device__ __forceinline__ double xexp(double x) { return exp(x); }
+// ---------------------------------------------------------------------------
+// FP64 elementary functions of the objectives, written from published
+// methods (explicit fused multiply-adds, so the result does not depend on
+// compiler contraction):
+//  sin/cos(2 pi x): exact argument reduction r = x - rint(x),
+//    q = rint(4 r), s = r - q/4 (|s| <= 1/8, every step exact), Taylor
+//    series of sin(2 pi s) through s^17 and cos(2 pi s) through s^16 in
+//    Horner form in s^2, quarter-turn identities for q.  Coefficients:
+//    S_k = (-1)^k (2 pi)^(2k+1)/(2k+1)!, C_k = (-1)^k (2 pi)^(2k)/(2k)!.
+//  e^x: Cody & Waite reduction x = k ln2 + r, k = rint(x / ln2),
+//    ln2 = L1 + L2 with a 32-bit head L1 (k L1 exact), Taylor series of e^r
+//    through r^13 in Horner form, exact scaling by 2^k.
+// Cost: sincos 2 rint + 3 add/mul + 16 FMA + 2 mul; e^x 1 rint + 4 +
+// 13 FMA.  FP32 uses CUDA's sincospif / expf.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sincos2pi(double x, double* sp, double* cp) {
+    const double n = rint(x);
+    const double r = x - n;
+    const double qf = rint(4.0 * r);
+    const double s = r - 0.25 * qf;
+    const int q = ((int)qf) & 3;
+    const double z = s * s;
+    double ps = 0x1.aaec32af93359p-4, pc = 0x1.20c62c2f2d7f5p-2;
+    ps = fma(ps, z, -0x1.6fadb9f155744p-1);
+    pc = fma(pc, z, -0x1.b6e24f44b128fp+0);
+    ps = fma(ps, z, 0x1.e8f434d018d63p+1);
+    pc = fma(pc, z, 0x1.f9d38a3763cc3p+2);
+    ps = fma(ps, z, -0x1.e3074fde8871fp+3);
+    pc = fma(pc, z, -0x1.a6d1f2a204a8cp+4);
+    ps = fma(ps, z, 0x1.50783487ee782p+5);
+    pc = fma(pc, z, 0x1.e1f506891babbp+5);
+    ps = fma(ps, z, -0x1.32d2cce62bd86p+6);
+    pc = fma(pc, z, -0x1.55d3c7e3cbffap+6);
+    ps = fma(ps, z, 0x1.466bc6775aae2p+6);
+    pc = fma(pc, z, 0x1.03c1f081b5ac4p+6);
+    ps = fma(ps, z, -0x1.4abbce625be53p+5);
+    pc = fma(pc, z, -0x1.3bd3cc9be45dep+4);
+    ps = fma(ps, z, 0x1.921fb54442d18p+2);
+    pc = fma(pc, z, 1.0);
+    ps = ps * s;
+    double so, co;
+    if (q == 0) {
+        so = ps;
+        co = pc;
+    } else if (q == 1) {
+        so = pc;
+        co = -ps;
+    } else if (q == 2) {
+        so = -ps;
+        co = -pc;
+    } else {
+        so = -pc;
+        co = ps;
+    }
+    *sp = so;
+    *cp = co;
+}
+
+__device__ __forceinline__ double exp_cw(double x) {
+    if (isnan(x)) return x;
+    if (x > 709.78) return CUDART_INF;
+    if (x < -745.2) return 0.0;
+    const double k = rint(x * 0x1.71547652b82fep+0);
+    const double r = (x - k * 0x1.62e42fee00000p-1) - k * 0x1.a39ef35793c76p-33;
+    double p = 0x1.6124613a86d09p-33;  // 1/13!
+    p = fma(p, r, 0x1.1eed8eff8d898p-29);
+    p = fma(p, r, 0x1.ae64567f544e4p-26);
+    p = fma(p, r, 0x1.27e4fb7789f5cp-22);
+    p = fma(p, r, 0x1.71de3a556c734p-19);
+    p = fma(p, r, 0x1.a01a01a01a01ap-16);
+    p = fma(p, r, 0x1.a01a01a01a01ap-13);
+    p = fma(p, r, 0x1.6c16c16c16c17p-10);
+    p = fma(p, r, 0x1.1111111111111p-7);
+    p = fma(p, r, 0x1.5555555555555p-5);
+    p = fma(p, r, 0x1.5555555555555p-3);
+    p = fma(p, r, 0x1.0000000000000p-1);
+    p = fma(p, r, 1.0);
+    p = fma(p, r, 1.0);
+    return ldexp(p, (int)k);
+}
+
+// sin(2 pi x), cos(2 pi x) in the working precision
+__device__ __forceinline__ void sc_2pi(double x, double* s, double* c) { sincos2pi(x, s, c); }
+__device__ __forceinline__ void sc_2pi(float x, float* s, float* c) { sincospif(2.0f * x, s, c); }
+__device__ __forceinline__ double c_2pi(double x) {
+    double s, c;
+    sincos2pi(x, &s, &c);
+    return c;
+}
+__device__ __forceinline__ float c_2pi(float x) { return cospif(2.0f * x); }
+__device__ __forceinline__ double xexp(double x) { return exp_cw(x); }
 __device__ __forceinline__ float xexp(float x) { return expf(x); }
 __device__ __forceinline__ double xsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float xsqrt(float x) { return sqrtf(x); }
@@ -163,13 +248,13 @@ __device__ __forceinline__ Part<A> value_partial(const T* x, int d, int lane, in
         if (lane == 0) p.s0 = A(10) * A(d);
         for (int i = lane; i < d; i += G) {
             const T xi = x[i];
-            p.s0 += A(xi * xi - T(10) * c_pi(T(2) * xi));
+            p.s0 += A(xi * xi - T(10) * c_2pi(xi));
         }
     } else if (OBJ == ZEUS_OBJ_ACKLEY) {
         for (int i = lane; i < d; i += G) {
             const T xi = x[i];
             p.s0 += A(xi * xi);
-            p.s1 += A(c_pi(T(2) * xi));
+            p.s1 += A(c_2pi(xi));
         }
     } else if (OBJ == ZEUS_OBJ_GOLDSTEIN_PRICE) {
         if (lane == 0) {
@@ -231,14 +316,14 @@ __device__ __forceinline__ Dual<T> forward_pass(const T* x, int d, int i) {
             const T xj = x[j];
             if (j == i) {
                 T s, c;
-                sc_pi(T(2) * xj, &s, &c);
+                sc_2pi(xj, &s, &c);
                 // x^2 - 10 cos(2 pi x) on duals with tangent 1
                 const T tx2 = xj + xj;
                 const T tcos = -s * Consts<T>::two_pi();
                 val += xj * xj - T(10) * c;
                 tan += tx2 - T(10) * tcos;
             } else {
-                val += xj * xj - T(10) * c_pi(T(2) * xj);
+                val += xj * xj - T(10) * c_2pi(xj);
             }
         }
         return dmk(val, tan);
@@ -248,25 +333,26 @@ __device__ __forceinline__ Dual<T> forward_pass(const T* x, int d, int i) {
             const T xj = x[j];
             if (j == i) {
                 T s, c;
-                sc_pi(T(2) * xj, &s, &c);
+                sc_2pi(xj, &s, &c);
                 s1 += xj * xj;
                 t1 += xj + xj;
                 s2 += c;
                 t2 += -s * Consts<T>::two_pi();
             } else {
                 s1 += xj * xj;
-                s2 += c_pi(T(2) * xj);
+                s2 += c_2pi(xj);
             }
         }
-        const T invd = T(1) / T(d);
+        // dual division by the constant d: (a/d, (b d - a 0)/(d d))
+        const T dd = T(d);
         // u = s1/d, r = sqrt(u) (tangent 0 at u = 0), e1 = exp(-0.2 r)
-        const T u = s1 * invd, ut = t1 * invd;
+        const T u = s1 / dd, ut = (t1 * dd) / (dd * dd);
         const T r = xsqrt(u);
         const T rt = r > T(0) ? ut / (T(2) * r) : T(0);
         const T e1 = xexp(T(-0.2) * r);
         const T e1t = e1 * (T(-0.2) * rt);
-        const T e2 = xexp(s2 * invd);
-        const T e2t = e2 * (t2 * invd);
+        const T e2 = xexp(s2 / dd);
+        const T e2t = e2 * ((t2 * dd) / (dd * dd));
         const T val = (T(-20) * e1 - e2) + (T(20) + Consts<T>::e());
         const T tan = T(-20) * e1t - e2t;
         return dmk(val, tan);
@@ -295,100 +381,84 @@ __device__ __forceinline__ Dual<T> forward_pass(const T* x, int d, int i) {
     }
 }
 
-// Reverse-mode adjoint: lanes split coordinates, partial sums reduced over
-// the group.  Writes g[j] for the lane's own j (j = lane, lane+G, ...) and
-// returns f (identical on every lane of the group).
-template <int OBJ, class T, class GRP>
-__device__ __forceinline__ T adjoint(const T* x, int d, T* g, const GRP& grp) {
-    const int lane = grp.lane, G = grp.G;
-    if (OBJ == ZEUS_OBJ_ROSENBROCK) {
-        T s = T(0);
-        for (int j = lane; j < d; j += G) {
-            const T xj = x[j];
-            T gj = T(0);
-            if (j + 1 < d) {  // term j: (1 - x_j)^2 + 100 (x_{j+1} - x_j^2)^2
-                const T a = T(1) - xj;
-                const T b = x[j + 1] - xj * xj;
-                s += a * a + T(100) * (b * b);
-                gj += T(-2) * a - T(400) * xj * b;
-            }
-            if (j > 0) {  // term j-1 through x_j
-                const T xp = x[j - 1];
-                const T b = xj - xp * xp;
-                gj += T(200) * b;
-            }
-            g[j] = gj;
-        }
-        return grp.sum(s);
-    } else if (OBJ == ZEUS_OBJ_RASTRIGIN) {
-        T s = lane == 0 ? T(10) * T(d) : T(0);
-        for (int j = lane; j < d; j += G) {
-            const T xj = x[j];
-            T sn, c;
-            sc_pi(T(2) * xj, &sn, &c);
-            s += xj * xj - T(10) * c;
-            g[j] = (xj + xj) + T(10) * Consts<T>::two_pi() * sn;
-        }
-        return grp.sum(s);
-    } else if (OBJ == ZEUS_OBJ_ACKLEY) {
+// Reverse-mode adjoint in two stages: adjoint_prep forms, on one thread,
+// the quantities every component shares (for Ackley the adjoints of its two
+// sums, which are formed in index order); adjoint_component then gives
+// df/dx_i from x_i (and its neighbours) alone, so components can run on
+// separate threads.  One forward and one reverse sweep in total, O(d).
+struct AdjShared {
+    double c1, c2;
+};
+
+template <int OBJ, class T>
+__device__ __forceinline__ AdjShared adjoint_prep(const T* x, int d) {
+    AdjShared a;
+    a.c1 = 0.0;
+    a.c2 = 0.0;
+    if (OBJ == ZEUS_OBJ_ACKLEY) {
         T s1 = T(0), s2 = T(0);
-        for (int j = lane; j < d; j += G) {
+        for (int j = 0; j < d; ++j) {
             const T xj = x[j];
-            s1 += xj * xj;
-            s2 += c_pi(T(2) * xj);
+            s1 = s1 + xj * xj;
+            s2 = s2 + c_2pi(xj);
         }
-        s1 = grp.sum(s1);
-        s2 = grp.sum(s2);
-        const T invd = T(1) / T(d);
-        const T r = xsqrt(s1 * invd);
+        const T dd = T(d);
+        const T r = xsqrt(s1 / dd);
         const T e1 = xexp(T(-0.2) * r);
-        const T e2 = xexp(s2 * invd);
-        // adjoints of s1 and s2
-        const T a1 = r > T(0) ? (T(-20) * e1) * (T(-0.2) / (T(2) * r)) * invd : T(0);
-        const T a2 = -e2 * invd;
-        for (int j = lane; j < d; j += G) {
-            const T xj = x[j];
-            T sn, c;
-            sc_pi(T(2) * xj, &sn, &c);
-            g[j] = a1 * (xj + xj) - a2 * Consts<T>::two_pi() * sn;
+        const T e2 = xexp(s2 / dd);
+        // f = -20 e1 - e2 + 20 + e; adjoints of s1 and s2
+        a.c1 = r > T(0) ? (double)(((T(-20) * e1) * (T(-0.2) / (T(2) * r))) / dd) : 0.0;
+        a.c2 = (double)(-e2 / dd);
+    }
+    return a;
+}
+
+template <int OBJ, class T>
+__device__ __forceinline__ T adjoint_component(const T* x, int d, int i, const AdjShared& sh) {
+    if (OBJ == ZEUS_OBJ_ROSENBROCK) {
+        const T xi = x[i];
+        T gi = T(0);
+        if (i + 1 < d) {  // term i: (1 - x_i)^2 + 100 (x_{i+1} - x_i^2)^2
+            const T a = T(1) - xi;
+            const T b = x[i + 1] - xi * xi;
+            gi = gi + (T(-2) * a - T(400) * xi * b);
         }
-        return (T(-20) * e1 - e2) + (T(20) + Consts<T>::e());
+        if (i > 0) {  // term i-1 through x_i
+            const T xp = x[i - 1];
+            gi = gi + T(200) * (xi - xp * xp);
+        }
+        return gi;
+    } else if (OBJ == ZEUS_OBJ_RASTRIGIN) {
+        const T xi = x[i];
+        T sn, c;
+        sc_2pi(xi, &sn, &c);
+        return (xi + xi) + T(10) * Consts<T>::two_pi() * sn;
+    } else if (OBJ == ZEUS_OBJ_ACKLEY) {
+        const T xi = x[i];
+        T sn, c;
+        sc_2pi(xi, &sn, &c);
+        return T(sh.c1) * (xi + xi) - T(sh.c2) * Consts<T>::two_pi() * sn;
     } else if (OBJ == ZEUS_OBJ_GOLDSTEIN_PRICE) {
-        T f = T(0);
-        if (lane == 0) {
-            const T x1 = x[0], x2 = x[1];
-            const T t = (x1 + x2) + T(1);
-            const T pa = T(19) - T(14) * x1 + T(3) * (x1 * x1) - T(14) * x2 + T(6) * (x1 * x2) +
-                         T(3) * (x2 * x2);
-            const T a = T(1) + (t * t) * pa;
-            const T u = T(2) * x1 - T(3) * x2;
-            const T pb = T(18) - T(32) * x1 + T(12) * (x1 * x1) + T(48) * x2 - T(36) * (x1 * x2) +
-                         T(27) * (x2 * x2);
-            const T b = T(30) + (u * u) * pb;
-            f = a * b;
-            // reverse sweep: f = a b
-            const T da = b, db = a;
-            const T dt = da * (T(2) * t * pa), dpa = da * (t * t);
-            const T du = db * (T(2) * u * pb), dpb = db * (u * u);
-            const T g1 = dt + dpa * (T(-14) + T(6) * x1 + T(6) * x2) + du * T(2) +
-                         dpb * (T(-32) + T(24) * x1 - T(36) * x2);
-            const T g2 = dt + dpa * (T(-14) + T(6) * x1 + T(6) * x2) + du * T(-3) +
-                         dpb * (T(48) - T(36) * x1 + T(54) * x2);
-            // lane 0 writes both coordinates; callers sync the group
-            // before reading g
-            g[0] = g1;
-            g[1] = g2;
-        }
-        return grp.bcast(f);
+        const T x1 = x[0], x2 = x[1];
+        const T t = (x1 + x2) + T(1);
+        const T pa = T(19) - T(14) * x1 + T(3) * (x1 * x1) - T(14) * x2 + T(6) * (x1 * x2) +
+                     T(3) * (x2 * x2);
+        const T a = T(1) + (t * t) * pa;
+        const T u = T(2) * x1 - T(3) * x2;
+        const T pb = T(18) - T(32) * x1 + T(12) * (x1 * x1) + T(48) * x2 - T(36) * (x1 * x2) +
+                     T(27) * (x2 * x2);
+        const T b = T(30) + (u * u) * pb;
+        // reverse sweep of f = a b
+        const T dt = b * (T(2) * t * pa), dpa = b * (t * t);
+        const T du = a * (T(2) * u * pb), dpb = a * (u * u);
+        if (i == 0)
+            return dt + dpa * (T(-14) + T(6) * x1 + T(6) * x2) + du * T(2) +
+                   dpb * (T(-32) + T(24) * x1 - T(36) * x2);
+        return dt + dpa * (T(-14) + T(6) * x1 + T(6) * x2) + du * T(-3) +
+               dpb * (T(48) - T(36) * x1 + T(54) * x2);
     } else {
-        T s = T(0);
-        for (int j = lane; j < d; j += G) {
-            const T xj = x[j];
-            const T c = T(0.5) * T(j + 1);
-            s += c * (xj * xj);
-            g[j] = c * (xj + xj);
-        }
-        return grp.sum(s);
+        const T xi = x[i];
+        return (T(0.5) * T(i + 1)) * (xi + xi);
     }
 }
 

@@ -17,13 +17,15 @@ struct Ctrl {
     unsigned int blocks_done;        // last-block counter of the fused grid reductions
     int stop;                        // shared stop flag (Alg. 10)
     int error;                       // device error word
-    int pad0;
+    unsigned int q_count;            // starts handed from the narrow to the wide kernel
+    unsigned int q_head;             // next queue item the wide kernel takes
+    unsigned int pad0;
     unsigned long long n_conv;       // starts that converged
     unsigned long long total_iters;  // sum of completed BFGS iterations
     unsigned long long total_feval;  // sum of line-search evaluations
     double gbest_f;                  // PSO global best value
     long long gbest_idx;             // and its particle
-    unsigned long long pad1[25];
+    unsigned long long pad1[24];
 };
 static_assert(sizeof(Ctrl) == 256, "control block is one 256-byte segment");
 
@@ -39,21 +41,39 @@ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Workspace carve-up (offsets in bytes from the workspace base).
 struct Layout {
-    size_t ctrl, partials, f_tmp, v, px, pf, gx, h, total;
+    size_t ctrl, partials, f_tmp, v, px, pf, gx, q_start, q_k, q_feval, q_h, total;
 };
+
+// Hand-over queue from the narrow to the wide BFGS kernel (workspace).
+struct Queue {
+    int* start;   // [cap] start index
+    int* k;       // [cap] iteration at hand-over
+    int* feval;   // [cap] line-search evaluations so far
+    double* H;    // [cap][d*d] inverse-Hessian approximation
+    int cap;
+};
+
+constexpr int kNarrowThreads = 128;
+constexpr int kWideThreads = 128;
 
 // Kernel-side configuration of a BFGS launch.
 struct BfgsLaunch {
-    int G;          // lanes per start
-    int S;          // starts per block
-    int stride;     // words of shared memory per start
-    size_t smem;    // dynamic shared memory per block (bytes)
-    int blocks;     // grid size
-    bool h_global;  // H kept in the workspace instead of shared memory
+    bool narrow;          // run the narrow (one lane per start) kernel first
+    int stride;           // doubles of shared memory per start in the narrow kernel
+    int narrow_threads;   // its block size
+    size_t narrow_smem;   // its dynamic shared memory
+    int narrow_blocks;
+    int W;                // line-search trials evaluated at once by the wide kernel
+    size_t wide_smem;     // its dynamic shared memory
+    int wide_blocks;      // persistent grid of the wide kernel
+    int budget;           // narrow-kernel work budget (iterations + evaluations), 0 = none
+    int q_cap;            // hand-over queue capacity
 };
 
 // ---- launchers (defined in the kernel translation units) ----
-int lanes_for_dim(int d, int requested);
+// lanes per particle of the PSO and objective kernels: one lane (sums in
+// index order) up to d = 64, a warp above
+inline int lanes_for_dim(int d) { return d <= 64 ? 1 : 32; }
 
 cudaError_t launch_pso(const zeus_problem& p, int G, double* x, double* v, double* px, double* pf,
                        double* gx, Ctrl* ctrl, ArgPair* partials, zeus_result* res,
@@ -63,7 +83,7 @@ int pso_blocks(const zeus_problem& p, int G);
 int plan_bfgs(const zeus_problem& p, BfgsLaunch* L);
 cudaError_t launch_bfgs(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
                         double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
-                        int32_t* iters_out, double* h_ws, Ctrl* ctrl, cudaStream_t st);
+                        int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st);
 
 cudaError_t launch_argmin(const double* f, long long n, Ctrl* ctrl, ArgPair* partials,
                           zeus_result* res, int mode, cudaStream_t st);
@@ -73,6 +93,9 @@ cudaError_t launch_objective(int obj, int d, long long n, const double* x, doubl
                              int grad_mode, cudaStream_t st);
 cudaError_t launch_objective_f32(int obj, int d, long long n, const float* x, float* f, float* g,
                                  int grad_mode, cudaStream_t st);
+
+cudaError_t launch_math(int fn, long long n, const double* x, double* y0, double* y1,
+                        cudaStream_t st);
 
 cudaError_t launch_uniform(uint64_t seed, uint64_t problem, uint64_t phase, long long n, int d,
                            double* out, cudaStream_t st);

@@ -28,7 +28,15 @@ __global__ void __launch_bounds__(kObjThreads)
             }
             fv = grp.bcast(f0);
         } else {
-            fv = adjoint<OBJ, T>(xi, d, gi, grp);
+            AdjShared a;
+            if (grp.lane == 0) a = adjoint_prep<OBJ, T>(xi, d);
+            a.c1 = grp.bcast(a.c1);
+            a.c2 = grp.bcast(a.c2);
+            for (int k = grp.lane; k < d; k += G) gi[k] = adjoint_component<OBJ, T>(xi, d, k, a);
+            Part<double> q = value_partial<OBJ, T, double>(xi, d, grp.lane, G);
+            q.s0 = grp.sum(q.s0);
+            if (OBJ == ZEUS_OBJ_ACKLEY) q.s1 = grp.sum(q.s1);
+            fv = T(value_finish<OBJ, double>(q, d));
         }
     } else {
         Part<double> q = value_partial<OBJ, T, double>(xi, d, grp.lane, G);
@@ -43,7 +51,7 @@ template <class T>
 static cudaError_t objective_go(int obj, int d, long long n, const T* x, T* f, T* g, int grad,
                                 cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    const int G = lanes_for_dim(d, 0);
+    const int G = lanes_for_dim(d);
     const long long threads = n * G;
     const unsigned blocks = (unsigned)((threads + kObjThreads - 1) / kObjThreads);
 #define ZEUS_OBJ_CASE(O)                                                                    \
@@ -64,6 +72,32 @@ static cudaError_t objective_go(int obj, int d, long long n, const T* x, T* f, T
             ZEUS_OBJ_CASE(ZEUS_OBJ_QUADRATIC)
     }
 #undef ZEUS_OBJ_CASE
+    return cudaGetLastError();
+}
+
+__global__ void math_kernel(const int fn, const long long n, const double* __restrict__ x,
+                            double* __restrict__ y0, double* __restrict__ y1) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    double a = 0.0, b = 0.0;
+    if (fn == 0) {
+        sincos2pi(v, &a, &b);
+    } else if (fn == 1) {
+        a = exp_cw(v);
+    } else if (fn == 2) {
+        sincospi(2.0 * v, &a, &b);
+    } else {
+        a = exp(v);
+    }
+    y0[i] = a;
+    if (y1 && (fn == 0 || fn == 2)) y1[i] = b;
+}
+
+cudaError_t launch_math(int fn, long long n, const double* x, double* y0, double* y1,
+                        cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    math_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(fn, n, x, y0, y1);
     return cudaGetLastError();
 }
 

@@ -74,7 +74,7 @@ def test_defaults(z):
     dict(n_starts=2**31), dict(pso_iters=-1), dict(bfgs_max_iters=-1), dict(ls_max_iters=0),
     dict(required_converged=-2), dict(grad_tol=-1.0), dict(grad_tol=float("nan")), dict(w=float("inf")),
     dict(armijo_c=0.0), dict(armijo_c=1.0), dict(backtrack=1.0), dict(backtrack=0.0), dict(grad_mode=2),
-    dict(start_from_pbest=2), dict(threads_per_start=3), dict(threads_per_start=64), dict(precision=5),
+    dict(start_from_pbest=2), dict(threads_per_start=3), dict(threads_per_start=32), dict(precision=5),
 ])
 def test_validation_rejects(z, kw):
     assert z.zeus_validate(z.Problem(**kw)) == z._capi.ZEUS_EINVAL
@@ -83,7 +83,7 @@ def test_validation_rejects(z, kw):
 @pytest.mark.parametrize("kw", [
     dict(objective="rastrigin", dim=1), dict(objective="quadratic", dim=1), dict(objective="ackley", dim=4096),
     dict(n_starts=1), dict(pso_iters=0), dict(bfgs_max_iters=0), dict(grad_mode="adjoint"),
-    dict(threads_per_start=32), dict(start_from_pbest=1), dict(required_converged=3), dict(target_f=1e-6),
+    dict(threads_per_start=128), dict(threads_per_start=1), dict(start_from_pbest=1), dict(required_converged=3), dict(target_f=1e-6),
 ])
 def test_validation_accepts(z, kw):
     assert z.zeus_validate(z.Problem(**kw)) == 0
