@@ -70,3 +70,12 @@ def assert_bitwise(gpu: dict, ora: dict):
 
 def to_np(out: dict) -> dict:
     return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
+
+
+def clopper_pearson(k: int, n: int, level: float = 0.95):
+    """Exact two-sided binomial confidence interval for k successes in n."""
+    from scipy.stats import beta
+    a = (1.0 - level) / 2.0
+    lo = 0.0 if k == 0 else float(beta.ppf(a, k, n - k + 1))
+    hi = 1.0 if k == n else float(beta.ppf(1.0 - a, k + 1, n - k))
+    return lo, hi
