@@ -211,6 +211,37 @@ int zeus_uniform(uint64_t seed, uint64_t problem, uint64_t phase,
 int zeus_math_eval(int32_t fn, int64_t n, const double *x, double *y0, double *y1,
                    void *stream);
 
+/* ---- No-allocation variant (the paper has no counterpart) ----
+ *
+ * zeus_solve_from without a workspace argument, for callers that cannot
+ * call cudaMalloc: code running while a stream is being captured into a CUDA
+ * graph or under a framework's own allocator, plugins and embedded callers
+ * that are handed device buffers but no allocation rights.  The library
+ * allocates nothing in this call either: its scratch (control block,
+ * reduction partials, hand-over queue) is one static device array of
+ * ZEUS_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.
+ *   - Limit: when the automatic mode runs one lane per start and hands
+ *     long runs to the block-per-start kernel (dim <= 16 with
+ *     threads_per_start 0), every start must fit the queue:
+ *     n_starts * (12 + 8 * dim * dim) bytes within the array (about 20000
+ *     starts at dim 10); larger problems get ZEUS_EWORKSPACE.  Otherwise
+ *     zeus_validate's limits apply.
+ *   - f_out is required (device double [N]); the other arguments are those
+ *     of zeus_solve_from.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - All calls share the one array and it keeps the previous call's
+ *     contents (the call clears what must start at zero): calls that
+ *     overlap on the GPU, on any streams, race and give undefined results.
+ */
+#define ZEUS_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+int zeus_solve_from_noalloc(const zeus_problem *p, const double *x0, double *x_out,
+                            double *f_out, double *gnorm_out, int32_t *status_out,
+                            int32_t *iters_out, zeus_result *result, void *stream);
+
 /* ---- Host-buffer interface (owns device buffers; for callers without
  * CUDA memory of their own) ---- */
 typedef struct zeus_context zeus_context;

@@ -21,7 +21,7 @@ from ._capi import (GRAD_MODES, OBJECTIVES, PRECISIONS, RUN_STATUS, ZeusError, c
                     library_path, strerror, zeus_problem, zeus_result)
 
 __all__ = [
-    "Problem", "ZeusError", "zeus_solve", "zeus_solve_from", "zeus_pso", "zeus_objective_eval",
+    "Problem", "ZeusError", "zeus_solve", "zeus_solve_from", "zeus_solve_from_noalloc", "zeus_pso", "zeus_objective_eval",
     "zeus_objective_eval_f32", "zeus_argmin", "zeus_argmin_workspace_size", "zeus_uniform",
     "zeus_workspace_size", "zeus_validate", "zeus_default_problem", "zeus_strerror",
     "zeus_abi_version", "zeus_math_eval", "Context", "solve", "solve_from", "pso", "objective", "ObjectiveFn",
@@ -166,6 +166,19 @@ def zeus_solve_from(problem, x0, workspace, x_out, f_out=None, gnorm_out=None, s
         _ptr(gnorm_out, torch.float64, n, "gnorm_out"),
         _ptr(status_out, torch.int32, n, "status_out"), _ptr(iters_out, torch.int32, n, "iters_out"),
         _ptr(result, torch.uint8, RESULT_BYTES, "result"), _stream(stream)), "zeus_solve_from")
+
+
+def zeus_solve_from_noalloc(problem, x0, x_out, f_out, gnorm_out=None, status_out=None,
+                            iters_out=None, result=None, stream=None) -> None:
+    """zeus_solve_from without a workspace: for callers that cannot allocate
+    device memory (the library uses one static device array instead)."""
+    pc = _prob(problem)
+    n, d = pc.n_starts, pc.dim
+    check(lib().zeus_solve_from_noalloc(
+        C.byref(pc), _ptr(x0, torch.float64, n * d, "x0"), _ptr(x_out, torch.float64, n * d, "x_out"),
+        _ptr(f_out, torch.float64, n, "f_out"), _ptr(gnorm_out, torch.float64, n, "gnorm_out"),
+        _ptr(status_out, torch.int32, n, "status_out"), _ptr(iters_out, torch.int32, n, "iters_out"),
+        _ptr(result, torch.uint8, RESULT_BYTES, "result"), _stream(stream)), "zeus_solve_from_noalloc")
 
 
 def zeus_pso(problem, workspace, x_out, v_out, px_out, pf_out, gx_out, result=None,

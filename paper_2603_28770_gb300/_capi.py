@@ -84,6 +84,8 @@ SIGNATURES = {
     "zeus_uniform": (C.c_int, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int32, _VP,
                                _VP]),
     "zeus_math_eval": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, _VP, _VP]),
+    "zeus_solve_from_noalloc": (C.c_int, [C.POINTER(zeus_problem), _VP, _VP, _VP, _VP, _VP,
+                                          _VP, _VP, _VP]),
     "zeus_context_create": (C.c_int, [C.POINTER(_VP)]),
     "zeus_context_destroy": (C.c_int, [_VP]),
     "zeus_solve_host": (C.c_int, [_VP, C.POINTER(zeus_problem), _VP, _VP, _VP, _VP, _VP, _VP,

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libzeus.so")
 
-SOURCES = ["zeus_capi.cu", "zeus_pso.cu", "zeus_bfgs.cu", "zeus_objective.cu"]
+SOURCES = ["zeus_capi.cu", "zeus_pso.cu", "zeus_bfgs.cu", "zeus_objective.cu", "zeus_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
