@@ -214,9 +214,10 @@ int zeus_math_eval(int32_t fn, int64_t n, const double *x, double *y0, double *y
 /* ---- No-allocation variant (the paper has no counterpart) ----
  *
  * zeus_solve_from without a workspace argument, for callers that cannot
- * call cudaMalloc: code running while a stream is being captured into a CUDA
- * graph or under a framework's own allocator, plugins and embedded callers
- * that are handed device buffers but no allocation rights.  The library
+ * call cudaMalloc: code that must stay inside a framework's own caching
+ * allocator, plugins and embedded callers that are handed device buffers
+ * but no allocation rights, and code that must not pay the device-wide
+ * synchronisation that cudaMalloc and cudaFree can imply.  The library
  * allocates nothing in this call either: its scratch (control block,
  * reduction partials, hand-over queue) is one static device array of
  * ZEUS_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until

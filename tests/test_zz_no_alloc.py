@@ -1,7 +1,7 @@
 """zeus_solve_from_noalloc: BFGS from given starts for callers that cannot
-allocate device memory (code running during CUDA graph capture or under a
-framework's own allocator, plugins handed buffers but no allocation
-rights).  It uses one static device array as scratch instead of a
+allocate device memory (code that must stay inside a framework's own
+caching allocator, plugins handed device buffers but no allocation rights,
+code that must not pay the synchronisation cudaMalloc/cudaFree can imply).  It uses one static device array as scratch instead of a
 caller-provided workspace; its results must equal zeus_solve_from's.
 
 This file is collected last so that a run stopping at the first failure
