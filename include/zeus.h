@@ -206,6 +206,8 @@ int zeus_uniform(uint64_t seed, uint64_t problem, uint64_t phase,
  *   fn 1: y0 = e^x                             (the library's own method)
  *   fn 2: y0, y1 = CUDA sincospi(2x)           (CUDA math library)
  *   fn 3: y0 = CUDA exp(x)                     (CUDA math library)
+ *   fn 4: y0 = cos(2 pi x) by the cosine-only evaluation the objectives
+ *         use (bit for bit the y1 of fn 0)
  * x, y0: device double [n]; y1: device double [n] for fn 0 and 2, else
  * ignored (may be NULL). */
 int zeus_math_eval(int32_t fn, int64_t n, const double *x, double *y0, double *y1,

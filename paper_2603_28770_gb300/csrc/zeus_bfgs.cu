@@ -268,9 +268,10 @@ __global__ void __launch_bounds__(kNarrowThreads)
         }
         // curvature pair
         double sy = 0.0, ss = 0.0, yy = 0.0;
-        for (int j = 0; j < d; ++j) {
+        for (int j = 0; j < d; ++j) {  // s into sv, y over g (g is not needed again)
             const double sj = xn[j] - x[j], yj = gn[j] - g[j];
             sv[j] = sj;
+            g[j] = yj;
             sy = sy + yj * sj;
             ss = ss + sj * sj;
             yy = yy + yj * yj;
@@ -280,11 +281,11 @@ __global__ void __launch_bounds__(kNarrowThreads)
             for (int r = 0; r < d; ++r) {  // Hy into p (the direction is spent)
                 const double* Hr = H + r * d;
                 double a = 0.0;
-                for (int c = 0; c < d; ++c) a = a + Hr[c] * (gn[c] - g[c]);
+                for (int c = 0; c < d; ++c) a = a + Hr[c] * g[c];
                 pv[r] = a;
             }
             double yhy = 0.0;
-            for (int r = 0; r < d; ++r) yhy = yhy + (gn[r] - g[r]) * pv[r];
+            for (int r = 0; r < d; ++r) yhy = yhy + g[r] * pv[r];
             const double b2 = rho * rho * yhy + rho;
             for (int r = 0; r < d; ++r) {
                 const double sr = sv[r], hr = pv[r];
@@ -355,7 +356,12 @@ __global__ void __launch_bounds__(kWideThreads)
                      Ctrl* __restrict__ ctrl, const Queue q, const int all_starts) {
     extern __shared__ double smem[];
     __shared__ WideShared sh;
-    const int tid = threadIdx.x, T = blockDim.x;
+    const int T = blockDim.x;
+    // Roles rotate with the block index so that the thread doing the serial
+    // work (ordered sums, tests) sits in a different warp, hence on a
+    // different SM sub-partition, in each of the blocks sharing an SM.
+    const int lead = (32 * (int)blockIdx.x) % T;
+    const int tid = (threadIdx.x + T - lead) % T;
     const int d = p.dim;
     double* H = smem;
     double* x = H + (size_t)d * d;
@@ -522,9 +528,10 @@ __global__ void __launch_bounds__(kWideThreads)
             __syncthreads();
             fn = sh.red[2];
             // ---- curvature pair
-            for (int j = tid; j < d; j += T) {
+            for (int j = tid; j < d; j += T) {  // s into sv, y over g
                 const double sj = xn[j] - x[j], yj = gn[j] - g[j];
                 sv[j] = sj;
+                g[j] = yj;
                 sc0[j] = yj * sj;
                 sc1[j] = sj * sj;
                 sc2[j] = yj * yj;
@@ -539,9 +546,9 @@ __global__ void __launch_bounds__(kWideThreads)
                 for (int r = tid; r < d; r += T) {  // Hy into p (the direction is spent)
                     const double* Hr = H + r * d;
                     double a = 0.0;
-                    for (int c = 0; c < d; ++c) a = a + Hr[c] * (gn[c] - g[c]);
+                    for (int c = 0; c < d; ++c) a = a + Hr[c] * g[c];
                     pv[r] = a;
-                    sc0[r] = (gn[r] - g[r]) * a;
+                    sc0[r] = g[r] * a;
                 }
                 __syncthreads();
                 if (tid == 0) sh.red[3] = ordered_sum(sc0, d, 0.0);

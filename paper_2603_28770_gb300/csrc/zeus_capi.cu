@@ -320,7 +320,7 @@ int zeus_uniform(uint64_t seed, uint64_t problem, uint64_t phase, int64_t n, int
 }
 
 int zeus_math_eval(int32_t fn, int64_t n, const double* x, double* y0, double* y1, void* stream) {
-    if (fn < 0 || fn > 3 || n < 0) return ZEUS_EINVAL;
+    if (fn < 0 || fn > 4 || n < 0) return ZEUS_EINVAL;
     if (n > 0 && (!x || !y0 || ((fn == 0 || fn == 2) && !y1))) return ZEUS_EINVAL;
     return cuda_status(launch_math(fn, n, x, y0, y1, as_stream(stream)));
 }

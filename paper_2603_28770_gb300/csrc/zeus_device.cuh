@@ -185,14 +185,36 @@ __device__ __forceinline__ double exp_cw(double x) {
     return ldexp(p, (int)k);
 }
 
+// cos(2 pi x) alone, bit for bit the cosine of sincos2pi: the quadrant
+// picks per lane which of the two series (sin for odd quarter turns, cos for
+// even) the single Horner chain evaluates, so SIMT lanes with different
+// quadrants still run one chain (9 FMA instead of 16).
+__device__ __forceinline__ double cos2pi(double x) {
+    const double n = rint(x);
+    const double r = x - n;
+    const double qf = rint(4.0 * r);
+    const double s = r - 0.25 * qf;
+    const int q = ((int)qf) & 3;
+    const bool odd = (q & 1) != 0;
+    const double z = s * s;
+    double v = odd ? 0x1.aaec32af93359p-4 : 0x1.20c62c2f2d7f5p-2;
+    v = fma(v, z, odd ? -0x1.6fadb9f155744p-1 : -0x1.b6e24f44b128fp+0);
+    v = fma(v, z, odd ? 0x1.e8f434d018d63p+1 : 0x1.f9d38a3763cc3p+2);
+    v = fma(v, z, odd ? -0x1.e3074fde8871fp+3 : -0x1.a6d1f2a204a8cp+4);
+    v = fma(v, z, odd ? 0x1.50783487ee782p+5 : 0x1.e1f506891babbp+5);
+    v = fma(v, z, odd ? -0x1.32d2cce62bd86p+6 : -0x1.55d3c7e3cbffap+6);
+    v = fma(v, z, odd ? 0x1.466bc6775aae2p+6 : 0x1.03c1f081b5ac4p+6);
+    v = fma(v, z, odd ? -0x1.4abbce625be53p+5 : -0x1.3bd3cc9be45dep+4);
+    v = fma(v, z, odd ? 0x1.921fb54442d18p+2 : 1.0);
+    const double ps = v * s;
+    const double w = odd ? ps : v;  // q even: cos series; q odd: sin series times s
+    return (q == 0 || q == 3) ? w : -w;
+}
+
 // sin(2 pi x), cos(2 pi x) in the working precision
 __device__ __forceinline__ void sc_2pi(double x, double* s, double* c) { sincos2pi(x, s, c); }
 __device__ __forceinline__ void sc_2pi(float x, float* s, float* c) { sincospif(2.0f * x, s, c); }
-__device__ __forceinline__ double c_2pi(double x) {
-    double s, c;
-    sincos2pi(x, &s, &c);
-    return c;
-}
+__device__ __forceinline__ double c_2pi(double x) { return cos2pi(x); }
 __device__ __forceinline__ float c_2pi(float x) { return cospif(2.0f * x); }
 __device__ __forceinline__ double xexp(double x) { return exp_cw(x); }
 __device__ __forceinline__ float xexp(float x) { return expf(x); }

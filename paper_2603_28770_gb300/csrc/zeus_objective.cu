@@ -87,8 +87,10 @@ __global__ void math_kernel(const int fn, const long long n, const double* __res
         a = exp_cw(v);
     } else if (fn == 2) {
         sincospi(2.0 * v, &a, &b);
-    } else {
+    } else if (fn == 3) {
         a = exp(v);
+    } else {
+        a = cos2pi(v);
     }
     y0[i] = a;
     if (y1 && (fn == 0 || fn == 2)) y1[i] = b;

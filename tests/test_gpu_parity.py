@@ -304,6 +304,9 @@ def test_elementary_functions(z, ora):
     cs, cc = torch.empty_like(xt), torch.empty_like(xt)
     z.zeus_math_eval(2, xt, cs, cc)  # CUDA's sincospi(2x) for comparison
     cs, cc = cs.cpu().numpy(), cc.cpu().numpy()
+    co = torch.empty_like(xt)
+    z.zeus_math_eval(4, xt, co)  # the cosine-only evaluation used by the objectives
+    assert np.array_equal(co.cpu().numpy(), c)
     for i, v in enumerate(x):
         os_, oc = ora.sincos2pi(v)
         assert s[i] == os_ and c[i] == oc  # same method, same bits as the oracle
