@@ -45,7 +45,10 @@ def _args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--grad-mode", default="forward", choices=["forward", "adjoint"])
     ap.add_argument("--lanes", type=int, default=0, help="threads per start (0 = automatic)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_guarded"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--form-seeds", type=int, default=5)
     return ap.parse_args()
 
 
@@ -67,7 +70,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -148,7 +151,8 @@ def run_zeus(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    fields = workloads.workload(a.workload, grad_mode=a.grad_mode, threads_per_start=a.lanes)
+    fields = workloads.workload(a.workload, grad_mode=a.grad_mode, threads_per_start=a.lanes,
+                                precision=a.precision)
     # weak scaling: every rank solves its own independent multistart problem
     fields["seed"] = fields["seed"] + rank
     p = z.Problem(**{k: v for k, v in fields.items() if k in z.Problem.__dataclass_fields__})
@@ -260,7 +264,7 @@ def run_zeus(a):
         "data": "synthetic (seeded Philox draws of the method itself; no dataset)",
         "config": {"workload": a.workload, "objective": p.objective, "dim": d, "n_starts": n,
                    "pso_iters": p.pso_iters, "bfgs_max_iters": p.bfgs_max_iters,
-                   "grad_mode": a.grad_mode, "precision": "fp64",
+                   "grad_mode": a.grad_mode, "precision": a.precision,
                    "start_iters_per_step": iters_per_step, "feval_per_step": feval_per_step,
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
@@ -273,12 +277,64 @@ def run_zeus(a):
         "wall_s_timed": round(t_wall, 3),
         "clocks": clk.summary(),
     }
+    if rank == 0 and not a.no_forms:
+        out["forms"] = run_forms(z, dev, stream, seeds=a.form_seeds)
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(fields, budget_s=12.0)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+FORM_WORKLOADS = ("rosenbrock2d_n128", "rastrigin5d_n16384", "rastrigin10d_n16384")
+
+
+def run_forms(z, dev, stream, seeds=5):
+    """Time to 1e-6 of the global minimum (f* = 0) of the whole path (PSO +
+    BFGS + reduction) with the stop-on-target flag, per workload and form,
+    over seeds: median time, success rate (best f <= 1e-6), and the
+    start-iterations the run made.  Forms: the plain FP64 method
+    (forward-mode duals), the FP64 adjoint, and the FP32 form with FP64
+    guards (forward and adjoint).  A run that never reaches the target
+    runs to its iteration cap; its time is the time to finish."""
+    out = {}
+    for w in FORM_WORKLOADS:
+        out[w] = _forms_on(z, workloads.workload(w), dev, stream, seeds)
+    return out
+
+
+def _forms_on(z, fields, dev, stream, seeds):
+    import torch
+    forms = [("fp64", "forward"), ("fp64", "adjoint"), ("fp32_guarded", "forward"),
+             ("fp32_guarded", "adjoint")]
+    out = {}
+    for prec, grad in forms:
+        times, ok, iters = [], 0, []
+        for r in range(seeds + 1):  # the first run warms up
+            f = dict(fields, precision=prec, grad_mode=grad, target_f=1e-6, seed=1000 + r)
+            p = z.Problem(**{k: v for k, v in f.items() if k in z.Problem.__dataclass_fields__})
+            pc = p.to_c()
+            ws = z.new_workspace(pc, dev)
+            xo = torch.empty(p.n_starts, p.dim, dtype=torch.float64, device=dev)
+            fo = torch.empty(p.n_starts, dtype=torch.float64, device=dev)
+            res = z.new_result(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            z.zeus_solve(pc, ws, xo, fo, None, None, None, res, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if r == 0:
+                continue
+            s = z.decode_result(res)
+            times.append(e0.elapsed_time(e1))
+            ok += int(s["best_f"] <= 1e-6)
+            iters.append(int(s["total_iters"]))
+        out[f"{prec}/{grad}"] = {"time_to_target_ms": round(statistics.median(times), 3),
+                                 "success": f"{ok}/{seeds}",
+                                 "start_iters_median": int(statistics.median(iters))}
+    return out
 
 
 FP64_PEAK_TFLOPS = 1.25  # FP64 FMA throughput measured on GB300 (= nominal)

@@ -49,8 +49,7 @@ int validate(const zeus_problem* p) {
     if (p->grad_mode != ZEUS_GRAD_FORWARD && p->grad_mode != ZEUS_GRAD_ADJOINT) return ZEUS_EINVAL;
     if (p->start_from_pbest != 0 && p->start_from_pbest != 1) return ZEUS_EINVAL;
     if (!valid_lanes(p->threads_per_start)) return ZEUS_EINVAL;
-    if (p->precision == ZEUS_FP32_GUARDED) return ZEUS_EUNSUPPORTED;
-    if (p->precision != ZEUS_FP64) return ZEUS_EINVAL;
+    if (p->precision != ZEUS_FP64 && p->precision != ZEUS_FP32_GUARDED) return ZEUS_EINVAL;
     return ZEUS_OK;
 }
 

@@ -22,6 +22,11 @@ WORKLOADS = {
                                 n_starts=16384, pso_iters=20, bfgs_max_iters=1000, ls_max_iters=20,
                                 grad_tol=1e-8, w=0.7, c1=1.5, c2=1.5, armijo_c=1e-4, backtrack=0.5,
                                 seed=0),
+    # 5-D Rastrigin: 16384 particles in [-5.12,5.12]^5, 20 PSO updates, 1000 BFGS iterations
+    "rastrigin5d_n16384": dict(objective="rastrigin", dim=5, lower=-5.12, upper=5.12,
+                               n_starts=16384, pso_iters=20, bfgs_max_iters=1000, ls_max_iters=20,
+                               grad_tol=1e-8, w=0.7, c1=1.5, c2=1.5, armijo_c=1e-4, backtrack=0.5,
+                               seed=0),
     # Rosenbrock chain d=256: 8192 particles in [-2,2]^256, 10 PSO updates, 2000 iterations
     "rosenbrock256d_n8192": dict(objective="rosenbrock", dim=256, lower=-2.0, upper=2.0,
                                  n_starts=8192, pso_iters=10, bfgs_max_iters=2000, ls_max_iters=20,

@@ -83,7 +83,7 @@ def test_validation_rejects(z, kw):
 @pytest.mark.parametrize("kw", [
     dict(objective="rastrigin", dim=1), dict(objective="quadratic", dim=1), dict(objective="ackley", dim=4096),
     dict(n_starts=1), dict(pso_iters=0), dict(bfgs_max_iters=0), dict(grad_mode="adjoint"),
-    dict(threads_per_start=128), dict(threads_per_start=1), dict(start_from_pbest=1), dict(required_converged=3), dict(target_f=1e-6),
+    dict(threads_per_start=128), dict(threads_per_start=1), dict(start_from_pbest=1), dict(precision="fp32_guarded"), dict(required_converged=3), dict(target_f=1e-6),
 ])
 def test_validation_accepts(z, kw):
     assert z.zeus_validate(z.Problem(**kw)) == 0
