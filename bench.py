@@ -243,24 +243,36 @@ def run_zeus(a):
     e2e_value = iters_per_step * len(e2e_ms) / (sum(e2e_ms) / 1e3)
     d2h = n * d * 8 + n * 8 * 2 + n * 4 * 2 + 64
 
-    # roofline of the dominant launch sequence: the BFGS phase (the narrow
-    # one-lane-per-start kernel, the wide hand-over kernel and the argmin),
-    # FP64-bound; timed by the events around zeus_solve_from on its stream
-    flops = fp64_flops(d, iters_per_step, feval_per_step)
+    # roofline of the dominant launch sequence, the BFGS phase, timed by the
+    # events around zeus_solve_from on its stream
+    plan = z.zeus_plan_info(pc)
     bfgs_s = statistics.mean(bfgs_ms) / 1e3
-    achieved = flops / bfgs_s / 1e12
-    peak = FP64_PEAK_TFLOPS
-    roof = {"kernel": "bfgs_narrow_kernel + bfgs_wide_kernel (+ argmin)", "bound": "alu",
-            "achieved": round(achieved, 5), "peak": peak, "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 5), "traffic": None,
-            "peak_source": "FP64 FMA rate measured on this GB300 (1.25 TFLOP/s, equal to the "
-                           "part's nominal FP64 rate)",
-            "flops_per_launch": flops, "launch_ms": round(bfgs_s * 1e3, 3)}
+    if plan["stream"]:
+        # H streamed from HBM: 2 d^2 sizeof(T) bytes per start-iteration
+        nbytes = 2.0 * plan["h_bytes"] * iters_per_step
+        achieved = nbytes / bfgs_s / 1e9
+        peak = _peaks().get("hbm_gbs", 6800.0)
+        roof = {"kernel": "bfgs_stream_kernel (+ argmin)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json)",
+                "bytes_per_launch": nbytes, "launch_ms": round(bfgs_s * 1e3, 3)}
+    else:
+        flops = fp64_flops(d, iters_per_step, feval_per_step)
+        achieved = flops / bfgs_s / 1e12
+        peak = FP64_PEAK_TFLOPS
+        roof = {"kernel": "bfgs_narrow_kernel + bfgs_wide_kernel (+ argmin)", "bound": "alu",
+                "achieved": round(achieved, 5), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 5), "traffic": None,
+                "peak_source": "FP64 FMA rate measured on this GB300 (1.25 TFLOP/s, equal to "
+                               "the part's nominal FP64 rate)",
+                "flops_per_launch": flops, "launch_ms": round(bfgs_s * 1e3, 3)}
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "start-iters/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if a.precision == "fp32_guarded" else "f64",
         "data": "synthetic (seeded Philox draws of the method itself; no dataset)",
         "config": {"workload": a.workload, "objective": p.objective, "dim": d, "n_starts": n,
                    "pso_iters": p.pso_iters, "bfgs_max_iters": p.bfgs_max_iters,

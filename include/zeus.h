@@ -101,8 +101,10 @@ typedef struct {
     int32_t start_from_pbest;   /* 0: BFGS from current positions (Alg. 10), 1: from personal bests */
     int32_t threads_per_start;  /* 0 = automatic: one lane per start for small d, with the
                                    long-running starts handed to one 128-thread block
-                                   each; 1 = one lane per start throughout;
-                                   128 = one 128-thread block per start throughout */
+                                   each; H streamed from HBM when it does not fit on
+                                   chip; 1 = one lane per start throughout;
+                                   128 = one 128-thread block per start throughout;
+                                   256 = one 256-thread block per start, H streamed */
 } zeus_problem;
 
 /* Summary written on the device by zeus_solve / zeus_solve_from. */
@@ -131,6 +133,18 @@ int zeus_default_problem(zeus_problem *p);
 
 /* Check every field of *p; ZEUS_OK, ZEUS_EINVAL or ZEUS_EUNSUPPORTED. */
 int zeus_validate(const zeus_problem *p);
+
+/* Which kernels zeus_solve / zeus_solve_from run for problem *p. */
+typedef struct {
+    int32_t narrow;          /* 1: one lane per start (the bulk) */
+    int32_t handover;        /* 1: long runs handed to one block per start */
+    int32_t block;           /* 1: one 128-thread block per start, H in shared memory */
+    int32_t stream;          /* 1: one 256-thread block per start, H streamed from HBM */
+    int32_t blocks;          /* grid of the block-per-start / streaming kernel */
+    int32_t pad;
+    int64_t h_bytes;         /* bytes of H per start in the chosen precision */
+} zeus_plan;
+int zeus_plan_info(const zeus_problem *p, zeus_plan *plan);
 
 /* Device workspace needed by zeus_solve / zeus_solve_from / zeus_pso /
  * zeus_argmin for problem *p (host pointer), in bytes. */
@@ -230,6 +244,8 @@ int zeus_math_eval(int32_t fn, int64_t n, const double *x, double *y0, double *y
  *     n_starts * (12 + 8 * dim * dim) bytes within the array (about 20000
  *     starts at dim 10); larger problems get ZEUS_EWORKSPACE.  Otherwise
  *     zeus_validate's limits apply.
+ *   - Problems whose H must stream from HBM (zeus_plan_info().stream) need
+ *     more than the array and get ZEUS_EWORKSPACE.
  *   - f_out is required (device double [N]); the other arguments are those
  *     of zeus_solve_from.
  *   - The first call on a device looks up the array's device address

@@ -23,7 +23,7 @@ from ._capi import (GRAD_MODES, OBJECTIVES, PRECISIONS, RUN_STATUS, ZeusError, c
 __all__ = [
     "Problem", "ZeusError", "zeus_solve", "zeus_solve_from", "zeus_solve_from_noalloc", "zeus_pso", "zeus_objective_eval",
     "zeus_objective_eval_f32", "zeus_argmin", "zeus_argmin_workspace_size", "zeus_uniform",
-    "zeus_workspace_size", "zeus_validate", "zeus_default_problem", "zeus_strerror",
+    "zeus_workspace_size", "zeus_plan_info", "zeus_validate", "zeus_default_problem", "zeus_strerror",
     "zeus_abi_version", "zeus_math_eval", "Context", "solve", "solve_from", "pso", "objective", "ObjectiveFn",
     "decode_result", "library_path", "lib",
 ]
@@ -131,6 +131,13 @@ def zeus_default_problem() -> zeus_problem:
 
 def zeus_validate(problem) -> int:
     return lib().zeus_validate(C.byref(_prob(problem)))
+
+
+def zeus_plan_info(problem) -> dict:
+    """Which kernels a solve of this problem runs."""
+    pl = _capi.zeus_plan()
+    check(lib().zeus_plan_info(C.byref(_prob(problem)), C.byref(pl)), "zeus_plan_info")
+    return {name: getattr(pl, name) for name, _ in _capi.zeus_plan._fields_ if name != "pad"}
 
 
 def zeus_workspace_size(problem) -> int:

@@ -52,6 +52,12 @@ class zeus_result(C.Structure):
     ]
 
 
+class zeus_plan(C.Structure):
+    _fields_ = [("narrow", C.c_int32), ("handover", C.c_int32), ("block", C.c_int32),
+                ("stream", C.c_int32), ("blocks", C.c_int32), ("pad", C.c_int32),
+                ("h_bytes", C.c_int64)]
+
+
 class ZeusError(RuntimeError):
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {strerror(code)} ({code})")
@@ -69,6 +75,7 @@ SIGNATURES = {
     "zeus_default_problem": (C.c_int, [C.POINTER(zeus_problem)]),
     "zeus_validate": (C.c_int, [C.POINTER(zeus_problem)]),
     "zeus_workspace_size": (C.c_int, [C.POINTER(zeus_problem), C.POINTER(C.c_size_t)]),
+    "zeus_plan_info": (C.c_int, [C.POINTER(zeus_problem), C.POINTER(zeus_plan)]),
     "zeus_solve": (C.c_int, [C.POINTER(zeus_problem), _VP, C.c_size_t, _VP, _VP, _VP, _VP, _VP,
                              _VP, _VP]),
     "zeus_solve_from": (C.c_int, [C.POINTER(zeus_problem), _VP, _VP, C.c_size_t, _VP, _VP, _VP,

@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libzeus.so")
 
-SOURCES = ["zeus_capi.cu", "zeus_pso.cu", "zeus_bfgs.cu", "zeus_objective.cu", "zeus_noalloc.cu"]
+SOURCES = ["zeus_capi.cu", "zeus_pso.cu", "zeus_bfgs.cu", "zeus_objective.cu", "zeus_noalloc.cu",
+           "zeus_stream.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

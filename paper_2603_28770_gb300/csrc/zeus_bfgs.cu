@@ -691,12 +691,17 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
     L->narrow_blocks = (int)((p.n_starts + nthreads - 1) / nthreads);
     L->W = wide_trials(d, p.ls_max_iters);
     L->wide_smem = wide_smem(d, L->W, p.ls_max_iters, ts);
-    if (!L->narrow && L->wide_smem > cap) return ZEUS_EUNSUPPORTED;
+    // H streamed from HBM when the block-per-start kernel cannot hold it
+    L->stream = (req == 256) || (!L->narrow && L->wide_smem > cap);
+    L->stream_blocks = stream_blocks(p);
+    L->stream_smem = stream_smem(d, ts);
+    L->hslot_bytes = L->stream ? (size_t)L->stream_blocks * d * d * ts : 0;
+    if (L->stream && L->stream_smem > cap) return ZEUS_EUNSUPPORTED;
     L->wide_blocks = 152 * 4;
     // hand-over budget (iterations + line-search evaluations) of the narrow
     // kernel; 0 = every start runs to its end in the narrow kernel.  Only
     // used when the wide kernel can hold the start (its shared memory fits).
-    L->budget = (L->narrow && L->wide_smem <= cap && req != 1) ? 160 : 0;
+    L->budget = (L->narrow && !L->stream && L->wide_smem <= cap && req != 1) ? 160 : 0;
     L->q_cap = 0;
     if (L->budget > 0) {
         // at most two starts per wide block: beyond that the long runs are
@@ -755,6 +760,9 @@ static cudaError_t bfgs_obj(const zeus_problem& p, const BfgsLaunch& L, const do
 cudaError_t launch_bfgs(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
                         double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
                         int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st) {
+    if (L.stream)
+        return launch_bfgs_stream(p, x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl,
+                                  q.hslots, st);
     switch (p.objective) {
         case ZEUS_OBJ_ROSENBROCK:
             return bfgs_obj<ZEUS_OBJ_ROSENBROCK>(p, L, x0, x_out, f_out, gnorm_out, status_out,

@@ -16,7 +16,7 @@ namespace {
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-bool valid_lanes(int g) { return g == 0 || g == 1 || g == kWideThreads; }
+bool valid_lanes(int g) { return g == 0 || g == 1 || g == kWideThreads || g == 256; }
 
 int validate(const zeus_problem* p) {
     if (!p) return ZEUS_EINVAL;
@@ -83,6 +83,8 @@ Layout layout_for(const zeus_problem& p, const BfgsLaunch& L) {
     off += align256(qc * sizeof(int));
     lay.q_h = off;
     off += align256(qc * d * d * sizeof(double));
+    lay.hslots = off;
+    off += align256(L.hslot_bytes);
     lay.total = off;
     return lay;
 }
@@ -108,6 +110,7 @@ Queue queue_for(void* ws, const Layout& lay, const BfgsLaunch& L) {
     q.feval = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + lay.q_feval);
     q.H = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + lay.q_h);
     q.cap = L.q_cap;
+    q.hslots = reinterpret_cast<char*>(ws) + lay.hslots;
     return q;
 }
 
@@ -174,6 +177,23 @@ int zeus_default_problem(zeus_problem* p) {
 }
 
 int zeus_validate(const zeus_problem* p) { return validate(p); }
+
+int zeus_plan_info(const zeus_problem* p, zeus_plan* plan) {
+    if (!plan) return ZEUS_EINVAL;
+    const int v = validate(p);
+    if (v != ZEUS_OK) return v;
+    BfgsLaunch L;
+    const int r = plan_bfgs(*p, &L);
+    if (r != ZEUS_OK) return r;
+    memset(plan, 0, sizeof(*plan));
+    plan->narrow = L.narrow ? 1 : 0;
+    plan->handover = L.budget > 0 ? 1 : 0;
+    plan->stream = L.stream ? 1 : 0;
+    plan->block = (!L.narrow && !L.stream) ? 1 : 0;
+    plan->blocks = L.stream ? L.stream_blocks : L.wide_blocks;
+    plan->h_bytes = (int64_t)p->dim * p->dim * (p->precision == ZEUS_FP32_GUARDED ? 4 : 8);
+    return ZEUS_OK;
+}
 
 int zeus_workspace_size(const zeus_problem* p, size_t* bytes) {
     if (!bytes) return ZEUS_EINVAL;

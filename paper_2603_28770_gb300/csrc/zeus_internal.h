@@ -41,7 +41,7 @@ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Workspace carve-up (offsets in bytes from the workspace base).
 struct Layout {
-    size_t ctrl, partials, f_tmp, v, px, pf, gx, q_start, q_k, q_feval, q_h, total;
+    size_t ctrl, partials, f_tmp, v, px, pf, gx, q_start, q_k, q_feval, q_h, hslots, total;
 };
 
 // Hand-over queue from the narrow to the wide BFGS kernel (workspace).
@@ -51,6 +51,7 @@ struct Queue {
     int* feval;   // [cap] line-search evaluations so far
     double* H;    // [cap][d*d] inverse-Hessian approximation
     int cap;
+    void* hslots; // H slots of the streaming kernel
 };
 
 constexpr int kNarrowThreads = 128;
@@ -68,6 +69,10 @@ struct BfgsLaunch {
     int wide_blocks;      // persistent grid of the wide kernel
     int budget;           // narrow-kernel work budget (iterations + evaluations), 0 = none
     int q_cap;            // hand-over queue capacity
+    bool stream;          // large d: H streamed from an HBM slot per block
+    int stream_blocks;    // blocks (= H slots) of the streaming kernel
+    size_t stream_smem;   // its dynamic shared memory
+    size_t hslot_bytes;   // bytes of all H slots
 };
 
 // ---- launchers (defined in the kernel translation units) ----
@@ -84,6 +89,12 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L);
 cudaError_t launch_bfgs(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
                         double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
                         int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st);
+
+size_t stream_smem(int d, size_t tsize);
+int stream_blocks(const zeus_problem& p);
+cudaError_t launch_bfgs_stream(const zeus_problem& p, const double* x0, double* x_out,
+                               double* f_out, double* gnorm_out, int32_t* status_out,
+                               int32_t* iters_out, Ctrl* ctrl, void* hslots, cudaStream_t st);
 
 cudaError_t launch_argmin(const double* f, long long n, Ctrl* ctrl, ArgPair* partials,
                           zeus_result* res, int mode, cudaStream_t st);

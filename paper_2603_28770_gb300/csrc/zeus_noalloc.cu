@@ -75,6 +75,8 @@ extern "C" int zeus_solve_from_noalloc(const zeus_problem* p, const double* x0, 
     q.feval = reinterpret_cast<int*>(b + off_queue + 2 * align256(qc * sizeof(int)));
     q.H = reinterpret_cast<double*>(b + off_queue + 3 * align256(qc * sizeof(int)));
     q.cap = L.q_cap;
+    q.hslots = nullptr;
+    if (L.stream) return ZEUS_EWORKSPACE;  // H slots do not fit the static array
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(b);
     ArgPair* parts = reinterpret_cast<ArgPair*>(b + off_parts);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -1,0 +1,532 @@
+// zeus_stream.cu -- BFGS for large d: the inverse-Hessian approximation
+// streams from HBM (Alg. 4 / Alg. 10, one CTA per start, persistent over
+// the starts).
+//
+// H does not fit in shared memory once d*d*sizeof(T) passes ~200 KB (d >
+// ~160 in FP64, > ~230 in FP32).  Each block owns one H slot in the
+// workspace and keeps it lagged by one update: the slot holds H_{k-1} and
+// the block keeps the pending rank-two correction
+//     C_{k-1} = -rho (Hy s' + s Hy') + (rho^2 y'Hy + rho) s s'
+//             = s_c A_r + Hy_c B_r,  A = b2 s - rho Hy,  B = -rho s,
+// as vectors.  After the line search and the new gradient, ONE pass over
+// the slot reads H_{k-1}, writes H_k = H_{k-1} + C_{k-1} and forms
+// u = H_k g_{k+1}.  Then H_k y_k = u + p_k (since p_k = -H_k g_k), which
+// gives C_k, and the next direction is p_{k+1} = -(u + C_k g_{k+1}) =
+// -(u + A (s'g) + B (Hy'g)): no second pass.  Algorithmic traffic per
+// start-iteration: d*d*sizeof(T) read + d*d*sizeof(T) written.
+//
+// The arithmetic is the method's in exact arithmetic; the order of
+// operations differs from the oracle (lagged update, tree sums), so this
+// path is compared with the oracle within tolerance, not bit for bit.
+// T = float is the FP32 form (FP64 for y's, |s|, |y|, g'p, y'Hy, rho, the
+// Armijo sums and the final value); T = double is the FP64 method.
+#include "zeus_device.cuh"
+#include "zeus_internal.h"
+
+namespace zeus {
+
+constexpr int kStreamThreads = 256;
+constexpr int kStreamWarps = kStreamThreads / 32;
+constexpr int kStreamTrials = 4;  // line-search trials evaluated at once
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <class T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum N doubles over the block; every thread gets the totals.  Warp
+// shuffles first, then warp 0 adds the per-warp partials of each value over
+// groups of kStreamWarps lanes (three shuffle levels instead of one thread
+// adding eight partials per value).
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double* red) {
+    static_assert(kStreamWarps == 8, "second stage assumes 8 warps");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = warp_sum_d(v[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) red[i * kStreamWarps + w] = v[i];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int i0 = 0; i0 < N; i0 += 4) {
+            const int i = i0 + (lane >> 3);
+            double a = (i < N) ? red[i * kStreamWarps + (lane & 7)] : 0.0;
+            a += __shfl_xor_sync(0xffffffffu, a, 4);
+            a += __shfl_xor_sync(0xffffffffu, a, 2);
+            a += __shfl_xor_sync(0xffffffffu, a, 1);
+            if ((lane & 7) == 0 && i < N) red[8 * N + i] = a;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = red[8 * N + i];
+    __syncthreads();
+}
+
+// value of the objective at x + a p (a = 0: at x), FP64 sum of T terms
+template <int OBJ, class T>
+__device__ __forceinline__ void term_parts(const T* x, const T* p, T a, int d, int j, double& t0,
+                                           double& t1) {
+    t1 = 0.0;
+    const bool at_x = a == T(0);  // value at x itself: p is not read
+    const T xj = at_x ? x[j] : x[j] + a * p[j];
+    if (OBJ == ZEUS_OBJ_ROSENBROCK) {
+        t0 = 0.0;
+        if (j + 1 < d) {
+            const T xk = at_x ? x[j + 1] : x[j + 1] + a * p[j + 1];
+            const T u = T(1) - xj;
+            const T v = xk - xj * xj;
+            t0 = (double)(u * u + T(100) * (v * v));
+        }
+    } else if (OBJ == ZEUS_OBJ_RASTRIGIN) {
+        if (sizeof(T) == 4) {  // cancellation-free FP32 form of x^2 - 10 cos 2 pi x + 10
+            const float sp = sinpif((float)xj);
+            t0 = (double)(xj * xj + T(20) * T(sp * sp));
+        } else {
+            t0 = (double)(xj * xj - T(10) * c_2pi(xj)) + 10.0;
+        }
+    } else if (OBJ == ZEUS_OBJ_ACKLEY) {
+        t0 = (double)(xj * xj);
+        if (sizeof(T) == 4) {
+            const float sp = sinpif((float)xj);
+            t1 = (double)(sp * sp);
+        } else {
+            t1 = (double)c_2pi(xj);
+        }
+    } else {  // quadratic (Goldstein-Price is 2-D and never streams)
+        t0 = (double)((T(0.5) * T(j + 1)) * (xj * xj));
+    }
+}
+
+template <int OBJ, class T>
+__device__ __forceinline__ double finish_parts(double s0, double s1, int d) {
+    if (OBJ == ZEUS_OBJ_ACKLEY) {
+        const double dd = (double)d;
+        const double t1 = -20.0 * exp_cw(-0.2 * sqrt(s0 / dd));
+        const double t2 = sizeof(T) == 4 ? exp_cw(1.0 - 2.0 * (s1 / dd)) : exp_cw(s1 / dd);
+        return (t1 - t2) + (20.0 + 2.718281828459045235360287471352);
+    }
+    return s0;
+}
+
+// Trial values f(x + a_m p), m = 0..n-1 (n <= kStreamTrials), all threads
+template <int OBJ, class T>
+__device__ __forceinline__ void block_values(const T* x, const T* p, const double* alpha, int n,
+                                             int d, double* out, double* red) {
+    double s[2 * kStreamTrials];
+#pragma unroll
+    for (int m = 0; m < 2 * kStreamTrials; ++m) s[m] = 0.0;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+#pragma unroll
+        for (int m = 0; m < kStreamTrials; ++m) {
+            if (m < n) {
+                double t0, t1;
+                term_parts<OBJ>(x, p, T(alpha[m]), d, j, t0, t1);
+                s[2 * m] += t0;
+                s[2 * m + 1] += t1;
+            }
+        }
+    }
+    block_sum<2 * kStreamTrials>(s, red);
+#pragma unroll
+    for (int m = 0; m < kStreamTrials; ++m)
+        if (m < n) out[m] = finish_parts<OBJ, T>(s[2 * m], s[2 * m + 1], d);
+}
+
+template <int OBJ, int GRAD, class T>
+__device__ __forceinline__ void block_gradient(const T* x, T* g, int d, double* red) {
+    AdjShared a;
+    a.c1 = a.c2 = 0.0;
+    if (GRAD == ZEUS_GRAD_ADJOINT && OBJ == ZEUS_OBJ_ACKLEY) {
+        // the two shared sums of the adjoint, over the block
+        double v[2] = {0.0, 0.0};
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            v[0] += (double)(x[j] * x[j]);
+            v[1] += (double)c_2pi(x[j]);
+        }
+        block_sum<2>(v, red);
+        const T dd = T(d);
+        const T r = xsqrt(T(v[0]) / dd);
+        const T e1 = xexp(T(-0.2) * r);
+        const T e2 = xexp(T(v[1]) / dd);
+        a.c1 = r > T(0) ? (double)(((T(-20) * e1) * (T(-0.2) / (T(2) * r))) / dd) : 0.0;
+        a.c2 = (double)(-e2 / dd);
+    }
+    for (int i = threadIdx.x; i < d; i += blockDim.x)
+        g[i] = GRAD == ZEUS_GRAD_FORWARD ? forward_pass<OBJ, T>(x, d, i).b
+                                         : adjoint_component<OBJ>(x, d, i, a);
+    __syncthreads();
+}
+
+// 16-byte vector of T
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using V = float4;
+    static constexpr int n = 4;
+    __device__ static float get(const float4& v, int i) {
+        return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+    }
+    __device__ static void set(float4& v, int i, float a) {
+        if (i == 0) v.x = a;
+        else if (i == 1) v.y = a;
+        else if (i == 2) v.z = a;
+        else v.w = a;
+    }
+};
+template <>
+struct Vec16<double> {
+    using V = double2;
+    static constexpr int n = 2;
+    __device__ static double get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+    __device__ static void set(double2& v, int i, double a) {
+        if (i == 0) v.x = a;
+        else v.y = a;
+    }
+};
+
+// The pass: H_k = H_{k-1} + (s_c A_r + hy_c B_r) (if corr), u = H_k g.
+// One warp per row, 16-byte loads and stores along the row.
+template <class T>
+__device__ __forceinline__ void h_pass(T* __restrict__ Hs, int d, bool ident, bool corr,
+                                       const T* s, const T* hy, const T* A, const T* B,
+                                       const T* g, T* u) {
+    using VT = Vec16<T>;
+    using V = typename VT::V;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool vec = (d % VT::n) == 0;
+    for (int r = w; r < d; r += kStreamWarps) {
+        T* row = Hs + (size_t)r * d;
+        const T ar = corr ? A[r] : T(0), br = corr ? B[r] : T(0);
+        T acc = T(0);
+        if (vec) {
+            const int nv = d / VT::n;
+            V* rv = reinterpret_cast<V*>(row);
+#pragma unroll 4
+            for (int c4 = lane; c4 < nv; c4 += 32) {
+                V h;
+                if (ident) {
+#pragma unroll
+                    for (int i = 0; i < VT::n; ++i) VT::set(h, i, (c4 * VT::n + i == r) ? T(1) : T(0));
+                } else {
+                    h = __ldcs(rv + c4);
+                }
+#pragma unroll
+                for (int i = 0; i < VT::n; ++i) {
+                    const int c = c4 * VT::n + i;
+                    T e = VT::get(h, i);
+                    if (corr) e = fma(s[c], ar, fma(hy[c], br, e));
+                    VT::set(h, i, e);
+                    acc = fma(e, g[c], acc);
+                }
+                if (corr || ident) __stcs(rv + c4, h);
+            }
+        } else {
+            for (int c = lane; c < d; c += 32) {
+                T e = ident ? ((c == r) ? T(1) : T(0)) : row[c];
+                if (corr) e = fma(s[c], ar, fma(hy[c], br, e));
+                if (corr || ident) row[c] = e;
+                acc = fma(e, g[c], acc);
+            }
+        }
+        acc = warp_sum_t(acc);
+        if (lane == 0) u[r] = acc;
+    }
+    __syncthreads();
+}
+
+struct StreamShared {
+    int item;
+    int status;
+    int accepted;
+    int pad;
+    double vals[kStreamTrials];
+    double red[(kStreamWarps + 1) * 2 * kStreamTrials];
+};
+
+template <int OBJ, int GRAD, class T>
+__global__ void __launch_bounds__(kStreamThreads)
+    bfgs_stream_kernel(const zeus_problem p, const double* x0, double* x_out,
+                       double* __restrict__ f_out, double* __restrict__ gnorm_out,
+                       int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
+                       Ctrl* __restrict__ ctrl, T* __restrict__ hslots) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ StreamShared sh;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int d = p.dim;
+    T* x = reinterpret_cast<T*>(smem_raw);
+    T* g = x + d;
+    T* pv = g + d;
+    T* xn = pv + d;
+    T* gn = xn + d;
+    T* sv = gn + d;  // s of the pending correction
+    T* hy = sv + d;  // Hy of the pending correction
+    T* Av = hy + d;
+    T* Bv = Av + d;
+    T* u = Bv + d;
+    T* Hs = hslots + (size_t)blockIdx.x * d * d;
+
+    const bool use_target = !isnan(p.target_f);
+    const bool use_stop = use_target || p.required_converged > 0;
+    const double tol = p.grad_tol, cA = p.armijo_c, beta = p.backtrack;
+    const int K = p.bfgs_max_iters, L = p.ls_max_iters;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sh.item = (int)atomicAdd(&ctrl->q_head, 1u);
+        __syncthreads();
+        const long long s = sh.item;
+        if (s >= p.n_starts) break;
+        for (int j = tid; j < d; j += NT) x[j] = T(x0[s * d + j]);
+        __syncthreads();
+        block_gradient<OBJ, GRAD>(x, g, d, sh.red);
+        double a0 = 0.0;
+        block_values<OBJ, T>(x, pv, &a0, 1, d, sh.vals, sh.red);  // p unused at a = 0
+        double f0 = sh.vals[0];
+        for (int j = tid; j < d; j += NT) pv[j] = -g[j];  // H_0 = I
+        bool ident = true, corr = false;
+        int k = 0, feval = 0, status = ZEUS_RUN_MAX_ITER;
+        double gnorm = 0.0;
+        __syncthreads();
+        for (;;) {
+            // ---- tests at the top of iteration k, and g'p, in one reduction
+            double v3[3] = {0.0, 0.0, 0.0};
+            for (int j = tid; j < d; j += NT) {
+                v3[0] += (double)(g[j] * g[j]);
+                v3[1] += isfinite(g[j]) ? 0.0 : 1.0;
+                v3[2] += (double)(g[j] * pv[j]);
+            }
+            block_sum<3>(v3, sh.red);
+            gnorm = sqrt(v3[0]);
+            int st = -1;
+            if (k >= K) st = ZEUS_RUN_MAX_ITER;
+            else if (use_stop && *((volatile int*)&ctrl->stop)) st = ZEUS_RUN_STOPPED;
+            else if (!isfinite(f0) || v3[1] != 0.0) st = ZEUS_RUN_NONFINITE;
+            else if (gnorm < tol) st = ZEUS_RUN_CONVERGED;
+            else if (use_target && f0 <= p.target_f) st = ZEUS_RUN_CONVERGED;
+            if (tid == 0) sh.status = st;
+            __syncthreads();
+            st = sh.status;
+            if (st >= 0) {
+                if (tid == 0 && st == ZEUS_RUN_CONVERGED && use_stop) {
+                    const unsigned long long c = atomicAdd(&ctrl->n_conv, 1ull) + 1ull;
+                    if ((use_target && f0 <= p.target_f) ||
+                        (p.required_converged > 0 && c >= (unsigned long long)p.required_converged))
+                        atomicExch(&ctrl->stop, 1);
+                }
+                status = st;
+                break;
+            }
+            // ---- descent check
+            double ddir = v3[2];
+            if (!(ddir < 0.0)) {  // restart from H = I
+                ident = true;
+                corr = false;
+                double v1[1] = {0.0};
+                for (int j = tid; j < d; j += NT) {
+                    pv[j] = -g[j];
+                    v1[0] += (double)(g[j] * -g[j]);
+                }
+                block_sum<1>(v1, sh.red);
+                ddir = v1[0];
+            }
+            // ---- backtracking Armijo line search, kStreamTrials trials at once
+            double alpha_acc = 0.0, fn = 0.0;
+            int acc = -1;
+            double a_m = 1.0;
+            for (int m0 = 0; m0 < L && acc < 0;) {
+                // the first trial alone (usually accepted), then several at once
+                const int nw = min(m0 == 0 ? 1 : kStreamTrials, L - m0);
+                double al[kStreamTrials];
+                double a = a_m;
+#pragma unroll
+                for (int i = 0; i < kStreamTrials; ++i) {
+                    al[i] = a;
+                    a = beta * a;
+                }
+                block_values<OBJ, T>(x, pv, al, nw, d, sh.vals, sh.red);
+                for (int i = 0; i < nw; ++i) {
+                    if (sh.vals[i] <= f0 + cA * al[i] * ddir) {
+                        acc = m0 + i;
+                        alpha_acc = al[i];
+                        fn = sh.vals[i];
+                        break;
+                    }
+                }
+                feval += acc >= 0 ? acc - m0 + 1 : nw;
+                a_m = al[nw - 1] * beta;
+                m0 += nw;
+                __syncthreads();
+            }
+            if (acc < 0) alpha_acc = a_m;  // the step after the last halving
+            const T at = T(alpha_acc);
+            for (int j = tid; j < d; j += NT) xn[j] = x[j] + at * pv[j];
+            __syncthreads();
+            if (acc < 0) {
+                double z = 0.0;
+                block_values<OBJ, T>(xn, pv, &z, 1, d, sh.vals, sh.red);
+                fn = sh.vals[0];
+            }
+            block_gradient<OBJ, GRAD>(xn, gn, d, sh.red);
+            // ---- the pass: H_k = H_{k-1} + C_{k-1}, u = H_k g_{k+1}
+            if (ident && !corr) {
+                for (int j = tid; j < d; j += NT) u[j] = gn[j];
+                __syncthreads();
+            } else {
+                h_pass<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u);
+                ident = false;
+            }
+            // ---- curvature pair and the correction C_k: one reduction for
+            //      y's, |s|^2, |y|^2, y'Hy, s'g_new, Hy'g_new
+            double v6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int j = tid; j < d; j += NT) {
+                const T sj = xn[j] - x[j], yj = gn[j] - g[j];
+                const T hyj = u[j] + pv[j];  // H_k y_k = H_k g_{k+1} + p_k
+                v6[0] += (double)(yj * sj);
+                v6[1] += (double)(sj * sj);
+                v6[2] += (double)(yj * yj);
+                v6[3] += (double)(yj * hyj);
+                v6[4] += (double)(sj * gn[j]);
+                v6[5] += (double)(hyj * gn[j]);
+            }
+            block_sum<6>(v6, sh.red);
+            const double sy = v6[0];
+            if (sy > 1e-12 * sqrt(v6[1]) * sqrt(v6[2])) {
+                const double rho = 1.0 / sy;
+                const double b2 = rho * rho * v6[3] + rho;
+                const T sg = T(v6[4]), hg = T(v6[5]), rt = T(rho), bt = T(b2);
+                for (int j = tid; j < d; j += NT) {
+                    const T sj = xn[j] - x[j];
+                    const T hyj = u[j] + pv[j];
+                    sv[j] = sj;
+                    hy[j] = hyj;
+                    const T a = bt * sj - rt * hyj, b = -rt * sj;
+                    Av[j] = a;
+                    Bv[j] = b;
+                    pv[j] = -(u[j] + a * sg + b * hg);
+                }
+                corr = true;
+            } else {
+                for (int j = tid; j < d; j += NT) pv[j] = -u[j];
+                corr = false;
+            }
+            for (int j = tid; j < d; j += NT) {
+                x[j] = xn[j];
+                g[j] = gn[j];
+            }
+            f0 = fn;
+            ++k;
+            __syncthreads();
+        }
+        // final value in FP64 at the final point
+        double vf[2] = {0.0, 0.0};
+        for (int j = tid; j < d; j += NT) {
+            double t0, t1;
+            const double xj = (double)x[j];
+            if (OBJ == ZEUS_OBJ_ROSENBROCK) {
+                t1 = 0.0;
+                t0 = 0.0;
+                if (j + 1 < d) {
+                    const double xk = (double)x[j + 1];
+                    const double a = 1.0 - xj, b = xk - xj * xj;
+                    t0 = a * a + 100.0 * (b * b);
+                }
+            } else if (OBJ == ZEUS_OBJ_RASTRIGIN) {
+                t0 = (xj * xj - 10.0 * c_2pi(xj)) + 10.0;
+                t1 = 0.0;
+            } else if (OBJ == ZEUS_OBJ_ACKLEY) {
+                t0 = xj * xj;
+                t1 = c_2pi(xj);
+            } else {
+                t0 = (0.5 * (double)(j + 1)) * (xj * xj);
+                t1 = 0.0;
+            }
+            vf[0] += t0;
+            vf[1] += t1;
+        }
+        block_sum<2>(vf, sh.red);
+        const double ffin = finish_parts<OBJ, double>(vf[0], vf[1], d);
+        for (int j = tid; j < d; j += NT) x_out[s * d + j] = (double)x[j];
+        if (tid == 0) {
+            if (f_out) f_out[s] = ffin;
+            if (gnorm_out) gnorm_out[s] = gnorm;
+            if (status_out) status_out[s] = status;
+            if (iters_out) iters_out[s] = k;
+            atomicAdd(&ctrl->total_iters, (unsigned long long)k);
+            atomicAdd(&ctrl->total_feval, (unsigned long long)feval);
+            if (!use_stop && status == ZEUS_RUN_CONVERGED) atomicAdd(&ctrl->n_conv, 1ull);
+        }
+    }
+}
+
+size_t stream_smem(int d, size_t tsize) { return 10 * (size_t)d * tsize; }
+
+// About four blocks per SM, and the starts spread evenly over the rounds
+// (each block takes a start, runs it to the end, takes the next).
+int stream_blocks(const zeus_problem& p) {
+    const long long full = 152ll * 4;
+    const long long rounds = (p.n_starts + full - 1) / full;
+    long long b = (p.n_starts + rounds - 1) / rounds;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <int OBJ, int GRAD, class T>
+static cudaError_t stream_go(const zeus_problem& p, const double* x0, double* x_out, double* f_out,
+                             double* gnorm_out, int32_t* status_out, int32_t* iters_out,
+                             Ctrl* ctrl, void* hslots, cudaStream_t st) {
+    auto kern = bfgs_stream_kernel<OBJ, GRAD, T>;
+    const size_t sm = stream_smem(p.dim, sizeof(T));
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    kern<<<stream_blocks(p), kStreamThreads, sm, st>>>(p, x0, x_out, f_out, gnorm_out, status_out,
+                                                       iters_out, ctrl, static_cast<T*>(hslots));
+    return cudaGetLastError();
+}
+
+template <int OBJ>
+static cudaError_t stream_obj(const zeus_problem& p, const double* x0, double* x_out, double* f_out,
+                              double* gnorm_out, int32_t* status_out, int32_t* iters_out,
+                              Ctrl* ctrl, void* hslots, cudaStream_t st) {
+    const bool f32 = p.precision == ZEUS_FP32_GUARDED;
+    if (p.grad_mode == ZEUS_GRAD_ADJOINT)
+        return f32 ? stream_go<OBJ, ZEUS_GRAD_ADJOINT, float>(p, x0, x_out, f_out, gnorm_out,
+                                                              status_out, iters_out, ctrl, hslots, st)
+                   : stream_go<OBJ, ZEUS_GRAD_ADJOINT, double>(p, x0, x_out, f_out, gnorm_out,
+                                                               status_out, iters_out, ctrl, hslots, st);
+    return f32 ? stream_go<OBJ, ZEUS_GRAD_FORWARD, float>(p, x0, x_out, f_out, gnorm_out,
+                                                          status_out, iters_out, ctrl, hslots, st)
+               : stream_go<OBJ, ZEUS_GRAD_FORWARD, double>(p, x0, x_out, f_out, gnorm_out,
+                                                           status_out, iters_out, ctrl, hslots, st);
+}
+
+cudaError_t launch_bfgs_stream(const zeus_problem& p, const double* x0, double* x_out,
+                               double* f_out, double* gnorm_out, int32_t* status_out,
+                               int32_t* iters_out, Ctrl* ctrl, void* hslots, cudaStream_t st) {
+    switch (p.objective) {
+        case ZEUS_OBJ_ROSENBROCK:
+            return stream_obj<ZEUS_OBJ_ROSENBROCK>(p, x0, x_out, f_out, gnorm_out, status_out,
+                                                   iters_out, ctrl, hslots, st);
+        case ZEUS_OBJ_RASTRIGIN:
+            return stream_obj<ZEUS_OBJ_RASTRIGIN>(p, x0, x_out, f_out, gnorm_out, status_out,
+                                                  iters_out, ctrl, hslots, st);
+        case ZEUS_OBJ_ACKLEY:
+            return stream_obj<ZEUS_OBJ_ACKLEY>(p, x0, x_out, f_out, gnorm_out, status_out,
+                                               iters_out, ctrl, hslots, st);
+        default:
+            return stream_obj<ZEUS_OBJ_QUADRATIC>(p, x0, x_out, f_out, gnorm_out, status_out,
+                                                  iters_out, ctrl, hslots, st);
+    }
+}
+
+}  // namespace zeus

@@ -42,7 +42,8 @@ def test_struct_layouts_match_header(z, tmp_path):
     from paper_2603_28770_gb300 import _capi
     import subprocess
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "zeus.h"', 'int main(void){']
-    for cname, cls in (("zeus_problem", _capi.zeus_problem), ("zeus_result", _capi.zeus_result)):
+    for cname, cls in (("zeus_problem", _capi.zeus_problem), ("zeus_result", _capi.zeus_result),
+                       ("zeus_plan", _capi.zeus_plan)):
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:
             lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
@@ -53,7 +54,8 @@ def test_struct_layouts_match_header(z, tmp_path):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                                   check=True).stdout.splitlines())
-    for cname, cls in (("zeus_problem", _capi.zeus_problem), ("zeus_result", _capi.zeus_result)):
+    for cname, cls in (("zeus_problem", _capi.zeus_problem), ("zeus_result", _capi.zeus_result),
+                       ("zeus_plan", _capi.zeus_plan)):
         assert int(out[cname]) == C.sizeof(cls)
         for f, _ in cls._fields_:
             assert int(out[f"{cname}.{f}"]) == getattr(cls, f).offset, f
@@ -74,7 +76,7 @@ def test_defaults(z):
     dict(n_starts=2**31), dict(pso_iters=-1), dict(bfgs_max_iters=-1), dict(ls_max_iters=0),
     dict(required_converged=-2), dict(grad_tol=-1.0), dict(grad_tol=float("nan")), dict(w=float("inf")),
     dict(armijo_c=0.0), dict(armijo_c=1.0), dict(backtrack=1.0), dict(backtrack=0.0), dict(grad_mode=2),
-    dict(start_from_pbest=2), dict(threads_per_start=3), dict(threads_per_start=32), dict(precision=5),
+    dict(start_from_pbest=2), dict(threads_per_start=3), dict(threads_per_start=32), dict(threads_per_start=512), dict(precision=5),
 ])
 def test_validation_rejects(z, kw):
     assert z.zeus_validate(z.Problem(**kw)) == z._capi.ZEUS_EINVAL
@@ -118,3 +120,18 @@ def test_strerror(z):
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert z.zeus_strerror(code) and "unknown" not in z.zeus_strerror(code)
     assert "unknown" in z.zeus_strerror(-99)
+
+
+def test_plan_choice(z):
+    small = z.zeus_plan_info(z.Problem(objective="rastrigin", dim=10, n_starts=16384))
+    assert small["narrow"] == 1 and small["handover"] == 1 and small["stream"] == 0
+    mid = z.zeus_plan_info(z.Problem(objective="rastrigin", dim=100, n_starts=100))
+    assert mid["block"] == 1 and mid["narrow"] == 0 and mid["stream"] == 0
+    big = z.zeus_plan_info(z.Problem(objective="rosenbrock", dim=256, n_starts=8192,
+                                     precision="fp32_guarded"))
+    assert big["stream"] == 1 and big["h_bytes"] == 256 * 256 * 4
+    forced = z.zeus_plan_info(z.Problem(objective="rastrigin", dim=10, threads_per_start=256))
+    assert forced["stream"] == 1 and forced["narrow"] == 0
+    # the stream slots are part of the workspace
+    assert z.zeus_workspace_size(z.Problem(objective="rosenbrock", dim=256, n_starts=8192,
+                                           precision="fp32_guarded")) >= 300 * 256 * 256 * 4

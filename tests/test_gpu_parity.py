@@ -369,3 +369,39 @@ def test_fp32_form_against_fp64_oracle(z, ora, obj, d, n, lo, hi, fmin, grad):
     lo_, hi_ = clopper_pearson(k_o, n)
     rate = float((g["f"] <= fmin + 1e-6).mean())
     assert lo_ - 0.02 <= rate <= hi_ + 0.02, (rate, lo_, hi_)
+
+
+# ----------------------------------------------- H streamed from HBM (large d)
+
+STREAM_CASES = [("rosenbrock", 12, 64, -2.0, 2.0), ("rastrigin", 10, 64, -5.12, 5.12),
+                ("ackley", 40, 16, -5.0, 5.0), ("quadratic", 33, 8, -1.0, 1.0),
+                ("rosenbrock", 200, 8, -2.0, 2.0)]
+
+
+@pytest.mark.parametrize("obj,d,n,lo,hi", STREAM_CASES)
+@pytest.mark.parametrize("grad", ["forward", "adjoint"])
+def test_stream_fp64_first_iterations(z, ora, obj, d, n, lo, hi, grad):
+    # the one-pass lagged update and tree sums reorder the arithmetic:
+    # the first 10 iterates agree with the oracle to 1e-8
+    x0 = workloads.start_points(n, d, lo, hi, seed=7 * n + d)
+    fields = dict(objective=obj, dim=d, lower=lo, upper=hi, n_starts=n, bfgs_max_iters=10,
+                  grad_mode=grad, threads_per_start=256)
+    assert z.zeus_plan_info(zeus_problem(z, fields))["stream"] == 1
+    g = to_np(z.solve_from(zeus_problem(z, fields), torch.from_numpy(x0).cuda()))
+    o = ora.bfgs_many(oracle_problem(ora, fields), x0)
+    compare_runs(g, o, rtol=1e-8, max_flip_frac=0.1)
+
+
+@pytest.mark.parametrize("obj,d,n,lo,hi,fmin", [("rosenbrock", 64, 32, -2.0, 2.0, 0.0),
+                                                ("rastrigin", 12, 256, -5.12, 5.12, 0.0),
+                                                ("rosenbrock", 256, 8, -2.0, 2.0, 0.0)])
+def test_stream_fp32_ends_where_fp64_ends(z, ora, obj, d, n, lo, hi, fmin):
+    x0 = workloads.start_points(n, d, lo, hi, seed=3 * n + d)
+    base = dict(objective=obj, dim=d, lower=lo, upper=hi, n_starts=n, bfgs_max_iters=3000)
+    pf = zeus_problem(z, base, precision="fp32_guarded", grad_tol=1e-3, threads_per_start=256)
+    assert z.zeus_plan_info(pf)["stream"] == 1
+    g = to_np(z.solve_from(pf, torch.from_numpy(x0).cuda()))
+    o = ora.bfgs_many(oracle_problem(ora, base), x0)
+    err = np.abs(g["f"] - o["f"])  # per-start error against the FP64 oracle
+    same = err <= 1e-5 * np.maximum(1.0, np.abs(o["f"]))
+    assert same.mean() >= 0.85, f"{(~same).sum()} of {n}; errors {np.sort(err)[-5:]}"
