@@ -227,6 +227,67 @@ int zeus_uniform(uint64_t seed, uint64_t problem, uint64_t phase,
 int zeus_math_eval(int32_t fn, int64_t n, const double *x, double *y0, double *y1,
                    void *stream);
 
+/* ---- Batched form (the paper solves one problem per call) ----
+ *
+ * Many independent problems (any mix of objective, dim, N, T, K, seed)
+ * solved by one fixed sequence of kernels: PSO updates of every problem in
+ * one launch per update, BFGS of every start from a device work list
+ * (persistent blocks; one launch per shared-memory class), the hand-over
+ * launch, and one best-of-swarm reduction per problem.  Problem P's results
+ * equal those of zeus_solve(&probs[P]) bit for bit.
+ *
+ * Every problem of a batch shares `precision` and `grad_mode`; problems
+ * whose H must stream from HBM (zeus_plan_info().stream) are not batched
+ * (ZEUS_EUNSUPPORTED).  A problem's n_starts must be below 2^30.
+ *
+ * Outputs are the problems' arrays concatenated in problem order:
+ *   x_out      device double [sum_P N_P * dim_P]   final BFGS points (required)
+ *   f_out      device double [sum_P N_P]           final f (required)
+ *   gnorm_out  device double [sum_P N_P]           (may be NULL)
+ *   status_out device int32  [sum_P N_P]           (may be NULL)
+ *   iters_out  device int32  [sum_P N_P]           (may be NULL)
+ *   results    device zeus_result [n_problems]     (may be NULL)
+ * Problem P's rows start at the prefix sums of N_Q * dim_Q and N_Q, Q < P.
+ */
+#define ZEUS_BATCH_MAX_CLASSES 16
+
+typedef struct {
+    int32_t n_problems;
+    int32_t pso_blocks;       /* blocks of each batched PSO launch */
+    int32_t items;            /* BFGS work-list entries (lane tiles + block starts) */
+    int32_t pso_iters_max;    /* PSO launches = pso_iters_max + 1 */
+    int32_t q_cap;            /* hand-over queue entries */
+    int32_t d_max_handover;   /* largest dim that can be handed over */
+    int32_t precision, grad_mode;
+    int32_t n_classes;        /* BFGS launches over the work list */
+    int32_t handover_smem;    /* dynamic shared memory of the hand-over launch */
+    int32_t class_first[ZEUS_BATCH_MAX_CLASSES];  /* work-list range and dynamic */
+    int32_t class_count[ZEUS_BATCH_MAX_CLASSES];  /* shared memory of each BFGS */
+    int32_t class_smem[ZEUS_BATCH_MAX_CLASSES];   /* launch */
+    int64_t total_starts;     /* sum_P N_P */
+    int64_t total_coords;     /* sum_P N_P * dim_P */
+    int64_t total_g;          /* sum_P dim_P */
+    uint64_t workspace_bytes; /* device workspace the batch needs */
+} zeus_batch_plan;
+
+/* Plans a batch (host only, no CUDA call).  probs: host array [n]. */
+int zeus_batch_plan_make(const zeus_problem *probs, int32_t n, zeus_batch_plan *plan);
+
+/* Writes the batch's tables (problem parameters, offsets, work list) into
+ * the workspace: one host-to-device copy on `stream`, then synchronizes
+ * `stream`.  probs and plan must be those given to zeus_batch_plan_make;
+ * workspace: device, plan->workspace_bytes, 256-byte aligned.  The tables
+ * stay valid for any number of zeus_batch_solve calls on this workspace. */
+int zeus_batch_prepare(const zeus_problem *probs, int32_t n, const zeus_batch_plan *plan,
+                       void *workspace, size_t workspace_bytes, void *stream);
+
+/* Runs the prepared batch.  Enqueues kernels and one memset only (no copy,
+ * no synchronization, no allocation), so a call can be recorded in a CUDA
+ * graph and replayed; every replay recomputes the results from the tables. */
+int zeus_batch_solve(const zeus_batch_plan *plan, void *workspace, size_t workspace_bytes,
+                     double *x_out, double *f_out, double *gnorm_out, int32_t *status_out,
+                     int32_t *iters_out, zeus_result *results, void *stream);
+
 /* ---- No-allocation variant (the paper has no counterpart) ----
  *
  * zeus_solve_from without a workspace argument, for callers that cannot

@@ -25,7 +25,8 @@ __all__ = [
     "zeus_objective_eval_f32", "zeus_argmin", "zeus_argmin_workspace_size", "zeus_uniform",
     "zeus_workspace_size", "zeus_plan_info", "zeus_validate", "zeus_default_problem", "zeus_strerror",
     "zeus_abi_version", "zeus_math_eval", "Context", "solve", "solve_from", "pso", "objective", "ObjectiveFn",
-    "decode_result", "library_path", "lib",
+    "decode_result", "library_path", "lib", "zeus_batch_plan_make", "zeus_batch_prepare",
+    "zeus_batch_solve", "Batch",
 ]
 
 
@@ -288,6 +289,124 @@ class Context:
                                     hp(status_out), hp(iters_out), C.addressof(res),
                                     _stream(stream)), "zeus_solve_host")
         return {name: getattr(res, name) for name, _ in zeus_result._fields_}
+
+
+# ------------------------------------------------------------ batched form
+
+def _prob_array(problems):
+    arr = (zeus_problem * len(problems))()
+    for i, p in enumerate(problems):
+        arr[i] = _prob(p)
+    return arr
+
+
+def zeus_batch_plan_make(problems) -> _capi.zeus_batch_plan:
+    """Host-only plan of a batch (work list classes, workspace size)."""
+    arr = _prob_array(problems)
+    plan = _capi.zeus_batch_plan()
+    check(lib().zeus_batch_plan_make(arr, len(problems), C.byref(plan)), "zeus_batch_plan_make")
+    return plan
+
+
+def zeus_batch_prepare(problems, plan, workspace, stream=None) -> None:
+    """Upload the batch's tables into the workspace (synchronizes the stream)."""
+    arr = _prob_array(problems)
+    check(lib().zeus_batch_prepare(arr, len(problems), C.byref(plan),
+                                   _ptr(workspace, torch.uint8, name="workspace"),
+                                   workspace.numel(), _stream(stream)), "zeus_batch_prepare")
+
+
+def zeus_batch_solve(plan, workspace, x_out, f_out, gnorm_out=None, status_out=None,
+                     iters_out=None, results=None, stream=None) -> None:
+    """Run a prepared batch (kernels only: capturable in a CUDA graph)."""
+    ns, nc, npb = plan.total_starts, plan.total_coords, plan.n_problems
+    check(lib().zeus_batch_solve(
+        C.byref(plan), _ptr(workspace, torch.uint8, name="workspace"), workspace.numel(),
+        _ptr(x_out, torch.float64, nc, "x_out"), _ptr(f_out, torch.float64, ns, "f_out"),
+        _ptr(gnorm_out, torch.float64, ns, "gnorm_out"),
+        _ptr(status_out, torch.int32, ns, "status_out"), _ptr(iters_out, torch.int32, ns, "iters_out"),
+        _ptr(results, torch.uint8, npb * RESULT_BYTES, "results"), _stream(stream)),
+        "zeus_batch_solve")
+
+
+class Batch:
+    """A prepared batch of problems: owns the workspace and the concatenated
+    outputs; ``solve()`` runs it, ``capture()`` records one solve in a CUDA
+    graph that ``replay()`` runs again (same tables, same outputs).  With an
+    ``autotune.Autotuner`` the per-start layout of each problem is the
+    measured fastest (the results do not depend on it)."""
+
+    def __init__(self, problems, device="cuda", stream=None, autotuner=None):
+        self.problems = [_prob(p) for p in problems]
+        if autotuner is not None:  # per-start layout chosen by measurement
+            self.problems = autotuner.apply(self.problems)
+        self.plan = zeus_batch_plan_make(self.problems)
+        pl = self.plan
+        self.workspace = torch.empty(max(int(pl.workspace_bytes), 256), dtype=torch.uint8,
+                                     device=device)
+        self.x = torch.empty(pl.total_coords, dtype=torch.float64, device=device)
+        self.f = torch.empty(pl.total_starts, dtype=torch.float64, device=device)
+        self.gnorm = torch.empty(pl.total_starts, dtype=torch.float64, device=device)
+        self.status = torch.empty(pl.total_starts, dtype=torch.int32, device=device)
+        self.iters = torch.empty(pl.total_starts, dtype=torch.int32, device=device)
+        self.results = torch.empty(pl.n_problems * RESULT_BYTES, dtype=torch.uint8, device=device)
+        zeus_batch_prepare(self.problems, pl, self.workspace, stream)
+        self.graph = None
+        # row offsets of each problem in the concatenated outputs
+        self.xoff, self.soff = [], []
+        xo = so = 0
+        for p in self.problems:
+            self.xoff.append(xo)
+            self.soff.append(so)
+            xo += p.n_starts * p.dim
+            so += p.n_starts
+
+    @property
+    def launches(self) -> int:
+        """Kernels one solve launches (plus one memset)."""
+        pl = self.plan
+        return (pl.pso_iters_max + 1) + pl.n_classes + (1 if pl.q_cap > 0 else 0) + 1
+
+    def solve(self, stream=None) -> None:
+        zeus_batch_solve(self.plan, self.workspace, self.x, self.f, self.gnorm, self.status,
+                         self.iters, self.results, stream)
+
+    def capture(self) -> "torch.cuda.CUDAGraph":
+        """Record one solve in a CUDA graph (on a side stream, as torch requires)."""
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            g.capture_begin()
+            try:
+                self.solve(side)
+            finally:
+                g.capture_end()
+        torch.cuda.current_stream().wait_stream(side)
+        self.graph = g
+        return g
+
+    def replay(self) -> None:
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def problem(self, P: int) -> dict:
+        """Views of problem P's outputs and its decoded summary (synchronizes)."""
+        p = self.problems[P]
+        xo, so, n, d = self.xoff[P], self.soff[P], p.n_starts, p.dim
+        raw = self.results[P * RESULT_BYTES:(P + 1) * RESULT_BYTES]
+        return dict(x=self.x[xo:xo + n * d].view(n, d), f=self.f[so:so + n],
+                    gnorm=self.gnorm[so:so + n], status=self.status[so:so + n],
+                    iters=self.iters[so:so + n], summary=decode_result(raw))
+
+    def summaries(self) -> list[dict]:
+        raw = self.results.cpu().numpy().tobytes()
+        out = []
+        for P in range(self.plan.n_problems):
+            r = zeus_result.from_buffer_copy(raw[P * RESULT_BYTES:(P + 1) * RESULT_BYTES])
+            out.append({name: getattr(r, name) for name, _ in zeus_result._fields_})
+        return out
 
 
 # ------------------------------------------------------------ conveniences

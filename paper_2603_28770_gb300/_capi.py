@@ -58,6 +58,21 @@ class zeus_plan(C.Structure):
                 ("h_bytes", C.c_int64)]
 
 
+BATCH_MAX_CLASSES = 16
+
+
+class zeus_batch_plan(C.Structure):
+    _fields_ = [("n_problems", C.c_int32), ("pso_blocks", C.c_int32), ("items", C.c_int32),
+                ("pso_iters_max", C.c_int32), ("q_cap", C.c_int32), ("d_max_handover", C.c_int32),
+                ("precision", C.c_int32), ("grad_mode", C.c_int32), ("n_classes", C.c_int32),
+                ("handover_smem", C.c_int32),
+                ("class_first", C.c_int32 * BATCH_MAX_CLASSES),
+                ("class_count", C.c_int32 * BATCH_MAX_CLASSES),
+                ("class_smem", C.c_int32 * BATCH_MAX_CLASSES),
+                ("total_starts", C.c_int64), ("total_coords", C.c_int64), ("total_g", C.c_int64),
+                ("workspace_bytes", C.c_uint64)]
+
+
 class ZeusError(RuntimeError):
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {strerror(code)} ({code})")
@@ -91,6 +106,12 @@ SIGNATURES = {
     "zeus_uniform": (C.c_int, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int32, _VP,
                                _VP]),
     "zeus_math_eval": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, _VP, _VP]),
+    "zeus_batch_plan_make": (C.c_int, [C.POINTER(zeus_problem), C.c_int32,
+                                       C.POINTER(zeus_batch_plan)]),
+    "zeus_batch_prepare": (C.c_int, [C.POINTER(zeus_problem), C.c_int32,
+                                     C.POINTER(zeus_batch_plan), _VP, C.c_size_t, _VP]),
+    "zeus_batch_solve": (C.c_int, [C.POINTER(zeus_batch_plan), _VP, C.c_size_t, _VP, _VP, _VP,
+                                   _VP, _VP, _VP, _VP]),
     "zeus_solve_from_noalloc": (C.c_int, [C.POINTER(zeus_problem), _VP, _VP, _VP, _VP, _VP,
                                           _VP, _VP, _VP]),
     "zeus_context_create": (C.c_int, [C.POINTER(_VP)]),

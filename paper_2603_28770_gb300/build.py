@@ -19,8 +19,13 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libzeus.so")
 
-SOURCES = ["zeus_capi.cu", "zeus_pso.cu", "zeus_bfgs.cu", "zeus_objective.cu", "zeus_noalloc.cu",
-           "zeus_stream.cu"]
+# (source, extra defines): the kernels of each (gradient mode, precision)
+# pair are compiled as translation units of their own, in parallel
+_PAIRS = [("-DZEUS_KGRAD=%d" % g, "-DZEUS_KF32=%d" % f) for g in (0, 1) for f in (0, 1)]
+SOURCES = ([(s, ()) for s in ("zeus_capi.cu", "zeus_pso.cu", "zeus_bfgs.cu", "zeus_objective.cu",
+                              "zeus_noalloc.cu", "zeus_stream.cu", "zeus_batch.cu")]
+           + [("zeus_bfgs_kernels.cu", d) for d in _PAIRS]
+           + [("zeus_batch_kernels.cu", d) for d in _PAIRS])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,6 +50,11 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
+def _obj_name(src: str, defines) -> str:
+    tag = "".join("_" + d.split("=")[-1] for d in defines)
+    return os.path.join(BUILD, src.replace(".cu", tag + ".o"))
+
+
 def _compile(src: str, obj: str, extra=()) -> None:
     cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj, *_flags(extra)]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,9 +67,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
+    objs = [_obj_name(s, d) for s, d in SOURCES]
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        futs = [ex.submit(_compile, s, o, extra) for s, o in zip(SOURCES, objs)]
+        futs = [ex.submit(_compile, s, o, (*d, *extra)) for (s, d), o in zip(SOURCES, objs)]
         for f in futs:
             f.result()
     tmp = LIB + f".tmp{os.getpid()}"

@@ -1,0 +1,156 @@
+// zeus_batch_kernels.cu -- the batched BFGS kernel of zeus_batch.cu for one
+// (gradient mode, precision) pair, chosen at compile time by ZEUS_KGRAD
+// (0 forward, 1 adjoint) and ZEUS_KF32 (0 FP64, 1 FP32 with FP64 guards):
+// the library compiles this file once per pair, in parallel.
+#include "zeus_bfgs.cuh"
+
+#if !defined(ZEUS_KGRAD) || !defined(ZEUS_KF32)
+#error "compile with -DZEUS_KGRAD=0|1 -DZEUS_KF32=0|1"
+#endif
+
+namespace zeus {
+
+template <int GRAD, class T>
+__device__ __forceinline__ void batch_narrow(const zeus_problem& p, int P, long long s, T* slot,
+                                             const BatchDev& bd, const RunIO& io) {
+    const int b = bd.budget[P];
+    Ctrl* qc = bd.gctrl;
+    switch (p.objective) {
+        case ZEUS_OBJ_ROSENBROCK:
+            narrow_run<ZEUS_OBJ_ROSENBROCK, GRAD, T>(p, s, slot, b, io, qc, bd.q, P);
+            break;
+        case ZEUS_OBJ_RASTRIGIN:
+            narrow_run<ZEUS_OBJ_RASTRIGIN, GRAD, T>(p, s, slot, b, io, qc, bd.q, P);
+            break;
+        case ZEUS_OBJ_ACKLEY:
+            narrow_run<ZEUS_OBJ_ACKLEY, GRAD, T>(p, s, slot, b, io, qc, bd.q, P);
+            break;
+        case ZEUS_OBJ_GOLDSTEIN_PRICE:
+            narrow_run<ZEUS_OBJ_GOLDSTEIN_PRICE, GRAD, T>(p, s, slot, b, io, qc, bd.q, P);
+            break;
+        default:
+            narrow_run<ZEUS_OBJ_QUADRATIC, GRAD, T>(p, s, slot, b, io, qc, bd.q, P);
+            break;
+    }
+}
+
+template <int GRAD, class T>
+__device__ __forceinline__ void batch_wide(const zeus_problem& p, int W, long long s, int k,
+                                           int fe, const T* Hq, const T* xq, const RunIO& io,
+                                           WideShared& sh, unsigned char* smem_raw, int tid) {
+    switch (p.objective) {
+        case ZEUS_OBJ_ROSENBROCK:
+            wide_run<ZEUS_OBJ_ROSENBROCK, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);
+            break;
+        case ZEUS_OBJ_RASTRIGIN:
+            wide_run<ZEUS_OBJ_RASTRIGIN, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);
+            break;
+        case ZEUS_OBJ_ACKLEY:
+            wide_run<ZEUS_OBJ_ACKLEY, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);
+            break;
+        case ZEUS_OBJ_GOLDSTEIN_PRICE:
+            wide_run<ZEUS_OBJ_GOLDSTEIN_PRICE, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw,
+                                                        tid);
+            break;
+        default:
+            wide_run<ZEUS_OBJ_QUADRATIC, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);
+            break;
+    }
+}
+
+__device__ __forceinline__ RunIO batch_io(const BatchDev& bd, const zeus_problem& p, int P,
+                                          double* x_out, double* f_out, double* gnorm_out,
+                                          int32_t* status_out, int32_t* iters_out) {
+    const long long xo = bd.xoff[P], so = bd.soff[P];
+    const double* x0 = p.start_from_pbest ? bd.px + xo : x_out + xo;
+    return RunIO{x0,
+                 x_out + xo,
+                 f_out + so,
+                 gnorm_out ? gnorm_out + so : nullptr,
+                 status_out ? status_out + so : nullptr,
+                 iters_out ? iters_out + so : nullptr,
+                 bd.pctrl + P};
+}
+
+// Persistent blocks over work items [first, first + count) (cls >= 0) or
+// over the hand-over queue (cls < 0).  Item (P, s, c, 0): a tile of c
+// starts s.. of problem P, one lane each; item (P, s, W, 1): start s on the
+// whole block with W line-search trials at once.
+template <int GRAD, class T>
+__global__ void __launch_bounds__(kWideThreads)
+    batch_bfgs_kernel(const BatchDev bd, const int cls, const int first, const int count,
+                      double* x_out, double* __restrict__ f_out, double* __restrict__ gnorm_out,
+                      int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ WideShared sh;
+    const int tid = wide_role(blockDim.x);
+    unsigned* head = cls >= 0 ? bd.heads + cls : &bd.gctrl->q_head;
+    const int n_items =
+        cls >= 0 ? count
+                 : (int)min(*((volatile unsigned*)&bd.gctrl->q_count), (unsigned)bd.q.cap);
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sh.item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int item = sh.item;
+        if (item >= n_items) break;
+        if (cls >= 0) {
+            const int4 w = bd.items[first + item];
+            const int P = w.x;
+            const zeus_problem p = bd.probs[P];
+            const RunIO io = batch_io(bd, p, P, x_out, f_out, gnorm_out, status_out, iters_out);
+            if (w.w == 0) {
+                if ((int)threadIdx.x < w.z) {
+                    T* slot = reinterpret_cast<T*>(smem_raw) + (size_t)threadIdx.x * bd.stride[P];
+                    batch_narrow<GRAD, T>(p, P, (long long)w.y + threadIdx.x, slot, bd, io);
+                }
+            } else {
+                batch_wide<GRAD, T>(p, w.z, w.y, 0, 0, nullptr, nullptr, io, sh, smem_raw, tid);
+            }
+        } else {
+            const int P = bd.q.prob[item];
+            const zeus_problem p = bd.probs[P];
+            const RunIO io = batch_io(bd, p, P, x_out, f_out, gnorm_out, status_out, iters_out);
+            const long long s = bd.q.start[item];
+            const T* Hq = reinterpret_cast<const T*>(bd.q.H) + (size_t)item * bd.q.hstride;
+            const T* xq = reinterpret_cast<const T*>(io.x_out + s * p.dim);
+            batch_wide<GRAD, T>(p, wide_trials(p.dim, p.ls_max_iters), s, bd.q.k[item],
+                                bd.q.feval[item], Hq, xq, io, sh, smem_raw, tid);
+        }
+    }
+}
+
+template <int GRAD, class T>
+cudaError_t batch_launch_gt(const BatchDev& bd, int cls, int first, int count, size_t smem,
+                            double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
+                            int32_t* iters_out, cudaStream_t st) {
+    auto k = batch_bfgs_kernel<GRAD, T>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWideThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long blocks = (long long)sms * per_sm;
+    if (cls >= 0 && blocks > count) blocks = count;  // no block without an item
+    if (cls < 0 && blocks > bd.q.cap) blocks = bd.q.cap;
+    if (blocks < 1) return cudaSuccess;
+    k<<<(int)blocks, kWideThreads, smem, st>>>(bd, cls, first, count, x_out, f_out, gnorm_out,
+                                                status_out, iters_out);
+    return cudaGetLastError();
+}
+
+#if ZEUS_KF32
+template cudaError_t batch_launch_gt<ZEUS_KGRAD, float>(const BatchDev&, int, int, int, size_t,
+                                                        double*, double*, double*, int32_t*,
+                                                        int32_t*, cudaStream_t);
+#else
+template cudaError_t batch_launch_gt<ZEUS_KGRAD, double>(const BatchDev&, int, int, int, size_t,
+                                                         double*, double*, double*, int32_t*,
+                                                         int32_t*, cudaStream_t);
+#endif
+
+}  // namespace zeus

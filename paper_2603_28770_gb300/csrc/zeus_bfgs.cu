@@ -1,5 +1,6 @@
 // zeus_bfgs.cu -- one BFGS run per start (Alg. 4, per-thread body of
-// Alg. 10), FP64, in two kernels.
+// Alg. 10) in two kernels: launch planning here, the kernels in
+// zeus_bfgs_kernels.cu, the per-start bodies in zeus_bfgs.cuh.
 //
 // GB300 runs FP64 at one warp instruction per 64 cycles per SM
 // sub-partition whatever the number of active lanes, so FP64 throughput
@@ -34,646 +35,13 @@
 //   of the product update printed in Alg. 4).  The expanded form keeps H
 //   exactly symmetric (IEEE products and sums commute), so the narrow
 //   kernel computes the upper triangle and mirrors it.
-#include "zeus_device.cuh"
-#include "zeus_internal.h"
+#include "zeus_bfgs.cuh"
 
 namespace zeus {
 
 // ---------------------------------------------------------------------------
-// Objective value sweep in index order: init, term j, finish.  Coordinates
-// come through an accessor so the wide kernel can form a trial point
-// x + a p on the fly (the same bits as the materialised point).
-// ---------------------------------------------------------------------------
-template <class T>
-struct AtPoint {
-    const T* x;
-    __device__ __forceinline__ T operator()(int j) const { return x[j]; }
-};
-template <class T>
-struct AtTrial {
-    const T* x;
-    const T* p;
-    T a;
-    __device__ __forceinline__ T operator()(int j) const { return x[j] + a * p[j]; }
-};
-// FP32 coordinates read as FP64 (the final value of an FP32 run is an FP64
-// evaluation at its point)
-struct AtPromoted {
-    const float* x;
-    __device__ __forceinline__ double operator()(int j) const { return (double)x[j]; }
-};
-
-// The FP32 form evaluates Rastrigin as sum (x^2 + 20 sin^2(pi x)) and the
-// cosine mean of Ackley through 1 - (2/d) sum sin^2(pi x): the same
-// functions in exact arithmetic, without the cancellation that the literal
-// 10 d + sum(x^2 - 10 cos 2 pi x) suffers in FP32 near every integer point.
-template <class V>
-struct F32Terms {
-    static constexpr bool on = sizeof(V) == 4;
-};
-
-template <int OBJ, class T = double>
-__device__ __forceinline__ Part<double> val_init(int d) {
-    Part<double> a;
-    a.s0 = (OBJ == ZEUS_OBJ_RASTRIGIN && !F32Terms<T>::on) ? 10.0 * (double)d : 0.0;
-    a.s1 = 0.0;
-    return a;
-}
-
-template <int OBJ, class T = double>
-__device__ __forceinline__ double val_finish(const Part<double>& acc, int d) {
-    if (OBJ == ZEUS_OBJ_ACKLEY && F32Terms<T>::on) {
-        const double dd = (double)d;
-        const double t1 = -20.0 * exp_cw(-0.2 * sqrt(acc.s0 / dd));
-        const double t2 = exp_cw(1.0 - 2.0 * (acc.s1 / dd));
-        return (t1 - t2) + (20.0 + 2.718281828459045235360287471352);
-    }
-    return value_finish<OBJ, double>(acc, d);
-}
-
-template <int OBJ>
-__device__ __forceinline__ int val_nterms(int d) {
-    if (OBJ == ZEUS_OBJ_ROSENBROCK) return d - 1;
-    if (OBJ == ZEUS_OBJ_GOLDSTEIN_PRICE) return 1;
-    return d;
-}
-
-// term j of the sweep in the accessor's type V, returned as FP64 (the sums
-// of the FP32 form are FP64 sums of FP32 terms)
-template <int OBJ, class X>
-__device__ __forceinline__ void val_term(const X& xa, int j, double& t0, double& t1) {
-    using V = decltype(xa(0));
-    t1 = 0.0;
-    if (OBJ == ZEUS_OBJ_ROSENBROCK) {
-        const V xj = xa(j);
-        const V a = V(1) - xj;
-        const V b = xa(j + 1) - xj * xj;
-        t0 = (double)(a * a + V(100) * (b * b));
-    } else if (OBJ == ZEUS_OBJ_RASTRIGIN) {
-        const V xj = xa(j);
-        if (F32Terms<V>::on) {
-            const V sp = (V)sinpif((float)xj);
-            t0 = (double)(xj * xj + V(20) * (sp * sp));
-        } else {
-            t0 = (double)(xj * xj - V(10) * c_2pi(xj));
-        }
-    } else if (OBJ == ZEUS_OBJ_ACKLEY) {
-        const V xj = xa(j);
-        t0 = (double)(xj * xj);
-        if (F32Terms<V>::on) {
-            const V sp = (V)sinpif((float)xj);
-            t1 = (double)(sp * sp);
-        } else {
-            t1 = (double)c_2pi(xj);
-        }
-    } else if (OBJ == ZEUS_OBJ_GOLDSTEIN_PRICE) {
-        const V x1 = xa(0), x2 = xa(1);
-        const V t = (x1 + x2) + V(1);
-        const V pa = V(19) - V(14) * x1 + V(3) * (x1 * x1) - V(14) * x2 + V(6) * (x1 * x2) +
-                     V(3) * (x2 * x2);
-        const V a = V(1) + (t * t) * pa;
-        const V u = V(2) * x1 - V(3) * x2;
-        const V pb = V(18) - V(32) * x1 + V(12) * (x1 * x1) + V(48) * x2 - V(36) * (x1 * x2) +
-                     V(27) * (x2 * x2);
-        const V b = V(30) + (u * u) * pb;
-        t0 = (double)(a * b);
-    } else {
-        const V xj = xa(j);
-        t0 = (double)((V(0.5) * V(j + 1)) * (xj * xj));
-    }
-}
-
-template <int OBJ>
-__device__ __forceinline__ void val_add(Part<double>& acc, double t0, double t1) {
-    if (OBJ == ZEUS_OBJ_GOLDSTEIN_PRICE) {
-        acc.s0 = t0;
-    } else {
-        acc.s0 = acc.s0 + t0;
-        if (OBJ == ZEUS_OBJ_ACKLEY) acc.s1 = acc.s1 + t1;
-    }
-}
-
-// f at a point on one thread, index order (equals the oracle's sweep)
-template <int OBJ, class X>
-__device__ __forceinline__ double seq_value(const X& xa, int d) {
-    using V = decltype(xa(0));
-    Part<double> acc = val_init<OBJ, V>(d);
-    const int nt = val_nterms<OBJ>(d);
-    for (int j = 0; j < nt; ++j) {
-        double t0, t1;
-        val_term<OBJ>(xa, j, t0, t1);
-        val_add<OBJ>(acc, t0, t1);
-    }
-    return val_finish<OBJ, V>(acc, d);
-}
-
-// Gradient: forward pass i (Alg. 5) or adjoint component i.  The adjoint
-// first forms the quantities shared by all components (Ackley's two sums,
-// in index order) on one thread.
-template <int OBJ, int GRAD, class T>
-__device__ __forceinline__ AdjShared grad_prep(const T* x, int d) {
-    AdjShared a;
-    a.c1 = a.c2 = 0.0;
-    if (GRAD == ZEUS_GRAD_ADJOINT) a = adjoint_prep<OBJ>(x, d);
-    return a;
-}
-template <int OBJ, int GRAD, class T>
-__device__ __forceinline__ T grad_component(const T* x, int d, int i, const AdjShared& a) {
-    if (GRAD == ZEUS_GRAD_FORWARD) return forward_pass<OBJ, T>(x, d, i).b;
-    return adjoint_component<OBJ>(x, d, i, a);
-}
-
-// final f and its output: FP64 value at the point (FP32 points promoted)
-template <int OBJ>
-__device__ __forceinline__ double final_value(const double* x, int d, double f0) {
-    (void)x;
-    (void)d;
-    return f0;
-}
-template <int OBJ>
-__device__ __forceinline__ double final_value(const float* x, int d, double) {
-    return seq_value<OBJ>(AtPromoted{x}, d);
-}
-
-// ---------------------------------------------------------------------------
-// Narrow kernel: one lane per start.  T = double (the paper's FP64 method)
-// or float (the FP32 form: objective, gradient, H and the vectors in FP32;
-// y's, |s|^2, |y|^2, g'p, y'Hy, rho, the Armijo sums and the final f in
-// FP64).  With T = double every FP64 guard below is the plain FP64 operation.
-// Shared memory per start (T): H [d*d] | x | g | p | xn | gn | s
-// ---------------------------------------------------------------------------
-template <int OBJ, int GRAD, class T>
-__global__ void __launch_bounds__(kNarrowThreads)
-    bfgs_narrow_kernel(const zeus_problem p, const int stride, const int budget,
-                       const double* x0, double* x_out,  // may alias (in-place run)
-                       double* __restrict__ f_out, double* __restrict__ gnorm_out,
-                       int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
-                       Ctrl* __restrict__ ctrl, const Queue q) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* smem = reinterpret_cast<T*>(smem_raw);
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= p.n_starts) return;
-    const int d = p.dim;
-    T* H = smem + (size_t)threadIdx.x * stride;
-    T* x = H + (size_t)d * d;
-    T* g = x + d;
-    T* pv = g + d;
-    T* xn = pv + d;
-    T* gn = xn + d;
-    T* sv = gn + d;
-
-    const bool use_target = !isnan(p.target_f);
-    const bool use_stop = use_target || p.required_converged > 0;
-    const double tol = p.grad_tol, cA = p.armijo_c, beta = p.backtrack;
-    const int K = p.bfgs_max_iters, L = p.ls_max_iters;
-
-    for (int j = 0; j < d; ++j) x[j] = T(x0[s * d + j]);
-    for (int r = 0; r < d; ++r)
-        for (int c = 0; c < d; ++c) H[r * d + c] = (c == r) ? T(1) : T(0);
-    {
-        const AdjShared a = grad_prep<OBJ, GRAD>(x, d);
-        for (int i = 0; i < d; ++i) g[i] = grad_component<OBJ, GRAD>(x, d, i, a);
-    }
-    double f0 = seq_value<OBJ>(AtPoint<T>{x}, d);
-
-    int k = 0, status = ZEUS_RUN_MAX_ITER, feval = 0;
-    double gnorm;
-    for (;;) {
-        double gg = 0.0;
-        bool bad = false;
-        for (int j = 0; j < d; ++j) {
-            gg = gg + (double)(g[j] * g[j]);
-            bad |= !isfinite(g[j]);
-        }
-        gnorm = sqrt(gg);
-        if (k >= K) {
-            status = ZEUS_RUN_MAX_ITER;
-            break;
-        }
-        if (use_stop && *((volatile int*)&ctrl->stop)) {
-            status = ZEUS_RUN_STOPPED;
-            break;
-        }
-        if (!isfinite(f0) || bad) {
-            status = ZEUS_RUN_NONFINITE;
-            break;
-        }
-        if (gnorm < tol) {
-            status = ZEUS_RUN_CONVERGED;
-            if (use_stop) {
-                const unsigned long long c = atomicAdd(&ctrl->n_conv, 1ull) + 1ull;
-                if (p.required_converged > 0 && c >= (unsigned long long)p.required_converged)
-                    atomicExch(&ctrl->stop, 1);
-            }
-            break;
-        }
-        if (use_target && f0 <= p.target_f) {
-            status = ZEUS_RUN_CONVERGED;
-            atomicAdd(&ctrl->n_conv, 1ull);
-            atomicExch(&ctrl->stop, 1);
-            break;
-        }
-        if (budget > 0 && k + feval >= budget) {
-            // hand the start over to the wide kernel at the top of iteration k
-            const unsigned slot = atomicAdd(&ctrl->q_count, 1u);
-            if (slot < (unsigned)q.cap) {
-                q.start[slot] = (int)s;
-                q.k[slot] = k;
-                q.feval[slot] = feval;
-                T* Hq = reinterpret_cast<T*>(q.H) + (size_t)slot * d * d;
-                for (int e = 0; e < d * d; ++e) Hq[e] = H[e];
-                T* xq = reinterpret_cast<T*>(x_out + s * d);  // the row holds x until the end
-                for (int j = 0; j < d; ++j) xq[j] = x[j];
-                return;
-            }
-        }
-        // direction p = -H g and ddir = g'p
-        for (int r = 0; r < d; ++r) {
-            const T* Hr = H + r * d;
-            T a = T(0);
-            for (int c = 0; c < d; ++c) a = a + Hr[c] * g[c];
-            pv[r] = -a;
-        }
-        double ddir = 0.0;
-        for (int r = 0; r < d; ++r) ddir = ddir + (double)(g[r] * pv[r]);
-        if (!(ddir < 0.0)) {  // not a descent direction: restart from H = I
-            for (int r = 0; r < d; ++r)
-                for (int c = 0; c < d; ++c) H[r * d + c] = (c == r) ? T(1) : T(0);
-            for (int r = 0; r < d; ++r) pv[r] = -g[r];
-            ddir = 0.0;
-            for (int r = 0; r < d; ++r) ddir = ddir + (double)(g[r] * pv[r]);
-        }
-        // backtracking Armijo line search (Alg. 6)
-        double alpha = 1.0, fn = 0.0;
-        bool accepted = false;
-        for (int m = 0; m < L; ++m) {
-            const T a = T(alpha);
-            for (int j = 0; j < d; ++j) xn[j] = x[j] + a * pv[j];
-            fn = seq_value<OBJ>(AtPoint<T>{xn}, d);
-            ++feval;
-            if (fn <= f0 + cA * alpha * ddir) {
-                accepted = true;
-                break;
-            }
-            alpha = beta * alpha;
-        }
-        if (!accepted) {  // Alg. 6 returns the step after the last halving
-            const T a = T(alpha);
-            for (int j = 0; j < d; ++j) xn[j] = x[j] + a * pv[j];
-            fn = seq_value<OBJ>(AtPoint<T>{xn}, d);
-        }
-        {
-            const AdjShared a = grad_prep<OBJ, GRAD>(xn, d);
-            for (int i = 0; i < d; ++i) gn[i] = grad_component<OBJ, GRAD>(xn, d, i, a);
-        }
-        // curvature pair
-        double sy = 0.0, ss = 0.0, yy = 0.0;
-        for (int j = 0; j < d; ++j) {  // s into sv, y over g (g is not needed again)
-            const T sj = xn[j] - x[j], yj = gn[j] - g[j];
-            sv[j] = sj;
-            g[j] = yj;
-            sy = sy + (double)(yj * sj);
-            ss = ss + (double)(sj * sj);
-            yy = yy + (double)(yj * yj);
-        }
-        if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
-            const double rho = 1.0 / sy;
-            for (int r = 0; r < d; ++r) {  // Hy into p (the direction is spent)
-                const T* Hr = H + r * d;
-                T a = T(0);
-                for (int c = 0; c < d; ++c) a = a + Hr[c] * g[c];
-                pv[r] = a;
-            }
-            double yhy = 0.0;
-            for (int r = 0; r < d; ++r) yhy = yhy + (double)(g[r] * pv[r]);
-            const double b2 = rho * rho * yhy + rho;
-            const T rt = T(rho), bt = T(b2);
-            for (int r = 0; r < d; ++r) {
-                const T sr = sv[r], hr = pv[r];
-                for (int c = r; c < d; ++c) {
-                    const T sc = sv[c];
-                    const T h = H[r * d + c] - rt * (hr * sc + sr * pv[c]) + bt * (sr * sc);
-                    H[r * d + c] = h;
-                    H[c * d + r] = h;
-                }
-            }
-        }
-        for (int j = 0; j < d; ++j) {
-            x[j] = xn[j];
-            g[j] = gn[j];
-        }
-        f0 = fn;
-        ++k;
-    }
-
-    const double ffin = final_value<OBJ>(x, d, f0);
-    for (int j = 0; j < d; ++j) x_out[s * d + j] = (double)x[j];
-    if (f_out) f_out[s] = ffin;
-    if (gnorm_out) gnorm_out[s] = gnorm;
-    if (status_out) status_out[s] = status;
-    if (iters_out) iters_out[s] = k;
-    atomicAdd(&ctrl->total_iters, (unsigned long long)k);
-    atomicAdd(&ctrl->total_feval, (unsigned long long)feval);
-    if (!use_stop && status == ZEUS_RUN_CONVERGED) atomicAdd(&ctrl->n_conv, 1ull);
-}
-
-// ---------------------------------------------------------------------------
-// Wide kernel: one CTA per start, persistent over a queue of starts.
-// Shared memory: T region H [d*d] | x | g | p | xn | gn | s, then an FP64
-// region scratch [3 d] | trial terms [W][d] x 2 | trial f [W] | alpha [L+1]
-// ---------------------------------------------------------------------------
-struct WideShared {
-    int item;
-    int status;
-    int accepted_m;
-    int pad;
-    double red[4];
-    AdjShared adj;
-    int ok[64];
-};
-
-// left-to-right sum of v[0..n) starting from init, on the calling thread
-__device__ __forceinline__ double ordered_sum(const double* v, int n, double init) {
-    double s = init;
-    for (int j = 0; j < n; ++j) s = s + v[j];
-    return s;
-}
-
-template <int OBJ, int GRAD, class T>
-__device__ __forceinline__ void wide_gradient(const T* x, T* g, int d, int tid, WideShared& sh) {
-    const int NT = blockDim.x;
-    if (GRAD == ZEUS_GRAD_ADJOINT) {
-        if (tid == 0) sh.adj = adjoint_prep<OBJ>(x, d);
-        __syncthreads();
-    }
-    const AdjShared a = sh.adj;
-    for (int i = tid; i < d; i += NT) g[i] = grad_component<OBJ, GRAD>(x, d, i, a);
-}
-
-__host__ __device__ __forceinline__ size_t wide_t_bytes(int d, size_t tsize) {
-    return (((size_t)d * d + 6 * (size_t)d) * tsize + 7) & ~size_t(7);
-}
-
-template <int OBJ, int GRAD, class T>
-__global__ void __launch_bounds__(kWideThreads)
-    bfgs_wide_kernel(const zeus_problem p, const int W, const double* x0, double* x_out,
-                     double* __restrict__ f_out, double* __restrict__ gnorm_out,
-                     int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
-                     Ctrl* __restrict__ ctrl, const Queue q, const int all_starts) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ WideShared sh;
-    const int NT = blockDim.x;
-    // Roles rotate with the block index so that the thread doing the serial
-    // work (ordered sums, tests) sits in a different warp, hence on a
-    // different SM sub-partition, in each of the blocks sharing an SM.
-    const int lead = (32 * (int)blockIdx.x) % NT;
-    const int tid = (threadIdx.x + NT - lead) % NT;
-    const int d = p.dim;
-    T* H = reinterpret_cast<T*>(smem_raw);
-    T* x = H + (size_t)d * d;
-    T* g = x + d;
-    T* pv = g + d;
-    T* xn = pv + d;
-    T* gn = xn + d;
-    T* sv = gn + d;
-    double* sc0 = reinterpret_cast<double*>(smem_raw + wide_t_bytes(d, sizeof(T)));
-    double* sc1 = sc0 + d;  // three FP64 scratch vectors
-    double* sc2 = sc1 + d;
-    double* tb0 = sc2 + d;              // [W][d]
-    double* tb1 = tb0 + (size_t)W * d;  // [W][d] (second sum of Ackley)
-    double* fb = tb1 + (size_t)W * d;   // [W]
-    double* al = fb + W;                // [L + 1]
-
-    const bool use_target = !isnan(p.target_f);
-    const bool use_stop = use_target || p.required_converged > 0;
-    const double tol = p.grad_tol, cA = p.armijo_c, beta = p.backtrack;
-    const int K = p.bfgs_max_iters, L = p.ls_max_iters;
-    const int nt = val_nterms<OBJ>(d);
-
-    if (tid == 0) {  // alpha_m = beta^m by repeated multiplication, as the sequential search
-        double a = 1.0;
-        for (int m = 0; m <= L; ++m) {
-            al[m] = a;
-            a = beta * a;
-        }
-        sh.adj.c1 = sh.adj.c2 = 0.0;
-    }
-
-    const long long n_items =
-        all_starts ? p.n_starts
-                   : (long long)min(*((volatile unsigned*)&ctrl->q_count), (unsigned)q.cap);
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) sh.item = (int)atomicAdd(&ctrl->q_head, 1u);
-        __syncthreads();
-        const long long item = sh.item;
-        if (item >= n_items) break;
-        const long long s = all_starts ? item : q.start[item];
-        int k = all_starts ? 0 : q.k[item];
-        int feval = all_starts ? 0 : q.feval[item];
-        if (all_starts) {
-            for (int j = tid; j < d; j += NT) x[j] = T(x0[s * d + j]);
-            for (int e = tid; e < d * d; e += NT) H[e] = (e / d == e % d) ? T(1) : T(0);
-        } else {
-            const T* xq = reinterpret_cast<const T*>(x_out + s * d);
-            for (int j = tid; j < d; j += NT) x[j] = xq[j];
-            const T* Hq = reinterpret_cast<const T*>(q.H) + (size_t)item * d * d;
-            for (int e = tid; e < d * d; e += NT) H[e] = Hq[e];
-        }
-        __syncthreads();
-        wide_gradient<OBJ, GRAD>(x, g, d, tid, sh);
-        if (tid == 0) sh.red[0] = seq_value<OBJ>(AtPoint<T>{x}, d);
-        __syncthreads();
-        double f0 = sh.red[0];
-        int status = ZEUS_RUN_MAX_ITER;
-        double gnorm = 0.0;
-        for (;;) {
-            // ---- tests at the top of iteration k
-            int b = 0;
-            for (int j = tid; j < d; j += NT) {
-                sc0[j] = (double)(g[j] * g[j]);
-                b |= !isfinite(g[j]);
-            }
-            const int bad = __syncthreads_or(b);
-            if (tid == 0) {
-                gnorm = sqrt(ordered_sum(sc0, d, 0.0));
-                sh.red[1] = gnorm;
-                int st = -1;
-                if (k >= K) {
-                    st = ZEUS_RUN_MAX_ITER;
-                } else if (use_stop && *((volatile int*)&ctrl->stop)) {
-                    st = ZEUS_RUN_STOPPED;
-                } else if (!isfinite(f0) || bad) {
-                    st = ZEUS_RUN_NONFINITE;
-                } else if (gnorm < tol) {
-                    st = ZEUS_RUN_CONVERGED;
-                    if (use_stop) {
-                        const unsigned long long c = atomicAdd(&ctrl->n_conv, 1ull) + 1ull;
-                        if (p.required_converged > 0 &&
-                            c >= (unsigned long long)p.required_converged)
-                            atomicExch(&ctrl->stop, 1);
-                    }
-                } else if (use_target && f0 <= p.target_f) {
-                    st = ZEUS_RUN_CONVERGED;
-                    atomicAdd(&ctrl->n_conv, 1ull);
-                    atomicExch(&ctrl->stop, 1);
-                }
-                sh.status = st;
-            }
-            __syncthreads();
-            gnorm = sh.red[1];
-            if (sh.status >= 0) {
-                status = sh.status;
-                break;
-            }
-            // ---- direction p = -H g (one row per thread, columns in order)
-            for (int r = tid; r < d; r += NT) {
-                const T* Hr = H + r * d;
-                T a = T(0);
-                for (int c = 0; c < d; ++c) a = a + Hr[c] * g[c];
-                pv[r] = -a;
-                sc0[r] = (double)(g[r] * (-a));
-            }
-            __syncthreads();
-            if (tid == 0) sh.red[0] = ordered_sum(sc0, d, 0.0);
-            __syncthreads();
-            double ddir = sh.red[0];
-            if (!(ddir < 0.0)) {  // not a descent direction: restart from H = I
-                __syncthreads();
-                for (int e = tid; e < d * d; e += NT) H[e] = (e / d == e % d) ? T(1) : T(0);
-                for (int r = tid; r < d; r += NT) {
-                    pv[r] = -g[r];
-                    sc0[r] = (double)(g[r] * (-g[r]));
-                }
-                __syncthreads();
-                if (tid == 0) sh.red[0] = ordered_sum(sc0, d, 0.0);
-                __syncthreads();
-                ddir = sh.red[0];
-            }
-            // ---- line search: W trials at a time, the first accepted wins
-            int acc_m = -1;
-            double fn = 0.0;
-            for (int m0 = 0; m0 < L && acc_m < 0; m0 += W) {
-                const int nw = min(W, L - m0);
-                for (int e = tid; e < nw * nt; e += NT) {
-                    const int mm = e / nt, j = e - mm * nt;
-                    double t0, t1;
-                    val_term<OBJ>(AtTrial<T>{x, pv, T(al[m0 + mm])}, j, t0, t1);
-                    tb0[mm * d + j] = t0;
-                    tb1[mm * d + j] = t1;
-                }
-                __syncthreads();
-                if (tid < nw) {  // one thread per trial: its terms in order, then the test
-                    Part<double> acc = val_init<OBJ, T>(d);
-                    for (int j = 0; j < nt; ++j)
-                        val_add<OBJ>(acc, tb0[tid * d + j], tb1[tid * d + j]);
-                    const double ft = val_finish<OBJ, T>(acc, d);
-                    fb[tid] = ft;
-                    sh.ok[tid] = (ft <= f0 + cA * al[m0 + tid] * ddir) ? 1 : 0;
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    int am = -1;
-                    for (int mm = 0; mm < nw; ++mm)
-                        if (sh.ok[mm]) {
-                            am = m0 + mm;
-                            break;
-                        }
-                    sh.accepted_m = am;
-                    if (am >= 0) sh.red[2] = fb[am - m0];
-                }
-                __syncthreads();
-                acc_m = sh.accepted_m;
-                feval += (acc_m >= 0) ? (acc_m - m0 + 1) : nw;
-            }
-            const T alpha = T((acc_m >= 0) ? al[acc_m] : al[L]);
-            for (int j = tid; j < d; j += NT) xn[j] = x[j] + alpha * pv[j];
-            __syncthreads();
-            if (acc_m < 0 && tid == 0) sh.red[2] = seq_value<OBJ>(AtPoint<T>{xn}, d);
-            // ---- gradient at x_new
-            wide_gradient<OBJ, GRAD>(xn, gn, d, tid, sh);
-            __syncthreads();
-            fn = sh.red[2];
-            // ---- curvature pair
-            for (int j = tid; j < d; j += NT) {  // s into sv, y over g
-                const T sj = xn[j] - x[j], yj = gn[j] - g[j];
-                sv[j] = sj;
-                g[j] = yj;
-                sc0[j] = (double)(yj * sj);
-                sc1[j] = (double)(sj * sj);
-                sc2[j] = (double)(yj * yj);
-            }
-            __syncthreads();
-            if (tid < 3) sh.red[tid] = ordered_sum(tid == 0 ? sc0 : (tid == 1 ? sc1 : sc2), d, 0.0);
-            __syncthreads();
-            const double sy = sh.red[0], ss = sh.red[1], yy = sh.red[2];
-            if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
-                const double rho = 1.0 / sy;
-                __syncthreads();
-                for (int r = tid; r < d; r += NT) {  // Hy into p (the direction is spent)
-                    const T* Hr = H + r * d;
-                    T a = T(0);
-                    for (int c = 0; c < d; ++c) a = a + Hr[c] * g[c];
-                    pv[r] = a;
-                    sc0[r] = (double)(g[r] * a);
-                }
-                __syncthreads();
-                if (tid == 0) sh.red[3] = ordered_sum(sc0, d, 0.0);
-                __syncthreads();
-                const double b2 = rho * rho * sh.red[3] + rho;
-                const T rt = T(rho), bt = T(b2);
-                for (int e = tid; e < d * d; e += NT) {
-                    const int r = e / d, c = e - r * d;
-                    const T sr = sv[r], sc = sv[c];
-                    H[e] = H[e] - rt * (pv[r] * sc + sr * pv[c]) + bt * (sr * sc);
-                }
-            }
-            __syncthreads();
-            for (int j = tid; j < d; j += NT) {
-                x[j] = xn[j];
-                g[j] = gn[j];
-            }
-            f0 = fn;
-            ++k;
-            __syncthreads();
-        }
-        if (tid == 0) sh.red[0] = final_value<OBJ>(x, d, f0);
-        __syncthreads();
-        for (int j = tid; j < d; j += NT) x_out[s * d + j] = (double)x[j];
-        if (tid == 0) {
-            if (f_out) f_out[s] = sh.red[0];
-            if (gnorm_out) gnorm_out[s] = gnorm;
-            if (status_out) status_out[s] = status;
-            if (iters_out) iters_out[s] = k;
-            atomicAdd(&ctrl->total_iters, (unsigned long long)k);
-            atomicAdd(&ctrl->total_feval, (unsigned long long)feval);
-            if (!use_stop && status == ZEUS_RUN_CONVERGED) atomicAdd(&ctrl->n_conv, 1ull);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Launch planning
 // ---------------------------------------------------------------------------
-static size_t narrow_stride(int d) {
-    size_t st = (size_t)d * d + 6 * (size_t)d;
-    if ((st & 1) == 0) st += 1;  // odd: the 32 starts of a warp fall in distinct banks
-    return st;
-}
-
-static int wide_trials(int d, int L) {
-    int W = (2 * kWideThreads) / (d > 0 ? d : 1);
-    if (W < 1) W = 1;
-    if (W > 64) W = 64;
-    if (W > L) W = L;
-    return W;
-}
-
-static size_t wide_smem(int d, int W, int L, size_t tsize) {
-    return wide_t_bytes(d, tsize) +
-           sizeof(double) * (3 * (size_t)d + 2 * (size_t)W * d + W + L + 1);
-}
-
 int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
     const int d = p.dim;
     const size_t cap = 227 * 1024;
@@ -716,70 +84,22 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
     return ZEUS_OK;
 }
 
-template <int OBJ, int GRAD, class T>
-static cudaError_t bfgs_go(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
-                           double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
-                           int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st) {
-    cudaError_t e;
-    if (L.narrow) {
-        auto kn = bfgs_narrow_kernel<OBJ, GRAD, T>;
-        e = cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.narrow_smem);
-        if (e != cudaSuccess) return e;
-        kn<<<L.narrow_blocks, L.narrow_threads, L.narrow_smem, st>>>(
-            p, L.stride, L.budget, x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl, q);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        if (L.budget == 0) return cudaSuccess;
-    }
-    auto kw = bfgs_wide_kernel<OBJ, GRAD, T>;
-    e = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.wide_smem);
-    if (e != cudaSuccess) return e;
-    kw<<<L.wide_blocks, kWideThreads, L.wide_smem, st>>>(p, L.W, x0, x_out, f_out, gnorm_out,
-                                                         status_out, iters_out, ctrl, q,
-                                                         L.narrow ? 0 : 1);
-    return cudaGetLastError();
-}
-
-template <int OBJ>
-static cudaError_t bfgs_obj(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
-                            double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
-                            int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st) {
-    const bool f32 = p.precision == ZEUS_FP32_GUARDED;
-    if (p.grad_mode == ZEUS_GRAD_ADJOINT)
-        return f32 ? bfgs_go<OBJ, ZEUS_GRAD_ADJOINT, float>(p, L, x0, x_out, f_out, gnorm_out,
-                                                            status_out, iters_out, ctrl, q, st)
-                   : bfgs_go<OBJ, ZEUS_GRAD_ADJOINT, double>(p, L, x0, x_out, f_out, gnorm_out,
-                                                             status_out, iters_out, ctrl, q, st);
-    return f32 ? bfgs_go<OBJ, ZEUS_GRAD_FORWARD, float>(p, L, x0, x_out, f_out, gnorm_out,
-                                                        status_out, iters_out, ctrl, q, st)
-               : bfgs_go<OBJ, ZEUS_GRAD_FORWARD, double>(p, L, x0, x_out, f_out, gnorm_out,
-                                                         status_out, iters_out, ctrl, q, st);
-}
-
 cudaError_t launch_bfgs(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
                         double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
                         int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st) {
     if (L.stream)
         return launch_bfgs_stream(p, x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl,
                                   q.hslots, st);
-    switch (p.objective) {
-        case ZEUS_OBJ_ROSENBROCK:
-            return bfgs_obj<ZEUS_OBJ_ROSENBROCK>(p, L, x0, x_out, f_out, gnorm_out, status_out,
-                                                 iters_out, ctrl, q, st);
-        case ZEUS_OBJ_RASTRIGIN:
-            return bfgs_obj<ZEUS_OBJ_RASTRIGIN>(p, L, x0, x_out, f_out, gnorm_out, status_out,
-                                                iters_out, ctrl, q, st);
-        case ZEUS_OBJ_ACKLEY:
-            return bfgs_obj<ZEUS_OBJ_ACKLEY>(p, L, x0, x_out, f_out, gnorm_out, status_out,
-                                             iters_out, ctrl, q, st);
-        case ZEUS_OBJ_GOLDSTEIN_PRICE:
-            return bfgs_obj<ZEUS_OBJ_GOLDSTEIN_PRICE>(p, L, x0, x_out, f_out, gnorm_out,
-                                                      status_out, iters_out, ctrl, q, st);
-        default:
-            return bfgs_obj<ZEUS_OBJ_QUADRATIC>(p, L, x0, x_out, f_out, gnorm_out, status_out,
-                                                iters_out, ctrl, q, st);
-    }
+    const bool f32 = p.precision == ZEUS_FP32_GUARDED;
+    if (p.grad_mode == ZEUS_GRAD_ADJOINT)
+        return f32 ? bfgs_launch_gt<ZEUS_GRAD_ADJOINT, float>(p, L, x0, x_out, f_out, gnorm_out,
+                                                              status_out, iters_out, ctrl, q, st)
+                   : bfgs_launch_gt<ZEUS_GRAD_ADJOINT, double>(p, L, x0, x_out, f_out, gnorm_out,
+                                                               status_out, iters_out, ctrl, q, st);
+    return f32 ? bfgs_launch_gt<ZEUS_GRAD_FORWARD, float>(p, L, x0, x_out, f_out, gnorm_out,
+                                                          status_out, iters_out, ctrl, q, st)
+               : bfgs_launch_gt<ZEUS_GRAD_FORWARD, double>(p, L, x0, x_out, f_out, gnorm_out,
+                                                           status_out, iters_out, ctrl, q, st);
 }
 
 }  // namespace zeus

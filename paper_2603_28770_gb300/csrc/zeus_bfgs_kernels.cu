@@ -1,0 +1,119 @@
+// zeus_bfgs_kernels.cu -- the narrow and wide BFGS kernels of zeus_bfgs.cu
+// for one (gradient mode, precision) pair, chosen at compile time by
+// ZEUS_KGRAD (0 forward, 1 adjoint) and ZEUS_KF32 (0 FP64, 1 FP32 with FP64
+// guards): the library compiles this file once per pair, in parallel.
+#include "zeus_bfgs.cuh"
+
+#if !defined(ZEUS_KGRAD) || !defined(ZEUS_KF32)
+#error "compile with -DZEUS_KGRAD=0|1 -DZEUS_KF32=0|1"
+#endif
+
+namespace zeus {
+
+template <int OBJ, int GRAD, class T>
+__global__ void __launch_bounds__(kNarrowThreads)
+    bfgs_narrow_kernel(const zeus_problem p, const int stride, const int budget,
+                       const double* x0, double* x_out,  // may alias (in-place run)
+                       double* __restrict__ f_out, double* __restrict__ gnorm_out,
+                       int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
+                       Ctrl* __restrict__ ctrl, const Queue q) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* smem = reinterpret_cast<T*>(smem_raw);
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= p.n_starts) return;
+    const RunIO io{x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl};
+    narrow_run<OBJ, GRAD, T>(p, s, smem + (size_t)threadIdx.x * stride, budget, io, ctrl, q, 0);
+}
+
+template <int OBJ, int GRAD, class T>
+__global__ void __launch_bounds__(kWideThreads)
+    bfgs_wide_kernel(const zeus_problem p, const int W, const double* x0, double* x_out,
+                     double* __restrict__ f_out, double* __restrict__ gnorm_out,
+                     int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
+                     Ctrl* __restrict__ ctrl, const Queue q, const int all_starts) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ WideShared sh;
+    const int tid = wide_role(blockDim.x);
+    const RunIO io{x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl};
+    const long long n_items =
+        all_starts ? p.n_starts
+                   : (long long)min(*((volatile unsigned*)&ctrl->q_count), (unsigned)q.cap);
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sh.item = (int)atomicAdd(&ctrl->q_head, 1u);
+        __syncthreads();
+        const long long item = sh.item;
+        if (item >= n_items) break;
+        if (all_starts) {
+            wide_run<OBJ, GRAD, T>(p, W, item, 0, 0, nullptr, nullptr, io, sh, smem_raw, tid);
+        } else {
+            const long long s = q.start[item];
+            const T* Hq = reinterpret_cast<const T*>(q.H) + (size_t)item * p.dim * p.dim;
+            const T* xq = reinterpret_cast<const T*>(x_out + s * p.dim);
+            wide_run<OBJ, GRAD, T>(p, W, s, q.k[item], q.feval[item], Hq, xq, io, sh, smem_raw,
+                                   tid);
+        }
+    }
+}
+
+template <int OBJ, int GRAD, class T>
+static cudaError_t bfgs_go(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
+                           double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
+                           int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st) {
+    cudaError_t e;
+    if (L.narrow) {
+        auto kn = bfgs_narrow_kernel<OBJ, GRAD, T>;
+        e = cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)L.narrow_smem);
+        if (e != cudaSuccess) return e;
+        kn<<<L.narrow_blocks, L.narrow_threads, L.narrow_smem, st>>>(
+            p, L.stride, L.budget, x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl, q);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (L.budget == 0) return cudaSuccess;
+    }
+    auto kw = bfgs_wide_kernel<OBJ, GRAD, T>;
+    e = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.wide_smem);
+    if (e != cudaSuccess) return e;
+    kw<<<L.wide_blocks, kWideThreads, L.wide_smem, st>>>(p, L.W, x0, x_out, f_out, gnorm_out,
+                                                         status_out, iters_out, ctrl, q,
+                                                         L.narrow ? 0 : 1);
+    return cudaGetLastError();
+}
+
+template <int GRAD, class T>
+cudaError_t bfgs_launch_gt(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
+                           double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
+                           int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st) {
+    switch (p.objective) {
+        case ZEUS_OBJ_ROSENBROCK:
+            return bfgs_go<ZEUS_OBJ_ROSENBROCK, GRAD, T>(p, L, x0, x_out, f_out, gnorm_out,
+                                                         status_out, iters_out, ctrl, q, st);
+        case ZEUS_OBJ_RASTRIGIN:
+            return bfgs_go<ZEUS_OBJ_RASTRIGIN, GRAD, T>(p, L, x0, x_out, f_out, gnorm_out,
+                                                        status_out, iters_out, ctrl, q, st);
+        case ZEUS_OBJ_ACKLEY:
+            return bfgs_go<ZEUS_OBJ_ACKLEY, GRAD, T>(p, L, x0, x_out, f_out, gnorm_out,
+                                                     status_out, iters_out, ctrl, q, st);
+        case ZEUS_OBJ_GOLDSTEIN_PRICE:
+            return bfgs_go<ZEUS_OBJ_GOLDSTEIN_PRICE, GRAD, T>(p, L, x0, x_out, f_out, gnorm_out,
+                                                              status_out, iters_out, ctrl, q, st);
+        default:
+            return bfgs_go<ZEUS_OBJ_QUADRATIC, GRAD, T>(p, L, x0, x_out, f_out, gnorm_out,
+                                                        status_out, iters_out, ctrl, q, st);
+    }
+}
+
+#if ZEUS_KF32
+template cudaError_t bfgs_launch_gt<ZEUS_KGRAD, float>(const zeus_problem&, const BfgsLaunch&,
+                                                       const double*, double*, double*, double*,
+                                                       int32_t*, int32_t*, Ctrl*, const Queue&,
+                                                       cudaStream_t);
+#else
+template cudaError_t bfgs_launch_gt<ZEUS_KGRAD, double>(const zeus_problem&, const BfgsLaunch&,
+                                                        const double*, double*, double*, double*,
+                                                        int32_t*, int32_t*, Ctrl*, const Queue&,
+                                                        cudaStream_t);
+#endif
+
+}  // namespace zeus

@@ -105,6 +105,7 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? ZEUS_OK : ZEUS_ECUDA;
 
 Queue queue_for(void* ws, const Layout& lay, const BfgsLaunch& L) {
     Queue q;
+    q.prob = nullptr;
     q.start = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + lay.q_start);
     q.k = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + lay.q_k);
     q.feval = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + lay.q_feval);

@@ -44,14 +44,28 @@ struct Layout {
     size_t ctrl, partials, f_tmp, v, px, pf, gx, q_start, q_k, q_feval, q_h, hslots, total;
 };
 
+// Per-problem inputs and outputs of a BFGS run (pointers already offset to
+// the problem's rows) and its counters.
+struct RunIO {
+    const double* x0;
+    double* x_out;
+    double* f_out;
+    double* gnorm_out;
+    int32_t* status_out;
+    int32_t* iters_out;
+    Ctrl* pc;
+};
+
 // Hand-over queue from the narrow to the wide BFGS kernel (workspace).
 struct Queue {
+    int* prob;    // [cap] problem index (batched runs; nullptr otherwise)
     int* start;   // [cap] start index
     int* k;       // [cap] iteration at hand-over
     int* feval;   // [cap] line-search evaluations so far
     double* H;    // [cap][d*d] inverse-Hessian approximation
     int cap;
     void* hslots; // H slots of the streaming kernel
+    long long hstride = 0;  // elements per H entry (0: d*d of the run's problem)
 };
 
 constexpr int kNarrowThreads = 128;
@@ -75,6 +89,34 @@ struct BfgsLaunch {
     size_t hslot_bytes;   // bytes of all H slots
 };
 
+// Device tables of a batch (zeus_batch_*): per-problem parameters and
+// offsets into the concatenated outputs, the PSO block table and the BFGS
+// work list.  All pointers address the workspace.
+struct BatchDev {
+    const zeus_problem* probs;
+    const long long* xoff;   // first coordinate of problem P in x_out
+    const long long* soff;   // first start of problem P in f_out / status / iters
+    const long long* goff;   // its global best position in gx
+    const long long* poff;   // its PSO partials
+    const int* pblk0;        // its first PSO block
+    const int* pblk;         // its number of PSO blocks
+    const int* plane;        // PSO lanes per particle
+    const int* pso_table;    // problem of each PSO block
+    const int4* items;       // BFGS work: (problem, first start, count or W, mode 0 lane/1 block)
+    const int* stride;       // one-lane layout stride per problem
+    const int* budget;       // hand-over budget per problem (0 = none)
+    Ctrl* pctrl;             // [n] per-problem counters, stop flag, global best
+    Ctrl* gctrl;             // [1] hand-over queue counters
+    unsigned* heads;         // [ZEUS_BATCH_MAX_CLASSES] next work item of each class launch
+    ArgPair* partials;
+    double* v;
+    double* px;
+    double* pf;
+    double* gx;
+    Queue q;
+    int n, n_items, pso_blocks;
+};
+
 // ---- launchers (defined in the kernel translation units) ----
 // lanes per particle of the PSO and objective kernels: one lane (sums in
 // index order) up to d = 64, a warp above
@@ -95,6 +137,27 @@ int stream_blocks(const zeus_problem& p);
 cudaError_t launch_bfgs_stream(const zeus_problem& p, const double* x0, double* x_out,
                                double* f_out, double* gnorm_out, int32_t* status_out,
                                int32_t* iters_out, Ctrl* ctrl, void* hslots, cudaStream_t st);
+
+cudaError_t launch_batch_pso(const BatchDev& bd, int t, double* x_out, cudaStream_t st);
+cudaError_t launch_batch_argmin(const BatchDev& bd, const double* f_out, zeus_result* res,
+                                cudaStream_t st);
+// one persistent launch over work items [first, first + count) with class
+// counter `cls`; cls < 0: the hand-over queue
+cudaError_t launch_batch_bfgs(const BatchDev& bd, int precision, int grad_mode, int cls,
+                              int first, int count, size_t smem, double* x_out, double* f_out,
+                              double* gnorm_out, int32_t* status_out, int32_t* iters_out,
+                              cudaStream_t st);
+
+// the kernels of one (gradient mode, precision) pair, compiled in a
+// translation unit of their own (zeus_bfgs_kernels.cu, zeus_batch_kernels.cu)
+template <int GRAD, class T>
+cudaError_t bfgs_launch_gt(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
+                           double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
+                           int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st);
+template <int GRAD, class T>
+cudaError_t batch_launch_gt(const BatchDev& bd, int cls, int first, int count, size_t smem,
+                            double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
+                            int32_t* iters_out, cudaStream_t st);
 
 cudaError_t launch_argmin(const double* f, long long n, Ctrl* ctrl, ArgPair* partials,
                           zeus_result* res, int mode, cudaStream_t st);

@@ -70,6 +70,7 @@ extern "C" int zeus_solve_from_noalloc(const zeus_problem* p, const double* x0, 
     char* b = static_cast<char*>(base);
     const size_t qc = (size_t)L.q_cap;
     Queue q;
+    q.prob = nullptr;
     q.start = reinterpret_cast<int*>(b + off_queue);
     q.k = reinterpret_cast<int*>(b + off_queue + align256(qc * sizeof(int)));
     q.feval = reinterpret_cast<int*>(b + off_queue + 2 * align256(qc * sizeof(int)));

@@ -24,19 +24,20 @@ __device__ __forceinline__ double group_value(const double* x, int d, const Grou
     return value_finish<OBJ, double>(p, d);
 }
 
-// t < 0: initialisation (Alg. 2); t >= 0: PSO update number t (Alg. 3).
+// One block of PSO particles (Alg. 2 for t < 0, Alg. 3 update number t
+// otherwise): `block` of `nblocks` blocks of this problem; the last block of
+// the problem to finish reduces the personal bests to the global best.
 template <int OBJ>
-__global__ void __launch_bounds__(kPsoThreads)
-    pso_kernel(const zeus_problem p, const int t, const int G, double* __restrict__ x,
-               double* __restrict__ v, double* __restrict__ px, double* __restrict__ pf,
-               double* __restrict__ gx, Ctrl* __restrict__ ctrl, ArgPair* __restrict__ partials,
-               zeus_result* __restrict__ res) {
+__device__ __forceinline__ void pso_block(const zeus_problem& p, const int t, const int G,
+                                          const int block, const int nblocks, double* x,
+                                          double* v, double* px, double* pf, double* gx,
+                                          Ctrl* ctrl, ArgPair* partials, zeus_result* res) {
     __shared__ ArgPair scratch[32];
     __shared__ int s_last;
     const Group grp(G);
     const int d = p.dim;
     const int S = kPsoThreads / G;
-    const long long i = (long long)blockIdx.x * S + threadIdx.x / G;
+    const long long i = (long long)block * S + threadIdx.x / G;
     double fbest = CUDART_INF;
     long long ibest = 0x7fffffffffffffffll;
     if (i < p.n_starts) {
@@ -99,10 +100,10 @@ __global__ void __launch_bounds__(kPsoThreads)
         ibest = i;
     }
     block_argmin(fbest, ibest, scratch);
-    if (publish_and_check_last(fbest, ibest, partials, ctrl, &s_last)) {
+    if (publish_and_check_last(fbest, ibest, partials, ctrl, &s_last, block, nblocks)) {
         double bf;
         long long bi;
-        reduce_partials(partials, bf, bi, scratch);
+        reduce_partials(partials, bf, bi, scratch, nblocks);
         if (threadIdx.x == 0) {
             scratch[0].f = bf;
             scratch[0].idx = bi;
@@ -118,6 +119,56 @@ __global__ void __launch_bounds__(kPsoThreads)
         const long long b = scratch[0].idx;
         for (int j = threadIdx.x; j < d; j += blockDim.x) gx[j] = __ldcg(px + b * d + j);
     }
+}
+
+// t < 0: initialisation (Alg. 2); t >= 0: PSO update number t (Alg. 3).
+template <int OBJ>
+__global__ void __launch_bounds__(kPsoThreads)
+    pso_kernel(const zeus_problem p, const int t, const int G, double* __restrict__ x,
+               double* __restrict__ v, double* __restrict__ px, double* __restrict__ pf,
+               double* __restrict__ gx, Ctrl* __restrict__ ctrl, ArgPair* __restrict__ partials,
+               zeus_result* __restrict__ res) {
+    pso_block<OBJ>(p, t, G, blockIdx.x, gridDim.x, x, v, px, pf, gx, ctrl, partials, res);
+}
+
+// Batched PSO: each block belongs to one problem of the batch.
+__global__ void __launch_bounds__(kPsoThreads)
+    batch_pso_kernel(const BatchDev bd, const int t, double* __restrict__ x_out) {
+    const int P = bd.pso_table[blockIdx.x];
+    const zeus_problem p = bd.probs[P];
+    if (t >= p.pso_iters) return;  // this problem has made all its updates
+    const int lb = blockIdx.x - bd.pblk0[P];
+    double* x = x_out + bd.xoff[P];
+    double* v = bd.v + bd.xoff[P];
+    double* px = bd.px + bd.xoff[P];
+    double* pf = bd.pf + bd.soff[P];
+    double* gx = bd.gx + bd.goff[P];
+    ArgPair* parts = bd.partials + bd.poff[P];
+    Ctrl* ctrl = bd.pctrl + P;
+    const int G = bd.plane[P], nb = bd.pblk[P];
+    switch (p.objective) {
+        case ZEUS_OBJ_ROSENBROCK:
+            pso_block<ZEUS_OBJ_ROSENBROCK>(p, t, G, lb, nb, x, v, px, pf, gx, ctrl, parts, nullptr);
+            break;
+        case ZEUS_OBJ_RASTRIGIN:
+            pso_block<ZEUS_OBJ_RASTRIGIN>(p, t, G, lb, nb, x, v, px, pf, gx, ctrl, parts, nullptr);
+            break;
+        case ZEUS_OBJ_ACKLEY:
+            pso_block<ZEUS_OBJ_ACKLEY>(p, t, G, lb, nb, x, v, px, pf, gx, ctrl, parts, nullptr);
+            break;
+        case ZEUS_OBJ_GOLDSTEIN_PRICE:
+            pso_block<ZEUS_OBJ_GOLDSTEIN_PRICE>(p, t, G, lb, nb, x, v, px, pf, gx, ctrl, parts,
+                                                nullptr);
+            break;
+        default:
+            pso_block<ZEUS_OBJ_QUADRATIC>(p, t, G, lb, nb, x, v, px, pf, gx, ctrl, parts, nullptr);
+            break;
+    }
+}
+
+cudaError_t launch_batch_pso(const BatchDev& bd, int t, double* x_out, cudaStream_t st) {
+    batch_pso_kernel<<<bd.pso_blocks, kPsoThreads, 0, st>>>(bd, t, x_out);
+    return cudaGetLastError();
 }
 
 int pso_blocks(const zeus_problem& p, int G) {
@@ -222,6 +273,44 @@ int argmin_blocks(long long n) {
 cudaError_t launch_argmin(const double* f, long long n, Ctrl* ctrl, ArgPair* partials,
                           zeus_result* res, int mode, cudaStream_t st) {
     argmin_kernel<<<argmin_blocks(n), kArgminThreads, 0, st>>>(f, n, ctrl, partials, res, mode);
+    return cudaGetLastError();
+}
+
+// Batched best-of-swarm reduction: one block per problem.
+__global__ void __launch_bounds__(kArgminThreads)
+    batch_argmin_kernel(const BatchDev bd, const double* __restrict__ f, zeus_result* res) {
+    __shared__ ArgPair scratch[32];
+    const int P = blockIdx.x;
+    const long long n = bd.probs[P].n_starts;
+    const double* fp = f + bd.soff[P];
+    double bf = CUDART_INF;
+    long long bi = 0x7fffffffffffffffll;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = nan_to_inf(fp[i]);
+        if (better(v, i, bf, bi)) {
+            bf = v;
+            bi = i;
+        }
+    }
+    block_argmin(bf, bi, scratch);
+    if (threadIdx.x == 0 && res) {
+        volatile Ctrl* c = bd.pctrl + P;
+        zeus_result* r = res + P;
+        r->best_f = bf;
+        r->best_index = bi;
+        r->n_converged = (int64_t)c->n_conv;
+        r->total_iters = (int64_t)c->total_iters;
+        r->total_feval = (int64_t)c->total_feval;
+        r->gbest_f = c->gbest_f;
+        r->gbest_index = c->gbest_idx;
+        r->error = c->error;
+        r->stop_flag = c->stop;
+    }
+}
+
+cudaError_t launch_batch_argmin(const BatchDev& bd, const double* f_out, zeus_result* res,
+                                cudaStream_t st) {
+    batch_argmin_kernel<<<bd.n, kArgminThreads, 0, st>>>(bd, f_out, res);
     return cudaGetLastError();
 }
 

@@ -52,13 +52,18 @@ __device__ __forceinline__ void block_argmin(double& f, long long& idx, ArgPair*
 // every thread; returns the same bool to all threads of the block.  The
 // last block must reset ctrl->blocks_done to 0 when it has finished.
 __device__ __forceinline__ bool publish_and_check_last(double f, long long idx, ArgPair* partials,
-                                                       Ctrl* ctrl, int* s_last) {
+                                                       Ctrl* ctrl, int* s_last,
+                                                       int block = -1, int nblocks = -1) {
+    if (block < 0) {
+        block = blockIdx.x;
+        nblocks = gridDim.x;
+    }
     if (threadIdx.x == 0) {
-        partials[blockIdx.x].f = f;
-        partials[blockIdx.x].idx = idx;
+        partials[block].f = f;
+        partials[block].idx = idx;
         __threadfence();
         const unsigned prev = atomicAdd(&ctrl->blocks_done, 1u);
-        *s_last = (prev == gridDim.x - 1) ? 1 : 0;
+        *s_last = (prev == (unsigned)nblocks - 1) ? 1 : 0;
     }
     __syncthreads();
     const bool last = *s_last != 0;
@@ -68,10 +73,11 @@ __device__ __forceinline__ bool publish_and_check_last(double f, long long idx, 
 
 // In the last block: reduce the gridDim.x partials; thread 0 gets the result.
 __device__ __forceinline__ void reduce_partials(const ArgPair* partials, double& f, long long& idx,
-                                                ArgPair* scratch) {
+                                                ArgPair* scratch, int nblocks = -1) {
+    if (nblocks < 0) nblocks = gridDim.x;
     f = CUDART_INF;
     idx = 0x7fffffffffffffffll;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
         volatile const ArgPair* p = partials + b;
         const double pf = p->f;
         const long long pi = p->idx;

@@ -42,8 +42,9 @@ def test_struct_layouts_match_header(z, tmp_path):
     from paper_2603_28770_gb300 import _capi
     import subprocess
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "zeus.h"', 'int main(void){']
-    for cname, cls in (("zeus_problem", _capi.zeus_problem), ("zeus_result", _capi.zeus_result),
-                       ("zeus_plan", _capi.zeus_plan)):
+    structs = (("zeus_problem", _capi.zeus_problem), ("zeus_result", _capi.zeus_result),
+               ("zeus_plan", _capi.zeus_plan), ("zeus_batch_plan", _capi.zeus_batch_plan))
+    for cname, cls in structs:
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:
             lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
@@ -54,8 +55,7 @@ def test_struct_layouts_match_header(z, tmp_path):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                                   check=True).stdout.splitlines())
-    for cname, cls in (("zeus_problem", _capi.zeus_problem), ("zeus_result", _capi.zeus_result),
-                       ("zeus_plan", _capi.zeus_plan)):
+    for cname, cls in structs:
         assert int(out[cname]) == C.sizeof(cls)
         for f, _ in cls._fields_:
             assert int(out[f"{cname}.{f}"]) == getattr(cls, f).offset, f
@@ -135,3 +135,81 @@ def test_plan_choice(z):
     # the stream slots are part of the workspace
     assert z.zeus_workspace_size(z.Problem(objective="rosenbrock", dim=256, n_starts=8192,
                                            precision="fp32_guarded")) >= 300 * 256 * 256 * 4
+
+
+# ---------------------------------------------------------------- batched form
+
+def _mixed(z, n=12, **kw):
+    from paper_2603_28770_gb300.workloads import mixed_batch
+    return [z.Problem(**m, n_starts=64 + 7 * i, pso_iters=i % 4, bfgs_max_iters=50, seed=i, **kw)
+            for i, m in enumerate(mixed_batch(n, seed=7, dmin=2, dmax=64))]
+
+
+def test_batch_plan(z):
+    probs = _mixed(z)
+    pl = z.zeus_batch_plan_make(probs)
+    assert pl.n_problems == len(probs)
+    assert pl.total_starts == sum(p.n_starts for p in probs)
+    assert pl.total_coords == sum(p.n_starts * p.dim for p in probs)
+    assert pl.total_g == sum(p.dim for p in probs)
+    assert pl.pso_iters_max == max(p.pso_iters for p in probs)
+    assert pl.workspace_bytes % 256 == 0
+    # the classes tile the work list in order, each with some shared memory
+    nxt = 0
+    for c in range(pl.n_classes):
+        assert pl.class_first[c] == nxt and pl.class_count[c] > 0
+        assert 0 < pl.class_smem[c] <= 227 * 1024
+        nxt += pl.class_count[c]
+    assert nxt == pl.items
+    # work items: one per block-per-start start, one per lane tile of <= 128 starts
+    lane = [p for p in probs if z.zeus_plan_info(p)["narrow"]]
+    block = [p for p in probs if not z.zeus_plan_info(p)["narrow"]]
+    assert pl.items >= sum(p.n_starts for p in block) + sum(-(-p.n_starts // 128) for p in lane)
+    # hand-over queue only when some lane problem hands over
+    assert (pl.q_cap > 0) == any(z.zeus_plan_info(p)["handover"] for p in probs)
+    # planning is deterministic
+    assert bytes(z.zeus_batch_plan_make(probs)) == bytes(pl)
+
+
+def test_batch_rejects(z):
+    L = z.lib()
+    EINVAL, EUNS, EWS = z._capi.ZEUS_EINVAL, z._capi.ZEUS_EUNSUPPORTED, z._capi.ZEUS_EWORKSPACE
+    probs = _mixed(z, 4)
+    arr = (z._capi.zeus_problem * 4)(*[p.to_c() for p in probs])
+    pl = z._capi.zeus_batch_plan()
+    assert L.zeus_batch_plan_make(arr, 0, C.byref(pl)) == EINVAL
+    assert L.zeus_batch_plan_make(None, 4, C.byref(pl)) == EINVAL
+    assert L.zeus_batch_plan_make(arr, 4, None) == EINVAL
+    # all problems share precision and gradient mode
+    mixed = probs[:3] + [probs[3].replace(precision="fp32_guarded")]
+    with pytest.raises(z.ZeusError) as e:
+        z.zeus_batch_plan_make(mixed)
+    assert e.value.code == EINVAL
+    mixed = probs[:3] + [probs[3].replace(grad_mode="adjoint")]
+    with pytest.raises(z.ZeusError):
+        z.zeus_batch_plan_make(mixed)
+    # an invalid member problem
+    with pytest.raises(z.ZeusError):
+        z.zeus_batch_plan_make(probs[:3] + [probs[3].replace(dim=0)])
+    # H streamed from HBM is not batched
+    with pytest.raises(z.ZeusError) as e:
+        z.zeus_batch_plan_make(probs[:3] + [z.Problem(objective="rosenbrock", dim=256, n_starts=8)])
+    assert e.value.code == EUNS
+    assert L.zeus_batch_plan_make(arr, 4, C.byref(pl)) == 0
+    # prepare: missing or small workspace, and a plan of another batch, fail on the host
+    assert L.zeus_batch_prepare(arr, 4, C.byref(pl), None, 0, None) == EWS
+    assert L.zeus_batch_prepare(arr, 4, C.byref(pl), C.c_void_p(4096), pl.workspace_bytes - 256,
+                                None) == EWS
+    assert L.zeus_batch_prepare(arr, 4, C.byref(pl), C.c_void_p(4096 + 16), pl.workspace_bytes,
+                                None) == EWS
+    other = z.zeus_batch_plan_make(probs[:3])
+    assert L.zeus_batch_prepare(arr, 4, C.byref(other), C.c_void_p(4096), 1 << 40, None) == EINVAL
+    # solve: a damaged plan, a missing output or workspace
+    bad = z._capi.zeus_batch_plan.from_buffer_copy(bytes(pl))
+    bad.class_count[0] += 1
+    assert L.zeus_batch_solve(C.byref(bad), C.c_void_p(4096), 1 << 40, C.c_void_p(256),
+                              C.c_void_p(256), None, None, None, None, None) == EINVAL
+    assert L.zeus_batch_solve(C.byref(pl), C.c_void_p(4096), 1 << 40, None, C.c_void_p(256), None,
+                              None, None, None, None) == EINVAL
+    assert L.zeus_batch_solve(C.byref(pl), None, 0, C.c_void_p(256), C.c_void_p(256), None, None,
+                              None, None, None) == EWS
