@@ -9,6 +9,13 @@ start-iterations per second (sum over starts of completed BFGS iterations
 divided by device time).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl zeus|reference]
+                  [--workload rastrigin10d_n16384|mixed4096_n256|...]
+
+The default line also carries the forms' time-to-target comparison
+("forms") and the batched form on the first 1024 problems of the mixed
+4096-problem batch ("batched").  --workload mixed4096_n256 makes the whole
+batch (4096 problems x 256 starts, d in [2, 128]) the timed step, one CUDA
+graph replay of zeus_batch_solve per step.
 
 --impl reference times the FP64 CPU oracle (the only reference: the paper
 ships no code) on the host cores for the same workload, a bounded sample of
@@ -151,6 +158,8 @@ def run_zeus(a):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
+    if a.workload in workloads.BATCH_WORKLOADS:
+        return run_batch_main(a, z, dev, world, rank, local)
     fields = workloads.workload(a.workload, grad_mode=a.grad_mode, threads_per_start=a.lanes,
                                 precision=a.precision)
     # weak scaling: every rank solves its own independent multistart problem
@@ -291,6 +300,8 @@ def run_zeus(a):
     }
     if rank == 0 and not a.no_forms:
         out["forms"] = run_forms(z, dev, stream, seeds=a.form_seeds)
+        out["batched"] = {prec: run_batched(z, dev, BATCH_PROBLEMS_DEFAULT, precision=prec)
+                          for prec in ("fp64", "fp32_guarded")}
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(fields, budget_s=12.0)
     if rank == 0:
@@ -352,6 +363,181 @@ def _forms_on(z, fields, dev, stream, seeds):
 FP64_PEAK_TFLOPS = 1.25  # FP64 FMA throughput measured on GB300 (= nominal)
 
 
+# ------------------------------------------------------------ batched form
+
+BATCH_WORKLOAD = "mixed4096_n256"
+BATCH_PROBLEMS_DEFAULT = 1024  # the default run times the first quarter of the mix
+
+
+def _batch(z, n_problems, dev, precision="fp64", grad_mode="forward"):
+    fields = workloads.batch_problems(BATCH_WORKLOAD, n_problems, precision=precision,
+                                      grad_mode=grad_mode)
+    return z.Batch([z.Problem(**f) for f in fields], device=dev)
+
+
+def batch_flops(b) -> float:
+    """FP64-model operations of one batched solve (per-problem counters)."""
+    return float(sum(fp64_flops(p.dim, s["total_iters"], s["total_feval"])
+                     for p, s in zip(b.problems, b.summaries())))
+
+
+def run_batched(z, dev, n_problems, precision="fp64", loop_problems=128, reps=2) -> dict:
+    """The batched form on the first n_problems of the 4096-problem mix
+    (256 starts each, d log-uniform in [2, 128], mixed objectives), one CUDA
+    graph replay per solve; and, on the first loop_problems of them, one
+    batch against a loop of single-problem solves."""
+    import torch
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    b = _batch(z, n_problems, dev, precision)
+    b.solve()
+    torch.cuda.synchronize(dev)
+    b.capture()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for r in range(reps):
+        flush.fill_(r & 0xFF)
+        e0.record()
+        b.replay()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    iters = int(b.iters.sum().item())
+    flops = batch_flops(b)
+    out = {"workload": f"first {n_problems} problems of {BATCH_WORKLOAD}", "precision": precision,
+           "problems": n_problems, "starts": int(b.plan.total_starts), "ms": round(ms, 2),
+           "start_iters": iters, "value": round(iters / (ms / 1e3), 1), "unit": "start-iters/s",
+           "fp64_model_tflops": round(flops / (ms / 1e3) / 1e12, 4),
+           "launches_per_solve": b.launches, "bfgs_classes": int(b.plan.n_classes)}
+    del b
+    # one batch of the first loop_problems against one zeus_solve per problem
+    small = _batch(z, loop_problems, dev, precision)
+    small.solve()
+    torch.cuda.synchronize(dev)
+    e0.record()
+    small.solve()
+    e1.record()
+    torch.cuda.synchronize(dev)
+    batch_ms = e0.elapsed_time(e1)
+    singles = []
+    for p in small.problems:
+        singles.append((p, z.new_workspace(p, dev),
+                        torch.empty(p.n_starts * p.dim, dtype=torch.float64, device=dev),
+                        torch.empty(p.n_starts, dtype=torch.float64, device=dev)))
+    for p, ws, x, f in singles:
+        z.zeus_solve(p, ws, x, f)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for p, ws, x, f in singles:
+        z.zeus_solve(p, ws, x, f)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    loop_ms = e0.elapsed_time(e1)
+    out["vs_single_solves"] = {"problems": loop_problems, "batch_ms": round(batch_ms, 2),
+                               "loop_ms": round(loop_ms, 2), "speedup": round(loop_ms / batch_ms, 2)}
+    return out
+
+
+def run_batch_main(a, z, dev, world, rank, local):
+    """--workload mixed4096_n256: one step = one solve of the whole batch
+    (4096 problems, 2^20 starts), replayed from a CUDA graph."""
+    import torch
+    import torch.distributed as dist
+    fields = workloads.batch_problems(BATCH_WORKLOAD, None, precision=a.precision,
+                                      grad_mode=a.grad_mode)
+    # weak scaling: each rank solves its own batch (seeds shifted by rank)
+    b = z.Batch([z.Problem(**dict(f, seed=f["seed"] + 4096 * rank)) for f in fields], device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    b.solve()
+    torch.cuda.synchronize(dev)
+    b.capture()
+    for _ in range(max(0, a.warmup - 1)):
+        b.replay()
+    torch.cuda.synchronize(dev)
+    iters = int(b.iters.sum().item())
+    flops = batch_flops(b)
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(a.steps):
+            flush.fill_(k & 0xFF)
+            events[k][0].record()
+            b.replay()
+            events[k][1].record()
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    step_ms = [e[0].elapsed_time(e[1]) for e in events]
+    total_ms = sum(step_ms)
+    assert int(b.iters.sum().item()) == iters, "non-deterministic iteration count"
+    iters_all = float(iters)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        it_t = torch.tensor([iters_all], dtype=torch.float64, device=dev)
+        dist.all_reduce(it_t, op=dist.ReduceOp.SUM)
+        iters_all = float(it_t.item())
+    value = iters_all * a.steps / (total_ms / 1e3)
+
+    # end to end: the problem tables go up (zeus_batch_prepare), the graph
+    # runs, every per-start output and the per-problem summaries come back
+    pl = b.plan
+    host = {k: torch.empty(getattr(b, k).shape, dtype=getattr(b, k).dtype).pin_memory()
+            for k in ("x", "f", "gnorm", "status", "iters", "results")}
+    e2e_ms = []
+    for k in range(max(1, a.steps)):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        z.zeus_batch_prepare(b.problems, pl, b.workspace)
+        b.replay()
+        for name, h in host.items():
+            h.copy_(getattr(b, name), non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    assert int(host["iters"].sum().item()) == iters
+    e2e_value = iters * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+    d2h = sum(h.numel() * h.element_size() for h in host.values())
+
+    step_s = statistics.mean(step_ms) / 1e3
+    achieved = flops / step_s / 1e12
+    roof = {"kernel": "batch_bfgs_kernel (all classes + hand-over) + batch PSO + argmin",
+            "bound": "alu", "achieved": round(achieved, 5), "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 5), "traffic": None,
+            "peak_source": "FP64 FMA rate measured on this GB300 (1.25 TFLOP/s, equal to the "
+                           "part's nominal FP64 rate)",
+            "flops_per_launch": flops, "launch_ms": round(step_s * 1e3, 3)}
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "start-iters/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(total_ms / a.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if a.precision == "fp32_guarded" else "f64",
+        "data": "synthetic (seeded mixed problem list; Philox draws of the method itself)",
+        "config": {"workload": BATCH_WORKLOAD, "problems": pl.n_problems,
+                   "starts": int(pl.total_starts), "pso_iters": 10, "bfgs_max_iters": 500,
+                   "grad_mode": a.grad_mode, "precision": a.precision,
+                   "start_iters_per_step": iters, "bfgs_classes": int(pl.n_classes),
+                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "step": "one CUDA graph replay of zeus_batch_solve",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(e2e_value, 1), "unit": "start-iters/s",
+                "h2d_bytes_per_step": int(pl.table_bytes), "d2h_bytes_per_step": d2h,
+                "api": "zeus_batch_prepare (tables up, synchronizes) + graph replay + all outputs back"},
+        "gpu_launches": a.steps * b.launches,
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_batch(a.precision, budget_s=12.0)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------ oracle arm
 
 def _oracle_sample(fields, n_sample, threads):
@@ -383,6 +569,33 @@ def cpu_baseline(fields, budget_s=12.0) -> dict:
                       f"{n_sample} of them ({iters} start-iterations in {dt:.2f} s, OpenMP)"}
 
 
+def _oracle_batch_sample(budget_s, threads):
+    """Whole-method oracle solves of the batch's problems in order until
+    budget_s has passed: (start-iterations, seconds, problems)."""
+    import oracle
+    fields = workloads.batch_problems(BATCH_WORKLOAD, None)
+    iters, t0, n = 0, time.perf_counter(), 0
+    for f in fields:
+        op = oracle.Problem(**{k: v for k, v in f.items() if k in oracle.Problem.__dataclass_fields__})
+        op.n_threads = threads
+        iters += int(oracle.solve(op)["iters"].sum())
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return iters, time.perf_counter() - t0, n
+
+
+def cpu_baseline_batch(precision, budget_s=12.0) -> dict:
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    iters, dt, n = _oracle_batch_sample(budget_s, threads)
+    return {"value": round(iters / dt, 1), "unit": "start-iters/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"the first {n} problems of {BATCH_WORKLOAD}, whole method, FP64 "
+                      f"({iters} start-iterations in {dt:.2f} s, OpenMP)"}
+
+
 def run_reference(a):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -390,8 +603,31 @@ def run_reference(a):
         return
     import oracle
     oracle.build()
-    fields = workloads.workload(a.workload)
     threads = os.cpu_count() or 1
+    if a.workload in workloads.BATCH_WORKLOADS:
+        for _ in range(a.warmup):
+            _oracle_batch_sample(0.0, threads)
+        times, iters, probs = [], [], 0
+        for _ in range(a.steps):
+            it, dt, n = _oracle_batch_sample(10.0, threads)
+            times.append(dt)
+            iters.append(it)
+            probs = n
+        value = sum(iters) / sum(times)
+        sample = f"per step: whole-method oracle solves of the first {probs} problems"
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": round(value, 1),
+            "unit": "start-iters/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": round(1e3 * sum(times) / a.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": a.workload, "sample": sample},
+            "cpu_baseline": {"value": round(value, 1), "unit": "start-iters/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": "start-iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }), flush=True)
+        return
+    fields = workloads.workload(a.workload)
     n_sample = 256
     for _ in range(a.warmup):
         _oracle_sample(fields, 16, threads)

@@ -268,6 +268,7 @@ typedef struct {
     int64_t total_coords;     /* sum_P N_P * dim_P */
     int64_t total_g;          /* sum_P dim_P */
     uint64_t workspace_bytes; /* device workspace the batch needs */
+    uint64_t table_bytes;     /* bytes zeus_batch_prepare copies to the device */
 } zeus_batch_plan;
 
 /* Plans a batch (host only, no CUDA call).  probs: host array [n]. */

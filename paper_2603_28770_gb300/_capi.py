@@ -70,7 +70,7 @@ class zeus_batch_plan(C.Structure):
                 ("class_count", C.c_int32 * BATCH_MAX_CLASSES),
                 ("class_smem", C.c_int32 * BATCH_MAX_CLASSES),
                 ("total_starts", C.c_int64), ("total_coords", C.c_int64), ("total_g", C.c_int64),
-                ("workspace_bytes", C.c_uint64)]
+                ("workspace_bytes", C.c_uint64), ("table_bytes", C.c_uint64)]
 
 
 class ZeusError(RuntimeError):

@@ -290,6 +290,7 @@ void fill_plan(const BatchHost& B, const BatchLayout& l, zeus_batch_plan* plan) 
     plan->total_coords = B.sz.total_coords;
     plan->total_g = B.sz.total_g;
     plan->workspace_bytes = l.total;
+    plan->table_bytes = l.pctrl;
 }
 
 int check_ws(void* ws, size_t have, size_t need) {
@@ -312,7 +313,8 @@ bool plan_sane(const zeus_batch_plan& p) {
     if (next != p.items) return false;
     if (p.precision != ZEUS_FP64 && p.precision != ZEUS_FP32_GUARDED) return false;
     if (p.grad_mode != ZEUS_GRAD_FORWARD && p.grad_mode != ZEUS_GRAD_ADJOINT) return false;
-    return batch_layout(plan_sizes(p)).total == p.workspace_bytes;
+    const BatchLayout l = batch_layout(plan_sizes(p));
+    return l.total == p.workspace_bytes && l.pctrl == p.table_bytes;
 }
 
 }  // namespace

@@ -42,6 +42,15 @@ WORKLOADS = {
                                   backtrack=0.5, seed=0),
 }
 
+# batched form: many independent problems, each with its own swarm
+BATCH_WORKLOADS = {
+    # 4096 problems x 256 starts (2^20 starts), d log-uniform in [2, 128],
+    # objective uniform over Rosenbrock chain / Rastrigin / Ackley, 10 PSO
+    # updates, BFGS cap 500, FP64
+    "mixed4096_n256": dict(n_problems=4096, n_starts=256, pso_iters=10, bfgs_max_iters=500,
+                           mix_seed=12345, dmin=2, dmax=128),
+}
+
 # sampling box per objective for the mixed batches
 BOXES = {"rosenbrock": (-5.0, 5.0), "rastrigin": (-5.12, 5.12), "ackley": (-5.0, 5.0)}
 
@@ -67,3 +76,19 @@ def mixed_batch(n_problems: int, seed: int = 12345, dmin: int = 2, dmax: int = 1
     objs = rng.choice(["rosenbrock", "rastrigin", "ackley"], size=n_problems)
     return [dict(objective=str(o), dim=int(d), lower=BOXES[o][0], upper=BOXES[o][1])
             for o, d in zip(objs, dims)]
+
+
+def batch_problems(name: str, n_problems: int | None = None, **override) -> list[dict]:
+    """Problem fields of a batched workload (optionally its first n_problems);
+    problem P gets seed P."""
+    w = dict(BATCH_WORKLOADS[name])
+    mix = mixed_batch(w["n_problems"], seed=w["mix_seed"], dmin=w["dmin"], dmax=w["dmax"])
+    if n_problems is not None:
+        mix = mix[:n_problems]
+    out = []
+    for P, m in enumerate(mix):
+        f = dict(m, n_starts=w["n_starts"], pso_iters=w["pso_iters"],
+                 bfgs_max_iters=w["bfgs_max_iters"], seed=P)
+        f.update(override)
+        out.append(f)
+    return out
