@@ -506,36 +506,55 @@ double zo_line_search(int obj, int d, const double *x, const double *p,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Dot products and matrix-vector products (Alg. 4: H g, g^T p, y^T s,      */
+/* H y, y^T H y).  Reading: every product term is accumulated with one      */
+/* rounding, acc = fma(a_i, b_i, acc), in index order; the paper fixes the  */
+/* arithmetic only in exact terms.                                           */
+/* ------------------------------------------------------------------------ */
+
+static double zo_dot(int n, const double *a, const double *b)
+{
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) acc = fma(a[i], b[i], acc);
+    return acc;
+}
+
+/* out = M v for row-major M [d][d] */
+static void zo_matvec(int d, const double *M, const double *v, double *out)
+{
+    for (int r = 0; r < d; ++r) out[r] = zo_dot(d, M + (size_t)r * d, v);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Inverse-Hessian rank-two update (the update formula of Alg. 4).           */
 /* The printed product form (I - rho s y^T) H (I - rho y s^T) + rho s s^T    */
 /* expands, for symmetric H, to                                              */
-/*   H - rho (Hy s^T + s (Hy)^T) + (rho^2 y^T H y + rho) s s^T.              */
-/* Returns 1 if applied.  Reading: skipped when y^T s <= 1e-12 |s| |y|.      */
+/*   H - rho (Hy s^T + s (Hy)^T) + (rho^2 y^T H y + rho) s s^T,              */
+/* whose element (r, c) regroups as H_rc + s_c A_r + (Hy)_c B_r with         */
+/*   A_r = beta s_r - rho (Hy)_r,  B_r = -rho s_r,  beta = rho^2 y^T H y + rho.*/
+/* Reading: each element takes two fused multiply-adds,                      */
+/*   H_rc <- fma(s_c, A_r, fma((Hy)_c, B_r, H_rc)),                          */
+/* and A_r = fma(beta, s_r, -(rho (Hy)_r)).  Returns 1 if applied.  Reading: */
+/* skipped when y^T s <= 1e-12 |s| |y|.                                      */
 /* ------------------------------------------------------------------------ */
 
 int zo_bfgs_update(int d, double *H, const double *s, const double *y)
 {
-    double sy = 0.0, ss = 0.0, yy = 0.0;
-    for (int i = 0; i < d; ++i) {
-        sy = sy + y[i] * s[i];
-        ss = ss + s[i] * s[i];
-        yy = yy + y[i] * y[i];
-    }
+    const double sy = zo_dot(d, y, s), ss = zo_dot(d, s, s), yy = zo_dot(d, y, y);
     if (!(sy > 1e-12 * sqrt(ss) * sqrt(yy))) return 0;
     double rho = 1.0 / sy;
-    double *Hy = (double *)malloc(sizeof(double) * (size_t)d);
-    double yHy = 0.0;
+    double *Hy = (double *)malloc(sizeof(double) * (size_t)d * 3);
+    double *A = Hy + d, *B = Hy + 2 * d;
+    zo_matvec(d, H, y, Hy);
+    const double yHy = zo_dot(d, y, Hy);
+    const double beta = rho * rho * yHy + rho;
     for (int r = 0; r < d; ++r) {
-        double a = 0.0;
-        for (int c = 0; c < d; ++c) a = a + H[r * d + c] * y[c];
-        Hy[r] = a;
+        A[r] = fma(beta, s[r], -(rho * Hy[r]));
+        B[r] = -(rho * s[r]);
     }
-    for (int r = 0; r < d; ++r) yHy = yHy + y[r] * Hy[r];
-    double beta = rho * rho * yHy + rho;
     for (int r = 0; r < d; ++r)
         for (int c = 0; c < d; ++c)
-            H[r * d + c] = H[r * d + c] - rho * (Hy[r] * s[c] + s[r] * Hy[c])
-                           + beta * (s[r] * s[c]);
+            H[r * d + c] = fma(s[c], A[r], fma(Hy[c], B[r], H[r * d + c]));
     free(Hy);
     return 1;
 }
@@ -575,9 +594,7 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
     int k = 0, status = 0, n_feval = 0;
     double gnorm = NAN;
     for (;;) {
-        double gg = 0.0;
-        for (int i = 0; i < d; ++i) gg = gg + g[i] * g[i];
-        gnorm = sqrt(gg);
+        gnorm = sqrt(zo_dot(d, g, g));
         if (k >= pr->bfgs_max_iters) { status = 0; break; }
         if (stop && *stop) { status = 2; break; }
         if (!isfinite(f0) || !finite_vec(d, g)) { status = 3; break; }
@@ -599,20 +616,15 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
             break;
         }
         /* p = -H g, ddir = g^T p */
-        double ddir = 0.0;
-        for (int r = 0; r < d; ++r) {
-            double a = 0.0;
-            for (int c = 0; c < d; ++c) a = a + H[r * d + c] * g[c];
-            p[r] = -a;
-        }
-        for (int r = 0; r < d; ++r) ddir = ddir + g[r] * p[r];
+        zo_matvec(d, H, g, p);
+        for (int r = 0; r < d; ++r) p[r] = -p[r];
+        double ddir = zo_dot(d, g, p);
         if (!(ddir < 0.0)) {
             /* Reading: non-descent direction -> restart from H = I */
             for (int i = 0; i < d * d; ++i) H[i] = 0.0;
             for (int i = 0; i < d; ++i) H[i * d + i] = 1.0;
             for (int r = 0; r < d; ++r) p[r] = -g[r];
-            ddir = 0.0;
-            for (int r = 0; r < d; ++r) ddir = ddir + g[r] * p[r];
+            ddir = zo_dot(d, g, p);
         }
         int accepted = 0;
         double alpha = zo_line_search(obj, d, x, p, f0, ddir, pr->armijo_c,

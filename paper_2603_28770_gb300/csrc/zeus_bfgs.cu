@@ -23,18 +23,18 @@
 //
 // Both kernels perform exactly the oracle's operations in the oracle's
 // order: sums run left to right (the wide kernel gathers the terms in
-// shared memory and one thread adds them), no FMA contraction, the same
+// shared memory and one thread adds them), dot and matrix-vector products
+// take one fused multiply-add per term, no other FMA contraction, the same
 // elementary functions.  A run is therefore bitwise independent of which
 // kernel carried it and of the hand-over point.
 //
 // Per iteration (readings of the paper are listed in the design notes):
 //   ||g|| < tol -> converged; p = -H g (reset H = I, p = -g if not a descent
 //   direction); backtracking Armijo line search (Alg. 6); x_new = x + a p;
-//   g at x_new; y = g_new - g, s = x_new - x; if y's > 1e-12 |s||y|:
-//   H <- H - rho (Hy s' + s Hy') + (rho^2 y'Hy + rho) s s'  (the expanded form
-//   of the product update printed in Alg. 4).  The expanded form keeps H
-//   exactly symmetric (IEEE products and sums commute), so the narrow
-//   kernel computes the upper triangle and mirrors it.
+//   g at x_new; y = g_new - g, s = x_new - x; if y's > 1e-12 |s||y|: the
+//   product update printed in Alg. 4, expanded for symmetric H and grouped
+//   by rows, H_rc <- H_rc + s_c A_r + (Hy)_c B_r with A = b2 s - rho Hy,
+//   B = -rho s, b2 = rho^2 y'Hy + rho: two fused multiply-adds per element.
 #include "zeus_bfgs.cuh"
 
 namespace zeus {

@@ -33,6 +33,17 @@ struct AtPromoted {
     __device__ __forceinline__ double operator()(int j) const { return (double)x[j]; }
 };
 
+// Dot and matrix-vector products accumulate every term with one rounding
+// (fused multiply-add), in index order.  dot_fma: an FP64 sum (the FP32
+// form promotes its operands first; their product is exact in FP64, so its
+// FP64 guard sums also round once per term).  mv_fma: the working precision.
+__device__ __forceinline__ double dot_fma(double a, double b, double acc) { return fma(a, b, acc); }
+__device__ __forceinline__ double dot_fma(float a, float b, double acc) {
+    return fma((double)a, (double)b, acc);
+}
+__device__ __forceinline__ double mv_fma(double a, double b, double acc) { return fma(a, b, acc); }
+__device__ __forceinline__ float mv_fma(float a, float b, float acc) { return fmaf(a, b, acc); }
+
 // The FP32 form evaluates Rastrigin as sum (x^2 + 20 sin^2(pi x)) and the
 // cosine mean of Ackley through 1 - (2/d) sum sin^2(pi x): the same
 // functions in exact arithmetic, without the cancellation that the literal
@@ -149,7 +160,7 @@ __device__ __forceinline__ AdjShared grad_prep(const T* x, int d) {
 }
 template <int OBJ, int GRAD, class T>
 __device__ __forceinline__ T grad_component(const T* x, int d, int i, const AdjShared& a) {
-    if (GRAD == ZEUS_GRAD_FORWARD) return forward_pass<OBJ, T>(x, d, i).b;
+    if (GRAD == ZEUS_GRAD_FORWARD) return forward_tangent<OBJ, T>(x, d, i);
     return adjoint_component<OBJ>(x, d, i, a);
 }
 
@@ -207,7 +218,7 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
         double gg = 0.0;
         bool bad = false;
         for (int j = 0; j < d; ++j) {
-            gg = gg + (double)(g[j] * g[j]);
+            gg = dot_fma(g[j], g[j], gg);
             bad |= !isfinite(g[j]);
         }
         gnorm = sqrt(gg);
@@ -258,17 +269,17 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
         for (int r = 0; r < d; ++r) {
             const T* Hr = H + r * d;
             T a = T(0);
-            for (int c = 0; c < d; ++c) a = a + Hr[c] * g[c];
+            for (int c = 0; c < d; ++c) a = mv_fma(Hr[c], g[c], a);
             pv[r] = -a;
         }
         double ddir = 0.0;
-        for (int r = 0; r < d; ++r) ddir = ddir + (double)(g[r] * pv[r]);
+        for (int r = 0; r < d; ++r) ddir = dot_fma(g[r], pv[r], ddir);
         if (!(ddir < 0.0)) {  // not a descent direction: restart from H = I
             for (int r = 0; r < d; ++r)
                 for (int c = 0; c < d; ++c) H[r * d + c] = (c == r) ? T(1) : T(0);
             for (int r = 0; r < d; ++r) pv[r] = -g[r];
             ddir = 0.0;
-            for (int r = 0; r < d; ++r) ddir = ddir + (double)(g[r] * pv[r]);
+            for (int r = 0; r < d; ++r) ddir = dot_fma(g[r], pv[r], ddir);
         }
         // backtracking Armijo line search (Alg. 6)
         double alpha = 1.0, fn = 0.0;
@@ -299,35 +310,42 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
             const T sj = xn[j] - x[j], yj = gn[j] - g[j];
             sv[j] = sj;
             g[j] = yj;
-            sy = sy + (double)(yj * sj);
-            ss = ss + (double)(sj * sj);
-            yy = yy + (double)(yj * yj);
+            sy = dot_fma(yj, sj, sy);
+            ss = dot_fma(sj, sj, ss);
+            yy = dot_fma(yj, yj, yy);
         }
-        if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
+        const bool upd = sy > 1e-12 * sqrt(ss) * sqrt(yy);
+        T rt = T(0), bt = T(0);
+        if (upd) {
             const double rho = 1.0 / sy;
             for (int r = 0; r < d; ++r) {  // Hy into p (the direction is spent)
                 const T* Hr = H + r * d;
                 T a = T(0);
-                for (int c = 0; c < d; ++c) a = a + Hr[c] * g[c];
+                for (int c = 0; c < d; ++c) a = mv_fma(Hr[c], g[c], a);
                 pv[r] = a;
             }
             double yhy = 0.0;
-            for (int r = 0; r < d; ++r) yhy = yhy + (double)(g[r] * pv[r]);
+            for (int r = 0; r < d; ++r) yhy = dot_fma(g[r], pv[r], yhy);
             const double b2 = rho * rho * yhy + rho;
-            const T rt = T(rho), bt = T(b2);
-            for (int r = 0; r < d; ++r) {
-                const T sr = sv[r], hr = pv[r];
-                for (int c = r; c < d; ++c) {
-                    const T sc = sv[c];
-                    const T h = H[r * d + c] - rt * (hr * sc + sr * pv[c]) + bt * (sr * sc);
-                    H[r * d + c] = h;
-                    H[c * d + r] = h;
-                }
-            }
+            rt = T(rho);
+            bt = T(b2);
         }
         for (int j = 0; j < d; ++j) {
             x[j] = xn[j];
             g[j] = gn[j];
+        }
+        if (upd) {
+            // H_rc <- fma(s_c, A_r, fma(Hy_c, B_r, H_rc)), A = b2 s - rho Hy
+            // and B = -rho s in the spent x_new and g_new rows
+            for (int r = 0; r < d; ++r) {
+                xn[r] = mv_fma(bt, sv[r], -(rt * pv[r]));
+                gn[r] = -(rt * sv[r]);
+            }
+            for (int r = 0; r < d; ++r) {
+                const T ar = xn[r], br = gn[r];
+                T* Hr = H + r * d;
+                for (int c = 0; c < d; ++c) Hr[c] = mv_fma(sv[c], ar, mv_fma(pv[c], br, Hr[c]));
+            }
         }
         f0 = fn;
         ++k;
@@ -347,7 +365,7 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
 // ---------------------------------------------------------------------------
 // Wide kernel: one CTA per start, persistent over a queue of starts.
 // Shared memory: T region H [d*d] | x | g | p | xn | gn | s, then an FP64
-// region scratch [3 d] | trial terms [W][d] x 2 | trial f [W] | alpha [L+1]
+// region scratch [2 d] | trial terms [W][d] x 2 | trial f [W] | alpha [L+1]
 // ---------------------------------------------------------------------------
 struct WideShared {
     int item;
@@ -359,10 +377,12 @@ struct WideShared {
     int ok[64];
 };
 
-// left-to-right sum of v[0..n) starting from init, on the calling thread
-__device__ __forceinline__ double ordered_sum(const double* v, int n, double init) {
-    double s = init;
-    for (int j = 0; j < n; ++j) s = s + v[j];
+// a'b over [0, n) in index order, one rounding per term (dot_fma), on the
+// calling thread
+template <class T>
+__device__ __forceinline__ double ordered_dot(const T* a, const T* b, int n) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s = dot_fma(a[j], b[j], s);
     return s;
 }
 
@@ -381,6 +401,11 @@ __host__ __device__ __forceinline__ size_t wide_t_bytes(int d, size_t tsize) {
     return (((size_t)d * d + 6 * (size_t)d) * tsize + 7) & ~size_t(7);
 }
 
+// Row r of a matrix-vector product goes to the thread of role
+// (r + NT - 32) mod NT: the rows start on the last warp, away from the
+// threads of roles 0 and 32 that form the ordered sums of the same phase.
+__device__ __forceinline__ int row_of(int tid, int NT) { return (tid + 32) % NT; }
+
 // One start on one block, from iteration k with `feval` evaluations done:
 // H from Hq (nullptr: identity), x from xq (nullptr: row s of io.x0).
 template <int OBJ, int GRAD, class T>
@@ -398,9 +423,8 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
     T* gn = xn + d;
     T* sv = gn + d;
     double* sc0 = reinterpret_cast<double*>(smem_raw + wide_t_bytes(d, sizeof(T)));
-    double* sc1 = sc0 + d;  // three FP64 scratch vectors
-    double* sc2 = sc1 + d;
-    double* tb0 = sc2 + d;              // [W][d]
+    double* sc1 = sc0 + d;  // two FP64 scratch vectors
+    double* tb0 = sc1 + d;              // [W][d]
     double* tb1 = tb0 + (size_t)W * d;  // [W][d] (second sum of Ackley)
     double* fb = tb1 + (size_t)W * d;   // [W]
     double* al = fb + W;                // [L + 1]
@@ -438,15 +462,20 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
     int status = ZEUS_RUN_MAX_ITER;
     double gnorm = 0.0;
     for (;;) {
-        // ---- tests at the top of iteration k
+        // ---- tests at the top of iteration k, with the direction p = -H g
+        // formed alongside (one row per thread, columns in order; used only
+        // if the start goes on)
         int b = 0;
-        for (int j = tid; j < d; j += NT) {
-            sc0[j] = (double)(g[j] * g[j]);
-            b |= !isfinite(g[j]);
+        for (int j = tid; j < d; j += NT) b |= !isfinite(g[j]);
+        for (int r = row_of(tid, NT); r < d; r += NT) {
+            const T* Hr = H + r * d;
+            T a = T(0);
+            for (int c = 0; c < d; ++c) a = mv_fma(Hr[c], g[c], a);
+            pv[r] = -a;
         }
         const int bad = __syncthreads_or(b);
         if (tid == 0) {
-            gnorm = sqrt(ordered_sum(sc0, d, 0.0));
+            gnorm = sqrt(ordered_dot(g, g, d));
             sh.red[1] = gnorm;
             int st = -1;
             if (k >= K) {
@@ -469,6 +498,8 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 atomicExch(&ctrl->stop, 1);
             }
             sh.status = st;
+        } else if (tid == 32) {  // g'p, on another warp
+            sh.red[0] = ordered_dot(g, pv, d);
         }
         __syncthreads();
         gnorm = sh.red[1];
@@ -476,27 +507,13 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             status = sh.status;
             break;
         }
-        // ---- direction p = -H g (one row per thread, columns in order)
-        for (int r = tid; r < d; r += NT) {
-            const T* Hr = H + r * d;
-            T a = T(0);
-            for (int c = 0; c < d; ++c) a = a + Hr[c] * g[c];
-            pv[r] = -a;
-            sc0[r] = (double)(g[r] * (-a));
-        }
-        __syncthreads();
-        if (tid == 0) sh.red[0] = ordered_sum(sc0, d, 0.0);
-        __syncthreads();
         double ddir = sh.red[0];
         if (!(ddir < 0.0)) {  // not a descent direction: restart from H = I
             __syncthreads();
             for (int e = tid; e < d * d; e += NT) H[e] = (e / d == e % d) ? T(1) : T(0);
-            for (int r = tid; r < d; r += NT) {
-                pv[r] = -g[r];
-                sc0[r] = (double)(g[r] * (-g[r]));
-            }
+            for (int r = tid; r < d; r += NT) pv[r] = -g[r];
             __syncthreads();
-            if (tid == 0) sh.red[0] = ordered_sum(sc0, d, 0.0);
+            if (tid == 0) sh.red[0] = ordered_dot(g, pv, d);
             __syncthreads();
             ddir = sh.red[0];
         }
@@ -544,38 +561,41 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         wide_gradient<OBJ, GRAD>(xn, gn, d, tid, sh);
         __syncthreads();
         fn = sh.red[2];
-        // ---- curvature pair
+        // ---- curvature pair; H y formed alongside its sums (used only if
+        // the pair passes the curvature test)
         for (int j = tid; j < d; j += NT) {  // s into sv, y over g
-            const T sj = xn[j] - x[j], yj = gn[j] - g[j];
-            sv[j] = sj;
-            g[j] = yj;
-            sc0[j] = (double)(yj * sj);
-            sc1[j] = (double)(sj * sj);
-            sc2[j] = (double)(yj * yj);
+            sv[j] = xn[j] - x[j];
+            g[j] = gn[j] - g[j];
         }
         __syncthreads();
-        if (tid < 3) sh.red[tid] = ordered_sum(tid == 0 ? sc0 : (tid == 1 ? sc1 : sc2), d, 0.0);
+        if (tid < 96 && (tid & 31) == 0) {  // y's, s's, y'y on three warps
+            const int w = tid >> 5;
+            sh.red[w] = w == 0 ? ordered_dot(g, sv, d)
+                               : (w == 1 ? ordered_dot(sv, sv, d) : ordered_dot(g, g, d));
+        }
+        for (int r = row_of(tid, NT); r < d; r += NT) {  // Hy into p (the direction is spent)
+            const T* Hr = H + r * d;
+            T a = T(0);
+            for (int c = 0; c < d; ++c) a = mv_fma(Hr[c], g[c], a);
+            pv[r] = a;
+        }
         __syncthreads();
         const double sy = sh.red[0], ss = sh.red[1], yy = sh.red[2];
         if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
             const double rho = 1.0 / sy;
-            __syncthreads();
-            for (int r = tid; r < d; r += NT) {  // Hy into p (the direction is spent)
-                const T* Hr = H + r * d;
-                T a = T(0);
-                for (int c = 0; c < d; ++c) a = a + Hr[c] * g[c];
-                pv[r] = a;
-                sc0[r] = (double)(g[r] * a);
-            }
-            __syncthreads();
-            if (tid == 0) sh.red[3] = ordered_sum(sc0, d, 0.0);
+            if (tid == 0) sh.red[3] = ordered_dot(g, pv, d);
             __syncthreads();
             const double b2 = rho * rho * sh.red[3] + rho;
             const T rt = T(rho), bt = T(b2);
+            // A = b2 s - rho Hy and B = -rho s (in the spent scratch rows)
+            for (int r = tid; r < d; r += NT) {
+                sc0[r] = (double)mv_fma(bt, sv[r], -(rt * pv[r]));
+                sc1[r] = (double)(-(rt * sv[r]));
+            }
+            __syncthreads();
             for (int e = tid; e < d * d; e += NT) {
                 const int r = e / d, c = e - r * d;
-                const T sr = sv[r], sc = sv[c];
-                H[e] = H[e] - rt * (pv[r] * sc + sr * pv[c]) + bt * (sr * sc);
+                H[e] = mv_fma(sv[c], T(sc0[r]), mv_fma(pv[c], T(sc1[r]), H[e]));
             }
         }
         __syncthreads();
@@ -627,7 +647,7 @@ __host__ __device__ inline int wide_trials(int d, int L) {
 
 inline size_t wide_smem(int d, int W, int L, size_t tsize) {
     return wide_t_bytes(d, tsize) +
-           sizeof(double) * (3 * (size_t)d + 2 * (size_t)W * d + W + L + 1);
+           sizeof(double) * (2 * (size_t)d + 2 * (size_t)W * d + W + L + 1);
 }
 
 }  // namespace zeus

@@ -350,21 +350,22 @@ __device__ __forceinline__ Dual<T> forward_pass(const T* x, int d, int i) {
         }
         return dmk(val, tan);
     } else if (OBJ == ZEUS_OBJ_ACKLEY) {
-        T s1 = T(0), s2 = T(0), t1 = T(0), t2 = T(0);
+        // the sine of x_i (tangent of the cosine) is taken before the sweep
+        // so that the sweep itself is the same for every i (no divergence
+        // when passes run on the lanes of one warp); c_2pi is bit for bit
+        // the cosine of sc_2pi
+        T sn, cn;
+        sc_2pi(x[i], &sn, &cn);
+        T s1 = T(0), s2 = T(0);
         for (int j = 0; j < d; ++j) {
             const T xj = x[j];
-            if (j == i) {
-                T s, c;
-                sc_2pi(xj, &s, &c);
-                s1 += xj * xj;
-                t1 += xj + xj;
-                s2 += c;
-                t2 += -s * Consts<T>::two_pi();
-            } else {
-                s1 += xj * xj;
-                s2 += c_2pi(xj);
-            }
+            s1 += xj * xj;
+            s2 += c_2pi(xj);
         }
+        // the only non-zero tangents of the two sums are those of term i
+        T t1 = T(0), t2 = T(0);
+        t1 += x[i] + x[i];
+        t2 += -sn * Consts<T>::two_pi();
         // dual division by the constant d: (a/d, (b d - a 0)/(d d))
         const T dd = T(d);
         // u = s1/d, r = sqrt(u) (tangent 0 at u = 0), e1 = exp(-0.2 r)
@@ -400,6 +401,46 @@ __device__ __forceinline__ Dual<T> forward_pass(const T* x, int d, int i) {
             if (j == i) tan += c * (xj + xj);
         }
         return dmk(val, tan);
+    }
+}
+
+// Tangent of pass i alone (Alg. 5): the gradient needs only df/dx_i, so
+// the terms whose inputs all carry a zero tangent are left out (they add
+// exact zeros) and so is the value sweep wherever the tangent does not
+// depend on it; the tangent arithmetic of the remaining terms is that of
+// forward_pass, in the same order.  Ackley's tangent depends on its two
+// sums, so its pass still sweeps all d terms, as Alg. 5 does.
+template <int OBJ, class T>
+__device__ __forceinline__ T forward_tangent(const T* x, int d, int i) {
+    if (OBJ == ZEUS_OBJ_ROSENBROCK) {
+        T tan = T(0);
+        for (int j = i - 1; j <= i; ++j) {  // the terms (x_j, x_{j+1}) that contain x_i
+            if (j < 0 || j >= d - 1) continue;
+            const Dual<T> u = dmk(x[j], T(j == i ? 1 : 0));
+            const Dual<T> v = dmk(x[j + 1], T(j + 1 == i ? 1 : 0));
+            const Dual<T> a = dmk(T(1), T(0)) - u;
+            const Dual<T> b = v - u * u;
+            const Dual<T> t = a * a + T(100) * (b * b);
+            tan += t.b;
+        }
+        return tan;
+    } else if (OBJ == ZEUS_OBJ_RASTRIGIN) {
+        const T xi = x[i];
+        T s, c;
+        sc_2pi(xi, &s, &c);
+        const T tx2 = xi + xi;
+        const T tcos = -s * Consts<T>::two_pi();
+        T tan = T(0);
+        tan += tx2 - T(10) * tcos;
+        return tan;
+    } else if (OBJ == ZEUS_OBJ_QUADRATIC) {
+        const T xi = x[i];
+        const T c = T(0.5) * T(i + 1);
+        T tan = T(0);
+        tan += c * (xi + xi);
+        return tan;
+    } else {
+        return forward_pass<OBJ, T>(x, d, i).b;
     }
 }
 

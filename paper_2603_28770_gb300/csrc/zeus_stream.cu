@@ -162,7 +162,7 @@ __device__ __forceinline__ void block_gradient(const T* x, T* g, int d, double* 
         a.c2 = (double)(-e2 / dd);
     }
     for (int i = threadIdx.x; i < d; i += blockDim.x)
-        g[i] = GRAD == ZEUS_GRAD_FORWARD ? forward_pass<OBJ, T>(x, d, i).b
+        g[i] = GRAD == ZEUS_GRAD_FORWARD ? forward_tangent<OBJ, T>(x, d, i)
                                          : adjoint_component<OBJ>(x, d, i, a);
     __syncthreads();
 }
