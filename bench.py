@@ -144,6 +144,26 @@ def _peaks():
 
 # -------------------------------------------------------------- zeus arm
 
+def aggregate(total_ms: float, iters: int, world: int, device=None):
+    """Whole-job figures over the ranks of the process group: the slowest
+    rank's timed milliseconds and the sum of the ranks' start-iterations
+    (weak scaling: every rank solves its own independent problem)."""
+    if world <= 1:
+        return float(total_ms), float(iters)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
+def rank_seed(seed: int, rank: int, stride: int = 1) -> int:
+    """Seed of rank `rank`'s independent problem (rank 0 keeps the base seed)."""
+    return int(seed) + stride * int(rank)
+
+
 def run_zeus(a):
     import torch
     import torch.distributed as dist
@@ -163,7 +183,7 @@ def run_zeus(a):
     fields = workloads.workload(a.workload, grad_mode=a.grad_mode, threads_per_start=a.lanes,
                                 precision=a.precision)
     # weak scaling: every rank solves its own independent multistart problem
-    fields["seed"] = fields["seed"] + rank
+    fields["seed"] = rank_seed(fields["seed"], rank)
     p = z.Problem(**{k: v for k, v in fields.items() if k in z.Problem.__dataclass_fields__})
     pc = p.to_c()
     n, d = p.n_starts, p.dim
@@ -220,15 +240,7 @@ def run_zeus(a):
     summary = z.decode_result(res)
     assert int(summary["total_iters"]) == iters_per_step, "non-deterministic iteration count"
 
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        it_t = torch.tensor([iters_per_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(it_t, op=dist.ReduceOp.SUM)
-        iters_all = float(it_t.item())
-    else:
-        iters_all = float(iters_per_step)
+    total_ms, iters_all = aggregate(total_ms, iters_per_step, world, dev)
 
     value = iters_all * a.steps / (total_ms / 1e3)
 
@@ -369,10 +381,23 @@ BATCH_WORKLOAD = "mixed4096_n256"
 BATCH_PROBLEMS_DEFAULT = 1024  # the default run times the first quarter of the mix
 
 
-def _batch(z, n_problems, dev, precision="fp64", grad_mode="forward"):
+def _batch(z, n_problems, dev, precision="fp64", grad_mode="forward", tuner=None):
     fields = workloads.batch_problems(BATCH_WORKLOAD, n_problems, precision=precision,
                                       grad_mode=grad_mode)
-    return z.Batch([z.Problem(**f) for f in fields], device=dev)
+    return z.Batch([z.Problem(**f) for f in fields], device=dev, autotuner=tuner)
+
+
+def _tuner():
+    """The layout autotuner with its cache in the user's cache directory."""
+    from paper_2603_28770_gb300.autotune import Autotuner
+    return Autotuner()
+
+
+def _tuned_summary(b) -> dict:
+    counts = {}
+    for p in b.problems:
+        counts[str(int(p.threads_per_start))] = counts.get(str(int(p.threads_per_start)), 0) + 1
+    return {"threads_per_start_counts": counts}
 
 
 def batch_flops(b) -> float:
@@ -388,7 +413,10 @@ def run_batched(z, dev, n_problems, precision="fp64", loop_problems=128, reps=2)
     batch against a loop of single-problem solves."""
     import torch
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    b = _batch(z, n_problems, dev, precision)
+    tuner = _tuner()
+    t0 = time.perf_counter()
+    b = _batch(z, n_problems, dev, precision, tuner=tuner)
+    tune_s = time.perf_counter() - t0
     b.solve()
     torch.cuda.synchronize(dev)
     b.capture()
@@ -408,10 +436,11 @@ def run_batched(z, dev, n_problems, precision="fp64", loop_problems=128, reps=2)
            "problems": n_problems, "starts": int(b.plan.total_starts), "ms": round(ms, 2),
            "start_iters": iters, "value": round(iters / (ms / 1e3), 1), "unit": "start-iters/s",
            "fp64_model_tflops": round(flops / (ms / 1e3) / 1e12, 4),
-           "launches_per_solve": b.launches, "bfgs_classes": int(b.plan.n_classes)}
+           "launches_per_solve": b.launches, "bfgs_classes": int(b.plan.n_classes),
+           "autotune": dict(_tuned_summary(b), setup_s=round(tune_s, 2))}
     del b
     # one batch of the first loop_problems against one zeus_solve per problem
-    small = _batch(z, loop_problems, dev, precision)
+    small = _batch(z, loop_problems, dev, precision, tuner=tuner)
     small.solve()
     torch.cuda.synchronize(dev)
     e0.record()
@@ -445,8 +474,13 @@ def run_batch_main(a, z, dev, world, rank, local):
     import torch.distributed as dist
     fields = workloads.batch_problems(BATCH_WORKLOAD, None, precision=a.precision,
                                       grad_mode=a.grad_mode)
-    # weak scaling: each rank solves its own batch (seeds shifted by rank)
-    b = z.Batch([z.Problem(**dict(f, seed=f["seed"] + 4096 * rank)) for f in fields], device=dev)
+    # weak scaling: each rank solves its own batch (seeds shifted by rank);
+    # threads per start chosen by the autotuner (measured once, then cached)
+    t0 = time.perf_counter()
+    b = z.Batch([z.Problem(**dict(f, seed=rank_seed(f["seed"], rank, 4096))) for f in fields],
+                device=dev,
+                autotuner=_tuner())
+    tune_s = time.perf_counter() - t0
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     b.solve()
     torch.cuda.synchronize(dev)
@@ -472,14 +506,7 @@ def run_batch_main(a, z, dev, world, rank, local):
     step_ms = [e[0].elapsed_time(e[1]) for e in events]
     total_ms = sum(step_ms)
     assert int(b.iters.sum().item()) == iters, "non-deterministic iteration count"
-    iters_all = float(iters)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        it_t = torch.tensor([iters_all], dtype=torch.float64, device=dev)
-        dist.all_reduce(it_t, op=dist.ReduceOp.SUM)
-        iters_all = float(it_t.item())
+    total_ms, iters_all = aggregate(total_ms, iters, world, dev)
     value = iters_all * a.steps / (total_ms / 1e3)
 
     # end to end: the problem tables go up (zeus_batch_prepare), the graph
@@ -520,6 +547,7 @@ def run_batch_main(a, z, dev, world, rank, local):
                    "starts": int(pl.total_starts), "pso_iters": 10, "bfgs_max_iters": 500,
                    "grad_mode": a.grad_mode, "precision": a.precision,
                    "start_iters_per_step": iters, "bfgs_classes": int(pl.n_classes),
+                   "autotune": dict(_tuned_summary(b), setup_s=round(tune_s, 2)),
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "step": "one CUDA graph replay of zeus_batch_solve",
                    "parallelism": f"replicas x{world}"},
