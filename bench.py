@@ -56,6 +56,10 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form-seeds", type=int, default=5)
+    ap.add_argument("--starts", type=int, default=0,
+                    help="override the workload's number of starts (smaller profiling cases)")
+    ap.add_argument("--iters", type=int, default=0,
+                    help="override the workload's BFGS iteration cap (smaller profiling cases)")
     return ap.parse_args()
 
 
@@ -182,6 +186,10 @@ def run_zeus(a):
         return run_batch_main(a, z, dev, world, rank, local)
     fields = workloads.workload(a.workload, grad_mode=a.grad_mode, threads_per_start=a.lanes,
                                 precision=a.precision)
+    if a.starts:
+        fields["n_starts"] = a.starts
+    if a.iters:
+        fields["bfgs_max_iters"] = a.iters
     # weak scaling: every rank solves its own independent multistart problem
     fields["seed"] = rank_seed(fields["seed"], rank)
     p = z.Problem(**{k: v for k, v in fields.items() if k in z.Problem.__dataclass_fields__})
@@ -269,15 +277,19 @@ def run_zeus(a):
     plan = z.zeus_plan_info(pc)
     bfgs_s = statistics.mean(bfgs_ms) / 1e3
     if plan["stream"]:
-        # H streamed from HBM: 2 d^2 sizeof(T) bytes per start-iteration
-        nbytes = 2.0 * plan["h_bytes"] * iters_per_step
+        # H streamed from HBM: one H of d^2 sizeof(T) bytes per pass that
+        # read or wrote it (the kernel counts them; at most 2 per
+        # start-iteration, none while H = I)
+        nbytes = float(plan["h_bytes"]) * (summary["h_reads"] + summary["h_writes"])
         achieved = nbytes / bfgs_s / 1e9
         peak = _peaks().get("hbm_gbs", 6800.0)
         roof = {"kernel": "bfgs_stream_kernel (+ argmin)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json)",
-                "bytes_per_launch": nbytes, "launch_ms": round(bfgs_s * 1e3, 3)}
+                "bytes_per_launch": nbytes, "launch_ms": round(bfgs_s * 1e3, 3),
+                "h_passes": {"reads": summary["h_reads"], "writes": summary["h_writes"],
+                             "bytes_per_pass": plan["h_bytes"]}}
     else:
         flops = fp64_flops(d, iters_per_step, feval_per_step)
         achieved = flops / bfgs_s / 1e12

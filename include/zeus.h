@@ -118,6 +118,10 @@ typedef struct {
     int64_t gbest_index;    /* its particle index */
     int32_t error;          /* device-side error word, 0 = none */
     int32_t stop_flag;      /* 1 if the stop flag was raised */
+    int64_t h_reads;        /* streamed H (zeus_plan_info().stream): passes over a start's
+                               H that read it from device memory, summed over starts; the
+                               pass is skipped while H = I, 0 for on-chip H */
+    int64_t h_writes;       /* ... passes that wrote it back (an update was applied) */
 } zeus_result;
 
 /* Name of a zeus_status code (static string, never NULL). */

@@ -49,6 +49,7 @@ class zeus_result(C.Structure):
         ("n_converged", C.c_int64), ("total_iters", C.c_int64),
         ("total_feval", C.c_int64), ("gbest_f", C.c_double),
         ("gbest_index", C.c_int64), ("error", C.c_int32), ("stop_flag", C.c_int32),
+        ("h_reads", C.c_int64), ("h_writes", C.c_int64),
     ]
 
 

@@ -168,9 +168,13 @@ int build_host(const zeus_problem* probs, int n, BatchHost& B) {
     B.sz.n = n;
     B.sz.pso_blocks = (long long)B.pso_table.size();
     B.sz.items = (long long)B.items.size();
-    // as in the single-problem plan: at most two hand-overs per block of the
-    // hand-over launch, within 256 MB of H
-    B.sz.q_cap = std::min<long long>(handover_starts, 2ll * 152 * 4);
+    // Hand-over queue.  FP64: room for many long runs, so that lane tiles
+    // do not wait on a few of their lanes (lane efficiency); FP32 runs
+    // rarely meet the gradient tolerance and would all be handed over, so
+    // as in the single-problem plan at most two per block of the hand-over
+    // launch.  Within 256 MB of H either way.
+    B.sz.q_cap = std::min<long long>(handover_starts,
+                                     prec == ZEUS_FP32_GUARDED ? 2ll * 152 * 4 : 65536ll);
     if (B.sz.q_cap > 0) {
         const long long per = B.sz.d_max_handover * B.sz.d_max_handover * 8;
         B.sz.q_cap = std::max<long long>(1, std::min<long long>(B.sz.q_cap, (256ll << 20) / per));

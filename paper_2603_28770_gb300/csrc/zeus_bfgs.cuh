@@ -461,6 +461,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
     double f0 = sh.red[0];
     int status = ZEUS_RUN_MAX_ITER;
     double gnorm = 0.0;
+    int hint = W;  // trials the previous search needed
     for (;;) {
         // ---- tests at the top of iteration k, with the direction p = -H g
         // formed alongside (one row per thread, columns in order; used only
@@ -517,11 +518,17 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             __syncthreads();
             ddir = sh.red[0];
         }
-        // ---- line search: W trials at a time, the first accepted wins
+        // ---- line search: trials in chunks, the first accepted wins.
+        // Index L is the point after the last halving (taken when every
+        // trial fails, reading 4); a chunk may include it so that a search
+        // that fails costs no separate sweep.  The first chunk has as many
+        // trials as the previous iteration's search needed (all of them
+        // for a start that keeps failing), the later ones W.
         int acc_m = -1;
         double fn = 0.0;
-        for (int m0 = 0; m0 < L && acc_m < 0; m0 += W) {
-            const int nw = min(W, L - m0);
+        int m0 = 0;
+        while (acc_m < 0 && m0 <= L) {
+            const int nw = min(m0 == 0 ? min(W, hint) : W, L + 1 - m0);
             for (int e = tid; e < nw * nt; e += NT) {
                 const int mm = e / nt, j = e - mm * nt;
                 double t0, t1;
@@ -536,7 +543,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                     val_add<OBJ>(acc, tb0[tid * d + j], tb1[tid * d + j]);
                 const double ft = val_finish<OBJ, T>(acc, d);
                 fb[tid] = ft;
-                sh.ok[tid] = (ft <= f0 + cA * al[m0 + tid] * ddir) ? 1 : 0;
+                sh.ok[tid] = (m0 + tid < L && ft <= f0 + cA * al[m0 + tid] * ddir) ? 1 : 0;
             }
             __syncthreads();
             if (tid == 0) {
@@ -548,15 +555,17 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                     }
                 sh.accepted_m = am;
                 if (am >= 0) sh.red[2] = fb[am - m0];
+                else if (m0 + nw == L + 1) sh.red[2] = fb[L - m0];  // every trial failed
             }
             __syncthreads();
             acc_m = sh.accepted_m;
-            feval += (acc_m >= 0) ? (acc_m - m0 + 1) : nw;
+            feval += (acc_m >= 0) ? (acc_m - m0 + 1) : min(nw, L - m0);
+            m0 += nw;
         }
+        hint = (acc_m >= 0) ? acc_m + 1 : L + 1;
         const T alpha = T((acc_m >= 0) ? al[acc_m] : al[L]);
         for (int j = tid; j < d; j += NT) xn[j] = x[j] + alpha * pv[j];
         __syncthreads();
-        if (acc_m < 0 && tid == 0) sh.red[2] = seq_value<OBJ>(AtPoint<T>{xn}, d);
         // ---- gradient at x_new
         wide_gradient<OBJ, GRAD>(xn, gn, d, tid, sh);
         __syncthreads();
@@ -637,11 +646,13 @@ inline size_t narrow_stride(int d) {
     return st;
 }
 
+// trials a chunk of the block-per-start line search evaluates at once (up
+// to L + 1: the trials and the point after the last halving)
 __host__ __device__ inline int wide_trials(int d, int L) {
-    int W = (2 * kWideThreads) / (d > 0 ? d : 1);
+    int W = (4 * kWideThreads) / (d > 0 ? d : 1);
     if (W < 1) W = 1;
     if (W > 64) W = 64;
-    if (W > L) W = L;
+    if (W > L + 1) W = L + 1;
     return W;
 }
 

@@ -25,7 +25,9 @@ struct Ctrl {
     unsigned long long total_feval;  // sum of line-search evaluations
     double gbest_f;                  // PSO global best value
     long long gbest_idx;             // and its particle
-    unsigned long long pad1[24];
+    unsigned long long h_reads;      // H passes that read a start's H from HBM (streamed H)
+    unsigned long long h_writes;     // H passes that wrote it back
+    unsigned long long pad1[22];
 };
 static_assert(sizeof(Ctrl) == 256, "control block is one 256-byte segment");
 

@@ -246,12 +246,16 @@ __global__ void __launch_bounds__(kArgminThreads)
                     res->total_feval = (int64_t)c->total_feval;
                     res->error = c->error;
                     res->stop_flag = c->stop;
+                    res->h_reads = (int64_t)c->h_reads;
+                    res->h_writes = (int64_t)c->h_writes;
                 } else {
                     res->n_converged = 0;
                     res->total_iters = 0;
                     res->total_feval = 0;
                     res->error = 0;
                     res->stop_flag = 0;
+                    res->h_reads = 0;
+                    res->h_writes = 0;
                 }
                 if (mode != 1) {  // no PSO phase in this call
                     res->gbest_f = CUDART_NAN;
@@ -305,6 +309,8 @@ __global__ void __launch_bounds__(kArgminThreads)
         r->gbest_index = c->gbest_idx;
         r->error = c->error;
         r->stop_flag = c->stop;
+        r->h_reads = (int64_t)c->h_reads;
+        r->h_writes = (int64_t)c->h_writes;
     }
 }
 

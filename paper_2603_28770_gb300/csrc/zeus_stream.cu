@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(kStreamThreads)
         for (int j = tid; j < d; j += NT) pv[j] = -g[j];  // H_0 = I
         bool ident = true, corr = false;
         int k = 0, feval = 0, status = ZEUS_RUN_MAX_ITER;
+        unsigned long long n_read = 0, n_write = 0;  // H passes through HBM
         double gnorm = 0.0;
         __syncthreads();
         for (;;) {
@@ -384,6 +385,8 @@ __global__ void __launch_bounds__(kStreamThreads)
                 __syncthreads();
             } else {
                 h_pass<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u);
+                n_read += ident ? 0 : 1;             // H_{k-1} read unless still I
+                n_write += (corr || ident) ? 1 : 0;  // H_k stored when it changed
                 ident = false;
             }
             // ---- curvature pair and the correction C_k: one reduction for
@@ -464,6 +467,8 @@ __global__ void __launch_bounds__(kStreamThreads)
             if (iters_out) iters_out[s] = k;
             atomicAdd(&ctrl->total_iters, (unsigned long long)k);
             atomicAdd(&ctrl->total_feval, (unsigned long long)feval);
+            atomicAdd(&ctrl->h_reads, n_read);
+            atomicAdd(&ctrl->h_writes, n_write);
             if (!use_stop && status == ZEUS_RUN_CONVERGED) atomicAdd(&ctrl->n_conv, 1ull);
         }
     }

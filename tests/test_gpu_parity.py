@@ -392,6 +392,22 @@ def test_stream_fp64_first_iterations(z, ora, obj, d, n, lo, hi, grad):
     compare_runs(g, o, rtol=1e-8, max_flip_frac=0.1)
 
 
+def test_stream_counts_its_h_passes(z):
+    # the streamed path reports how often a start's H went through device
+    # memory: no pass while H = I, one write when the first update turns I
+    # into H_1, then a read and a write per applied update; on-chip H: none
+    n, d = 16, 33
+    x0 = torch.from_numpy(workloads.start_points(n, d, -1.0, 1.0, seed=5)).cuda()
+    base = dict(objective="quadratic", dim=d, lower=-1.0, upper=1.0, n_starts=n,
+                bfgs_max_iters=60)
+    s = z.solve_from(zeus_problem(z, base, threads_per_start=256), x0)["summary"]
+    it = s["total_iters"]
+    assert 0 < s["h_writes"] <= it and s["h_reads"] <= s["h_writes"]
+    assert s["h_writes"] - s["h_reads"] <= n  # one write without a read per start at most
+    s2 = z.solve_from(zeus_problem(z, base, threads_per_start=128), x0)["summary"]
+    assert s2["h_reads"] == 0 and s2["h_writes"] == 0
+
+
 @pytest.mark.parametrize("obj,d,n,lo,hi,fmin", [("rosenbrock", 64, 32, -2.0, 2.0, 0.0),
                                                 ("rastrigin", 12, 256, -5.12, 5.12, 0.0),
                                                 ("rosenbrock", 256, 8, -2.0, 2.0, 0.0)])
