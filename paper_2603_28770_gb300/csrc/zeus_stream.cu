@@ -29,11 +29,6 @@ constexpr int kStreamThreads = 256;
 constexpr int kStreamWarps = kStreamThreads / 32;
 constexpr int kStreamTrials = 4;  // line-search trials evaluated at once
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 template <class T>
 __device__ __forceinline__ T warp_sum_t(T v) {
 #pragma unroll
@@ -48,22 +43,44 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 template <int N>
 __device__ __forceinline__ void block_sum(double (&v)[N], double* red) {
     static_assert(kStreamWarps == 8, "second stage assumes 8 warps");
+    static_assert(N >= 1 && N <= 8, "up to eight sums");
+    constexpr int P = N <= 1 ? 1 : (N <= 2 ? 2 : (N <= 4 ? 4 : 8));  // N rounded up
+    constexpr int LP = P == 1 ? 0 : (P == 2 ? 1 : (P == 4 ? 2 : 3));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // Warp stage, transposed: at each of the first LP levels a lane keeps
+    // half of its values and adds its partner's copy of that half (P - 1
+    // FP64 adds in all instead of 5 N), then the single value left is
+    // summed over the remaining levels.  Lane l ends with the warp total
+    // of sum number (l >> (5 - LP)).
+    double u[P];
 #pragma unroll
-    for (int i = 0; i < N; ++i) v[i] = warp_sum_d(v[i]);
-    if (lane == 0)
+    for (int i = 0; i < P; ++i) u[i] = i < N ? v[i] : 0.0;
 #pragma unroll
-        for (int i = 0; i < N; ++i) red[i * kStreamWarps + w] = v[i];
+    for (int lev = 0, c = P; lev < LP; ++lev, c >>= 1) {
+        const int o = 16 >> lev, half = c >> 1;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const double keep = up ? u[half + k] : u[k];
+            const double give = up ? u[k] : u[half + k];
+            u[k] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+        }
+    }
+    double a = u[0];
+#pragma unroll
+    for (int o = 16 >> LP; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    const int which = LP == 0 ? 0 : (lane >> (5 - LP));  // bits of the halving levels
+    if ((lane & ((32 >> LP) - 1)) == 0 && which < N) red[which * kStreamWarps + w] = a;
     __syncthreads();
     if (w == 0) {
 #pragma unroll
         for (int i0 = 0; i0 < N; i0 += 4) {
             const int i = i0 + (lane >> 3);
-            double a = (i < N) ? red[i * kStreamWarps + (lane & 7)] : 0.0;
-            a += __shfl_xor_sync(0xffffffffu, a, 4);
-            a += __shfl_xor_sync(0xffffffffu, a, 2);
-            a += __shfl_xor_sync(0xffffffffu, a, 1);
-            if ((lane & 7) == 0 && i < N) red[8 * N + i] = a;
+            double b = (i < N) ? red[i * kStreamWarps + (lane & 7)] : 0.0;
+            b += __shfl_xor_sync(0xffffffffu, b, 4);
+            b += __shfl_xor_sync(0xffffffffu, b, 2);
+            b += __shfl_xor_sync(0xffffffffu, b, 1);
+            if ((lane & 7) == 0 && i < N) red[8 * N + i] = b;
         }
     }
     __syncthreads();
