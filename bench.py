@@ -280,7 +280,8 @@ def run_zeus(a):
         # H streamed from HBM: one H of d^2 sizeof(T) bytes per pass that
         # read or wrote it (the kernel counts them; at most 2 per
         # start-iteration, none while H = I)
-        nbytes = float(plan["h_bytes"]) * (summary["h_reads"] + summary["h_writes"])
+        reads, writes = summary["h_reads"], summary["h_writes"]
+        nbytes = float(plan["h_bytes"]) * (reads + writes)
         achieved = nbytes / bfgs_s / 1e9
         peak = _peaks().get("hbm_gbs", 6800.0)
         roof = {"kernel": "bfgs_stream_kernel (+ argmin)", "bound": "hbm",
@@ -288,8 +289,20 @@ def run_zeus(a):
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json)",
                 "bytes_per_launch": nbytes, "launch_ms": round(bfgs_s * 1e3, 3),
-                "h_passes": {"reads": summary["h_reads"], "writes": summary["h_writes"],
+                "h_passes": {"reads": reads, "writes": writes,
                              "bytes_per_pass": plan["h_bytes"]}}
+        if a.precision == "fp64":
+            # FP64 H: every pass takes d^2 FMAs for H g and 2 d^2 more when
+            # it applies an update; against the FP64 pipe this is the bound
+            pass_flops = 2.0 * d * d * max(reads, writes) + 4.0 * d * d * writes
+            tf = pass_flops / bfgs_s / 1e12
+            if tf / FP64_PEAK_TFLOPS > roof["frac"]:
+                roof = dict(roof, bound="alu", achieved=round(tf, 4), peak=FP64_PEAK_TFLOPS,
+                            unit="TFLOP/s", frac=round(tf / FP64_PEAK_TFLOPS, 4),
+                            peak_source="FP64 FMA rate measured on this GB300",
+                            flops_per_launch=pass_flops,
+                            hbm={"achieved_gbs": round(achieved, 1),
+                                 "frac": round(achieved / peak, 4)})
     else:
         flops = fp64_flops(d, iters_per_step, feval_per_step)
         achieved = flops / bfgs_s / 1e12

@@ -229,7 +229,12 @@ __device__ __forceinline__ void h_pass(T* __restrict__ Hs, int d, bool ident, bo
         if (vec) {
             const int nv = d / VT::n;
             V* rv = reinterpret_cast<V*>(row);
-#pragma unroll 4
+            // s, Hy and g as 16-byte vectors too (one shared load each per
+            // vector of H instead of one per element)
+            const V* sv4 = reinterpret_cast<const V*>(s);
+            const V* hv4 = reinterpret_cast<const V*>(hy);
+            const V* gv4 = reinterpret_cast<const V*>(g);
+#pragma unroll 2
             for (int c4 = lane; c4 < nv; c4 += 32) {
                 V h;
                 if (ident) {
@@ -238,13 +243,18 @@ __device__ __forceinline__ void h_pass(T* __restrict__ Hs, int d, bool ident, bo
                 } else {
                     h = __ldcs(rv + c4);
                 }
+                const V gq = gv4[c4];
+                V sq, hq;
+                if (corr) {
+                    sq = sv4[c4];
+                    hq = hv4[c4];
+                }
 #pragma unroll
                 for (int i = 0; i < VT::n; ++i) {
-                    const int c = c4 * VT::n + i;
                     T e = VT::get(h, i);
-                    if (corr) e = fma(s[c], ar, fma(hy[c], br, e));
+                    if (corr) e = fma(VT::get(sq, i), ar, fma(VT::get(hq, i), br, e));
                     VT::set(h, i, e);
-                    acc = fma(e, g[c], acc);
+                    acc = fma(e, VT::get(gq, i), acc);
                 }
                 if (corr || ident) __stcs(rv + c4, h);
             }
@@ -272,7 +282,7 @@ struct StreamShared {
 };
 
 template <int OBJ, int GRAD, class T>
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, 4)
     bfgs_stream_kernel(const zeus_problem p, const double* x0, double* x_out,
                        double* __restrict__ f_out, double* __restrict__ gnorm_out,
                        int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
