@@ -58,6 +58,8 @@ def _args():
     ap.add_argument("--form-seeds", type=int, default=5)
     ap.add_argument("--starts", type=int, default=0,
                     help="override the workload's number of starts (smaller profiling cases)")
+    ap.add_argument("--problems", type=int, default=0,
+                    help="batched workload: only its first N problems (smaller profiling cases)")
     ap.add_argument("--iters", type=int, default=0,
                     help="override the workload's BFGS iteration cap (smaller profiling cases)")
     return ap.parse_args()
@@ -497,7 +499,7 @@ def run_batch_main(a, z, dev, world, rank, local):
     (4096 problems, 2^20 starts), replayed from a CUDA graph."""
     import torch
     import torch.distributed as dist
-    fields = workloads.batch_problems(BATCH_WORKLOAD, None, precision=a.precision,
+    fields = workloads.batch_problems(BATCH_WORKLOAD, a.problems or None, precision=a.precision,
                                       grad_mode=a.grad_mode)
     # weak scaling: each rank solves its own batch (seeds shifted by rank);
     # threads per start chosen by the autotuner (measured once, then cached)
@@ -568,7 +570,9 @@ def run_batch_main(a, z, dev, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if a.precision == "fp32_guarded" else "f64",
         "data": "synthetic (seeded mixed problem list; Philox draws of the method itself)",
-        "config": {"workload": BATCH_WORKLOAD, "problems": pl.n_problems,
+        "config": {"workload": BATCH_WORKLOAD if not a.problems
+                   else f"first {pl.n_problems} problems of {BATCH_WORKLOAD}",
+                   "problems": pl.n_problems,
                    "starts": int(pl.total_starts), "pso_iters": 10, "bfgs_max_iters": 500,
                    "grad_mode": a.grad_mode, "precision": a.precision,
                    "start_iters_per_step": iters, "bfgs_classes": int(pl.n_classes),

@@ -125,7 +125,11 @@ cudaError_t batch_launch_gt(const BatchDev& bd, int cls, int first, int count, s
                             double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
                             int32_t* iters_out, cudaStream_t st) {
     auto k = batch_bfgs_kernel<GRAD, T>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // The launches of one solve use different shared memory sizes, and a
+    // captured graph launches its kernel nodes later: allow the largest
+    // size once rather than the size of the launch at hand.
+    if (smem > (size_t)(227 * 1024)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
