@@ -50,7 +50,8 @@ using namespace zeus;
 
 namespace {
 
-constexpr size_t kSmemCap = 227 * 1024;   // dynamic shared memory per block
+constexpr size_t kSmemCap = 226 * 1024;   // dynamic shared memory per block (the kernel's
+                                          // static shared memory takes the rest of 227 KB)
 constexpr size_t kSmemPerSM = 228 * 1024; // shared memory per SM
 constexpr int kMaxPerSM = 16;             // 128-thread blocks per SM (2048 threads)
 

@@ -127,12 +127,17 @@ cudaError_t batch_launch_gt(const BatchDev& bd, int cls, int first, int count, s
     auto k = batch_bfgs_kernel<GRAD, T>;
     // The launches of one solve use different shared memory sizes, and a
     // captured graph launches its kernel nodes later: allow the largest
-    // size once rather than the size of the launch at hand.
-    if (smem > (size_t)(227 * 1024)) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    // size the device offers once, rather than the size of the launch at
+    // hand (which a later launch would lower again).
+    int dev = 0, sms = 0, per_sm = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    e = cudaGetDevice(&dev);
+    const int maxdyn = optin - (int)fa.sharedSizeBytes;
+    if ((long long)smem > (long long)maxdyn) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWideThreads, smem);

@@ -44,7 +44,7 @@ namespace zeus {
 // ---------------------------------------------------------------------------
 int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
     const int d = p.dim;
-    const size_t cap = 227 * 1024;
+    const size_t cap = 226 * 1024;  // 227 KB per block, less the kernels' static shared memory
     const size_t ts = p.precision == ZEUS_FP32_GUARDED ? sizeof(float) : sizeof(double);
     const int req = p.threads_per_start;
     const size_t row = narrow_stride(d) * ts;
