@@ -363,7 +363,55 @@ def run_forms(z, dev, stream, seeds=5):
     out = {}
     for w in FORM_WORKLOADS:
         out[w] = _forms_on(z, workloads.workload(w), dev, stream, seeds)
+    out["batched_rastrigin5d_x16"] = _batched_to_target(z, dev, stream)
     return out
+
+
+def _batched_to_target(z, dev, stream, n_problems=16):
+    """Time to 1e-6 of the global minimum for 16 independent 5-D Rastrigin
+    problems (16384 particles each, seeds 2000..2015): the plain FP64 method
+    one problem after another, against one batch (FP64, and FP32 with FP64
+    guards) replayed from a CUDA graph.  Success = problems whose best f
+    reached 1e-6."""
+    import torch
+    base = dict(workloads.workload("rastrigin5d_n16384"), target_f=1e-6)
+    fields = [dict(base, seed=2000 + i) for i in range(n_problems)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    # plain FP64, one solve per problem
+    singles = []
+    for f in fields:
+        p = z.Problem(**{k: v for k, v in f.items() if k in z.Problem.__dataclass_fields__})
+        pc = p.to_c()
+        singles.append((pc, z.new_workspace(pc, dev),
+                        torch.empty(p.n_starts * p.dim, dtype=torch.float64, device=dev),
+                        torch.empty(p.n_starts, dtype=torch.float64, device=dev), z.new_result(dev)))
+    for rep in range(2):  # the first pass warms up
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for pc, ws, x, fo, r in singles:
+            z.zeus_solve(pc, ws, x, fo, None, None, None, r, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ok = sum(int(z.decode_result(r)["best_f"] <= 1e-6) for *_, r in singles)
+    res["fp64/forward one by one"] = {"time_to_target_ms": round(e0.elapsed_time(e1), 3),
+                                     "success": f"{ok}/{n_problems}"}
+    for prec in ("fp64", "fp32_guarded"):
+        b = z.Batch([z.Problem(**dict(f, precision=prec)) for f in fields], device=dev)
+        b.solve()
+        torch.cuda.synchronize(dev)
+        b.capture()
+        times = []
+        for rep in range(3):
+            e0.record()
+            b.replay()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1))
+        ok = sum(int(s["best_f"] <= 1e-6) for s in b.summaries())
+        res[f"{prec}/forward batched"] = {"time_to_target_ms": round(statistics.median(times), 3),
+                                         "success": f"{ok}/{n_problems}"}
+    return res
 
 
 def _forms_on(z, fields, dev, stream, seeds):
