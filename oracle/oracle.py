@@ -53,6 +53,7 @@ class _Problem(C.Structure):
         ("target_f", C.c_double),
         ("seed", C.c_uint64),
         ("start_from_pbest", C.c_int32), ("n_threads", C.c_int32),
+        ("lbfgs_m", C.c_int32), ("pad", C.c_int32),
     ]
 
 
@@ -87,6 +88,7 @@ class Problem:
     seed: int = 0
     start_from_pbest: int = 0
     n_threads: int = 0
+    lbfgs_m: int = 0  # 0: dense inverse Hessian (Alg. 4); m > 0: L-BFGS with m pairs
 
     def obj_id(self) -> int:
         o = self.objective
@@ -99,7 +101,7 @@ class Problem:
                         self.grad_tol, self.w, self.c1, self.c2,
                         self.armijo_c, self.backtrack, self.target_f,
                         self.seed & (2**64 - 1), self.start_from_pbest,
-                        self.n_threads)
+                        self.n_threads, self.lbfgs_m, 0)
 
 
 _lib = None
@@ -133,6 +135,7 @@ def lib():
                                  _D, _I32, _I32, _D]
     L.zo_line_search.restype = C.c_double
     L.zo_bfgs_update.argtypes = [C.c_int, _D, _D, _D]
+    L.zo_lbfgs_direction.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D]
     L.zo_bfgs_update.restype = C.c_int
     L.zo_bfgs.argtypes = [C.POINTER(_Problem), _D, _D, C.POINTER(_Result),
                           C.c_void_p, C.c_void_p]
@@ -311,3 +314,17 @@ def bfgs_quadratic_exact(A, x0, max_iters=100, tol=1e-10):
     k = lib().zo_bfgs_quadratic_exact(d, _dp(A), _dp(x0), max_iters, tol,
                                       _dp(xo), _dp(H))
     return int(k), xo, H
+
+
+def lbfgs_direction(S, Y, g):
+    """Two-loop L-BFGS direction p = -H g over the pairs (rows of S and Y,
+    oldest first) with the initial matrix gamma I."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    n, d = (S.shape[0], g.shape[0]) if S.size else (0, g.shape[0])
+    rho = np.array([1.0 / float(np.dot(Y[i], S[i])) for i in range(n)], dtype=np.float64)
+    p = np.zeros(d)
+    lib().zo_lbfgs_direction(d, n, _dp(S if n else np.zeros(1)), _dp(Y if n else np.zeros(1)),
+                             _dp(rho if n else np.zeros(1)), _dp(g), _dp(p))
+    return p

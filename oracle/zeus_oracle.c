@@ -54,6 +54,8 @@ typedef struct {
     uint64_t seed;
     int32_t start_from_pbest;   /* 0 = current swarm positions (Alg. 10) */
     int32_t n_threads;          /* OpenMP threads for the per-start loops */
+    int32_t lbfgs_m;            /* 0 = dense inverse Hessian (Alg. 4); m > 0 = L-BFGS, m pairs */
+    int32_t pad;
 } zo_problem;
 
 /* per-start result of one BFGS run (Alg. 4) */
@@ -560,6 +562,61 @@ int zo_bfgs_update(int d, double *H, const double *s, const double *y)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Limited-memory direction (L-BFGS, the paper's future work, Section VI):   */
+/* the two-loop recursion of Nocedal & Wright, Numerical Optimization,       */
+/* Alg. 7.4, over the n stored pairs (s_i, y_i), oldest first, with         */
+/* rho_i = 1 / y_i's_i and the initial matrix gamma I, gamma = s'y / y'y of  */
+/* the newest pair (their eq. 7.20; 1 when no pair is stored).  Returns      */
+/* p = -H g in p.  Dot products as zo_dot; each update of q and r is one     */
+/* fused multiply-add per element.                                           */
+/* ------------------------------------------------------------------------ */
+
+void zo_lbfgs_direction(int d, int n, const double *S, const double *Y, const double *rho,
+                        const double *g, double *p)
+{
+    double *q = (double *)malloc(sizeof(double) * (size_t)(d > 0 ? d : 1));
+    double *al = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int j = 0; j < d; ++j) q[j] = g[j];
+    for (int i = n - 1; i >= 0; --i) {
+        al[i] = rho[i] * zo_dot(d, S + (size_t)i * d, q);
+        for (int j = 0; j < d; ++j) q[j] = fma(-al[i], Y[(size_t)i * d + j], q[j]);
+    }
+    double gamma = 1.0;
+    if (n > 0) {
+        const double *sn = S + (size_t)(n - 1) * d, *yn = Y + (size_t)(n - 1) * d;
+        gamma = zo_dot(d, sn, yn) / zo_dot(d, yn, yn);
+    }
+    for (int j = 0; j < d; ++j) q[j] = gamma * q[j];  /* r = gamma q, in place */
+    for (int i = 0; i < n; ++i) {
+        const double b = rho[i] * zo_dot(d, Y + (size_t)i * d, q);
+        for (int j = 0; j < d; ++j) q[j] = fma(al[i] - b, S[(size_t)i * d + j], q[j]);
+    }
+    for (int j = 0; j < d; ++j) p[j] = -q[j];
+    free(q);
+    free(al);
+}
+
+/* Stores the pair (s, y) as the newest of at most m (the oldest is dropped)
+ * if it passes the curvature test of zo_bfgs_update; returns 1 if stored. */
+static int zo_lbfgs_push(int d, int m, int *n, double *S, double *Y, double *rho,
+                         const double *s, const double *y)
+{
+    const double sy = zo_dot(d, y, s), ss = zo_dot(d, s, s), yy = zo_dot(d, y, y);
+    if (!(sy > 1e-12 * sqrt(ss) * sqrt(yy))) return 0;
+    if (*n == m) {  /* drop the oldest */
+        memmove(S, S + d, sizeof(double) * (size_t)(m - 1) * d);
+        memmove(Y, Y + d, sizeof(double) * (size_t)(m - 1) * d);
+        memmove(rho, rho + 1, sizeof(double) * (size_t)(m - 1));
+        *n = m - 1;
+    }
+    memcpy(S + (size_t)(*n) * d, s, sizeof(double) * (size_t)d);
+    memcpy(Y + (size_t)(*n) * d, y, sizeof(double) * (size_t)d);
+    rho[*n] = 1.0 / sy;
+    *n += 1;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One BFGS run (Alg. 4, with the per-thread body of Alg. 10).               */
 /* Readings: the gradient at x_new is reused as the next iteration's         */
 /* gradient; a non-descent direction resets H to I and uses p = -g; the      */
@@ -580,14 +637,24 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
 {
     const int d = pr->dim, obj = pr->objective;
     size_t nb = sizeof(double) * (size_t)(d > 0 ? d : 1);
-    double *H = (double *)malloc(nb * (size_t)(d > 0 ? d : 1));
+    /* L-BFGS history (m > 0): pairs oldest first; the dense H otherwise */
+    const int m = pr->lbfgs_m;
+    int n_pairs = 0;
+    double *H = NULL, *S = NULL, *Y = NULL, *rho = NULL;
+    if (m > 0) {
+        S = (double *)malloc(nb * (size_t)m);
+        Y = (double *)malloc(nb * (size_t)m);
+        rho = (double *)malloc(sizeof(double) * (size_t)m);
+    } else {
+        H = (double *)malloc(nb * (size_t)(d > 0 ? d : 1));
+        for (int i = 0; i < d * d; ++i) H[i] = 0.0;
+        for (int i = 0; i < d; ++i) H[i * d + i] = 1.0;
+    }
     double *x = (double *)malloc(nb), *g = (double *)malloc(nb);
     double *p = (double *)malloc(nb), *xn = (double *)malloc(nb);
     double *gn = (double *)malloc(nb), *s = (double *)malloc(nb);
     double *y = (double *)malloc(nb);
     for (int i = 0; i < d; ++i) x[i] = x0[i];
-    for (int i = 0; i < d * d; ++i) H[i] = 0.0;
-    for (int i = 0; i < d; ++i) H[i * d + i] = 1.0;
     double f0;
     zo_grad_forward(obj, d, x, &f0, g);
     double margin = INFINITY;
@@ -616,13 +683,21 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
             break;
         }
         /* p = -H g, ddir = g^T p */
-        zo_matvec(d, H, g, p);
-        for (int r = 0; r < d; ++r) p[r] = -p[r];
+        if (m > 0) {
+            zo_lbfgs_direction(d, n_pairs, S, Y, rho, g, p);
+        } else {
+            zo_matvec(d, H, g, p);
+            for (int r = 0; r < d; ++r) p[r] = -p[r];
+        }
         double ddir = zo_dot(d, g, p);
         if (!(ddir < 0.0)) {
-            /* Reading: non-descent direction -> restart from H = I */
-            for (int i = 0; i < d * d; ++i) H[i] = 0.0;
-            for (int i = 0; i < d; ++i) H[i * d + i] = 1.0;
+            /* Reading: non-descent direction -> restart from H = I (L-BFGS:
+             * forget the stored pairs) */
+            if (H) {
+                for (int i = 0; i < d * d; ++i) H[i] = 0.0;
+                for (int i = 0; i < d; ++i) H[i * d + i] = 1.0;
+            }
+            n_pairs = 0;
             for (int r = 0; r < d; ++r) p[r] = -g[r];
             ddir = zo_dot(d, g, p);
         }
@@ -637,7 +712,10 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
             s[j] = xn[j] - x[j];
             y[j] = gn[j] - g[j];
         }
-        zo_bfgs_update(d, H, s, y);
+        if (m > 0)
+            zo_lbfgs_push(d, m, &n_pairs, S, Y, rho, s, y);
+        else
+            zo_bfgs_update(d, H, s, y);
         for (int j = 0; j < d; ++j) { x[j] = xn[j]; g[j] = gn[j]; }
         f0 = fn;
         ++k;
@@ -651,6 +729,7 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
     res->n_feval = n_feval;
     res->pad = 0;
     free(H); free(x); free(g); free(p); free(xn); free(gn); free(s); free(y);
+    free(S); free(Y); free(rho);
 }
 
 /* BFGS from n given starts (x0 row-major [n][d]); OpenMP over starts. */
