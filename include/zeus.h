@@ -105,6 +105,12 @@ typedef struct {
                                    chip; 1 = one lane per start throughout;
                                    128 = one 128-thread block per start throughout;
                                    256 = one 256-thread block per start, H streamed */
+    int32_t lbfgs_m;            /* 0 = the dense inverse-Hessian update of Alg. 4; m in 1..64 =
+                                   L-BFGS (the paper's future work, Section VI): the m most
+                                   recent pairs and the two-loop recursion, one 256-thread
+                                   block per start, no H (threads_per_start 0 or 256;
+                                   not for Goldstein-Price; not batched) */
+    int32_t pad;
 } zeus_problem;
 
 /* Summary written on the device by zeus_solve / zeus_solve_from. */
@@ -145,7 +151,7 @@ typedef struct {
     int32_t block;           /* 1: one 128-thread block per start, H in shared memory */
     int32_t stream;          /* 1: one 256-thread block per start, H streamed from HBM */
     int32_t blocks;          /* grid of the block-per-start / streaming kernel */
-    int32_t pad;
+    int32_t lbfgs;           /* 1: L-BFGS (problem.lbfgs_m > 0), block per start, no H */
     int64_t h_bytes;         /* bytes of H per start in the chosen precision */
 } zeus_plan;
 int zeus_plan_info(const zeus_problem *p, zeus_plan *plan);

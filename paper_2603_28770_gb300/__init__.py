@@ -56,6 +56,7 @@ class Problem:
     grad_mode: str | int = "forward"
     start_from_pbest: int = 0
     threads_per_start: int = 0
+    lbfgs_m: int = 0
 
     def to_c(self) -> zeus_problem:
         def code(v, table):
@@ -65,7 +66,8 @@ class Problem:
             self.pso_iters, self.bfgs_max_iters, self.ls_max_iters, self.required_converged,
             self.grad_tol, self.w, self.c1, self.c2, self.armijo_c, self.backtrack,
             self.target_f, self.seed & (2**64 - 1), code(self.precision, PRECISIONS),
-            code(self.grad_mode, GRAD_MODES), self.start_from_pbest, self.threads_per_start)
+            code(self.grad_mode, GRAD_MODES), self.start_from_pbest, self.threads_per_start,
+            self.lbfgs_m, 0)
 
     def replace(self, **kw) -> "Problem":
         d = {f.name: getattr(self, f.name) for f in fields(self)}
@@ -138,7 +140,7 @@ def zeus_plan_info(problem) -> dict:
     """Which kernels a solve of this problem runs."""
     pl = _capi.zeus_plan()
     check(lib().zeus_plan_info(C.byref(_prob(problem)), C.byref(pl)), "zeus_plan_info")
-    return {name: getattr(pl, name) for name, _ in _capi.zeus_plan._fields_ if name != "pad"}
+    return {name: getattr(pl, name) for name, _ in _capi.zeus_plan._fields_}
 
 
 def zeus_workspace_size(problem) -> int:

@@ -40,6 +40,7 @@ class zeus_problem(C.Structure):
         ("seed", C.c_uint64),
         ("precision", C.c_int32), ("grad_mode", C.c_int32),
         ("start_from_pbest", C.c_int32), ("threads_per_start", C.c_int32),
+        ("lbfgs_m", C.c_int32), ("pad", C.c_int32),
     ]
 
 
@@ -55,7 +56,7 @@ class zeus_result(C.Structure):
 
 class zeus_plan(C.Structure):
     _fields_ = [("narrow", C.c_int32), ("handover", C.c_int32), ("block", C.c_int32),
-                ("stream", C.c_int32), ("blocks", C.c_int32), ("pad", C.c_int32),
+                ("stream", C.c_int32), ("blocks", C.c_int32), ("lbfgs", C.c_int32),
                 ("h_bytes", C.c_int64)]
 
 

@@ -107,7 +107,7 @@ int build_host(const zeus_problem* probs, int n, BatchHost& B) {
         BfgsLaunch L;
         const int r = plan_bfgs(p, &L);
         if (r != ZEUS_OK) return r;
-        if (L.stream) return ZEUS_EUNSUPPORTED;  // H must fit on chip in a batch
+        if (L.stream) return ZEUS_EUNSUPPORTED;  // H on chip (and no L-BFGS) in a batch
         const int d = p.dim;
         const int G = lanes_for_dim(d);
         const int nb = pso_blocks(p, G);

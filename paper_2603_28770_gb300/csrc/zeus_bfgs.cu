@@ -47,6 +47,26 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
     const size_t cap = 226 * 1024;  // 227 KB per block, less the kernels' static shared memory
     const size_t ts = p.precision == ZEUS_FP32_GUARDED ? sizeof(float) : sizeof(double);
     const int req = p.threads_per_start;
+    L->lbfgs = p.lbfgs_m > 0;
+    if (L->lbfgs) {  // one 256-thread block per start, the pairs in shared memory
+        if (p.objective == ZEUS_OBJ_GOLDSTEIN_PRICE || (req != 0 && req != 256))
+            return ZEUS_EUNSUPPORTED;
+        L->narrow = false;
+        L->stride = 0;
+        L->narrow_threads = 0;
+        L->narrow_smem = 0;
+        L->narrow_blocks = 0;
+        L->W = 0;
+        L->wide_smem = 0;
+        L->wide_blocks = 0;
+        L->budget = 0;
+        L->q_cap = 0;
+        L->stream = true;
+        L->stream_blocks = stream_blocks(p);
+        L->stream_smem = lbfgs_smem(d, p.lbfgs_m, ts);
+        L->hslot_bytes = 0;
+        return L->stream_smem <= cap ? ZEUS_OK : ZEUS_EUNSUPPORTED;
+    }
     const size_t row = narrow_stride(d) * ts;
     const bool narrow_fits = row * 32 <= cap;
     L->narrow = (req == 1) || (req == 0 && narrow_fits && d <= 16);
@@ -72,9 +92,13 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
     L->budget = (L->narrow && !L->stream && L->wide_smem <= cap && req != 1) ? 160 : 0;
     L->q_cap = 0;
     if (L->budget > 0) {
-        // at most two starts per wide block: beyond that the long runs are
-        // the bulk and stay in the throughput kernel
-        long long capn = p.n_starts < 2ll * L->wide_blocks ? p.n_starts : 2ll * L->wide_blocks;
+        // FP64: room for every start (a start that finds the queue full
+        // runs on in its lane, at one lane's FP64 latency per iteration).
+        // FP32 runs rarely meet the gradient tolerance and would all be
+        // handed over: at most two per wide block, the long runs being the
+        // bulk that stays in the throughput kernel.
+        const long long lim = p.precision == ZEUS_FP32_GUARDED ? 2ll * L->wide_blocks : p.n_starts;
+        long long capn = p.n_starts < lim ? p.n_starts : lim;
         const long long max_bytes = 256ll << 20;
         const long long per = (long long)d * d * 8;
         if (capn * per > max_bytes) capn = max_bytes / per;

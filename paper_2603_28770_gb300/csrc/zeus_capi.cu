@@ -49,6 +49,7 @@ int validate(const zeus_problem* p) {
     if (p->grad_mode != ZEUS_GRAD_FORWARD && p->grad_mode != ZEUS_GRAD_ADJOINT) return ZEUS_EINVAL;
     if (p->start_from_pbest != 0 && p->start_from_pbest != 1) return ZEUS_EINVAL;
     if (!valid_lanes(p->threads_per_start)) return ZEUS_EINVAL;
+    if (p->lbfgs_m < 0 || p->lbfgs_m > 64 || p->pad != 0) return ZEUS_EINVAL;
     if (p->precision != ZEUS_FP64 && p->precision != ZEUS_FP32_GUARDED) return ZEUS_EINVAL;
     return ZEUS_OK;
 }
@@ -174,6 +175,8 @@ int zeus_default_problem(zeus_problem* p) {
     p->grad_mode = ZEUS_GRAD_FORWARD;
     p->start_from_pbest = 0;
     p->threads_per_start = 0;
+    p->lbfgs_m = 0;
+    p->pad = 0;
     return ZEUS_OK;
 }
 
@@ -189,10 +192,11 @@ int zeus_plan_info(const zeus_problem* p, zeus_plan* plan) {
     memset(plan, 0, sizeof(*plan));
     plan->narrow = L.narrow ? 1 : 0;
     plan->handover = L.budget > 0 ? 1 : 0;
-    plan->stream = L.stream ? 1 : 0;
+    plan->lbfgs = L.lbfgs ? 1 : 0;
+    plan->stream = (L.stream && !L.lbfgs) ? 1 : 0;
     plan->block = (!L.narrow && !L.stream) ? 1 : 0;
     plan->blocks = L.stream ? L.stream_blocks : L.wide_blocks;
-    plan->h_bytes = (int64_t)p->dim * p->dim * (p->precision == ZEUS_FP32_GUARDED ? 4 : 8);
+    plan->h_bytes = L.lbfgs ? 0 : (int64_t)p->dim * p->dim * (p->precision == ZEUS_FP32_GUARDED ? 4 : 8);
     return ZEUS_OK;
 }
 

@@ -89,6 +89,7 @@ struct BfgsLaunch {
     int stream_blocks;    // blocks (= H slots) of the streaming kernel
     size_t stream_smem;   // its dynamic shared memory
     size_t hslot_bytes;   // bytes of all H slots
+    bool lbfgs;           // L-BFGS: the streaming kernel's limited-memory variant (no H)
 };
 
 // Device tables of a batch (zeus_batch_*): per-problem parameters and
@@ -135,6 +136,7 @@ cudaError_t launch_bfgs(const zeus_problem& p, const BfgsLaunch& L, const double
                         int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st);
 
 size_t stream_smem(int d, size_t tsize);
+size_t lbfgs_smem(int d, int m, size_t tsize);
 int stream_blocks(const zeus_problem& p);
 cudaError_t launch_bfgs_stream(const zeus_problem& p, const double* x0, double* x_out,
                                double* f_out, double* gnorm_out, int32_t* status_out,

@@ -77,7 +77,7 @@ extern "C" int zeus_solve_from_noalloc(const zeus_problem* p, const double* x0, 
     q.H = reinterpret_cast<double*>(b + off_queue + 3 * align256(qc * sizeof(int)));
     q.cap = L.q_cap;
     q.hslots = nullptr;
-    if (L.stream) return ZEUS_EWORKSPACE;  // H slots do not fit the static array
+    if (L.stream && L.hslot_bytes > 0) return ZEUS_EWORKSPACE;  // H slots do not fit the array
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(b);
     ArgPair* parts = reinterpret_cast<ArgPair*>(b + off_parts);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -272,6 +272,77 @@ __device__ __forceinline__ void h_pass(T* __restrict__ Hs, int d, bool ident, bo
     __syncthreads();
 }
 
+// One L-BFGS step after the gradient at x_new: the pair (s, y) joins the
+// history if it passes the curvature test (as in Alg. 4's update), then
+// p = -H g_new by the two-loop recursion (Nocedal & Wright, Alg. 7.4) with
+// the initial matrix gamma I, gamma = s'y / y'y of the newest pair.  Dot
+// products are FP64 block sums of T products (the FP32 form's guards);
+// q and r live in u.
+template <class T>
+__device__ __forceinline__ void lbfgs_step(const T* x, const T* xn, const T* g, const T* gn,
+                                           T* pv, T* u, T* Sm, T* Ym, double* rho_m,
+                                           double* gam_m, double* al_m, int m, int& npair,
+                                           int& head, int d, double* red) {
+    const int tid = threadIdx.x, NT = blockDim.x;
+    double v3[3] = {0.0, 0.0, 0.0};
+    for (int j = tid; j < d; j += NT) {
+        const T sj = xn[j] - x[j], yj = gn[j] - g[j];
+        v3[0] += (double)(yj * sj);
+        v3[1] += (double)(sj * sj);
+        v3[2] += (double)(yj * yj);
+    }
+    block_sum<3>(v3, red);
+    if (v3[0] > 1e-12 * sqrt(v3[1]) * sqrt(v3[2])) {
+        int slot;
+        if (npair < m) {
+            slot = (head + npair) % m;
+            ++npair;
+        } else {  // drop the oldest
+            slot = head;
+            head = (head + 1) % m;
+        }
+        T* sr = Sm + (size_t)slot * d;
+        T* yr = Ym + (size_t)slot * d;
+        for (int j = tid; j < d; j += NT) {
+            sr[j] = xn[j] - x[j];
+            yr[j] = gn[j] - g[j];
+        }
+        if (tid == 0) {
+            rho_m[slot] = 1.0 / v3[0];
+            gam_m[slot] = v3[0] / v3[2];
+        }
+    }
+    for (int j = tid; j < d; j += NT) u[j] = gn[j];  // q = g_new
+    for (int i = npair - 1; i >= 0; --i) {            // newest to oldest
+        const int sl = (head + i) % m;
+        const T* sr = Sm + (size_t)sl * d;
+        const T* yr = Ym + (size_t)sl * d;
+        double v1[1] = {0.0};
+        for (int j = tid; j < d; j += NT) v1[0] += (double)(sr[j] * u[j]);
+        block_sum<1>(v1, red);  // its barriers also publish rho_m of a new pair
+        const double a = rho_m[sl] * v1[0];
+        if (tid == 0) al_m[i] = a;
+        const T at = T(a);
+        for (int j = tid; j < d; j += NT) u[j] = fma(-at, yr[j], u[j]);
+    }
+    if (npair > 0) {
+        const T gt = T(gam_m[(head + npair - 1) % m]);
+        for (int j = tid; j < d; j += NT) u[j] = gt * u[j];  // r = gamma q
+    }
+    for (int i = 0; i < npair; ++i) {  // oldest to newest
+        const int sl = (head + i) % m;
+        const T* sr = Sm + (size_t)sl * d;
+        const T* yr = Ym + (size_t)sl * d;
+        double v1[1] = {0.0};
+        for (int j = tid; j < d; j += NT) v1[0] += (double)(yr[j] * u[j]);
+        block_sum<1>(v1, red);
+        const T c = T(al_m[i] - rho_m[sl] * v1[0]);
+        for (int j = tid; j < d; j += NT) u[j] = fma(c, sr[j], u[j]);
+    }
+    for (int j = tid; j < d; j += NT) pv[j] = -u[j];
+    __syncthreads();
+}
+
 struct StreamShared {
     int item;
     int status;
@@ -281,7 +352,10 @@ struct StreamShared {
     double red[(kStreamWarps + 1) * 2 * kStreamTrials];
 };
 
-template <int OBJ, int GRAD, class T>
+// LB = false: dense H streamed from its HBM slot (the pass above).
+// LB = true: L-BFGS (the paper's future work, Section VI) with the m most
+// recent pairs in shared memory and the two-loop recursion for p; no H.
+template <int OBJ, int GRAD, class T, bool LB>
 __global__ void __launch_bounds__(kStreamThreads, 4)
     bfgs_stream_kernel(const zeus_problem p, const double* x0, double* x_out,
                        double* __restrict__ f_out, double* __restrict__ gnorm_out,
@@ -301,7 +375,15 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     T* Av = hy + d;
     T* Bv = Av + d;
     T* u = Bv + d;
-    T* Hs = hslots + (size_t)blockIdx.x * d * d;
+    T* Hs = LB ? nullptr : hslots + (size_t)blockIdx.x * d * d;
+    // L-BFGS history: m pairs (ring, slot of the i-th oldest = (head + i) % m)
+    const int lm = LB ? p.lbfgs_m : 0;
+    T* Sm = u + d;
+    T* Ym = Sm + (size_t)lm * d;
+    double* rho_m = reinterpret_cast<double*>(
+        smem_raw + ((((size_t)10 * d + 2 * (size_t)lm * d) * sizeof(T) + 7) & ~size_t(7)));
+    double* gam_m = rho_m + lm;  // s'y / y'y of each pair (the initial scaling)
+    double* al_m = gam_m + lm;   // alpha of the first loop
 
     const bool use_target = !isnan(p.target_f);
     const bool use_stop = use_target || p.required_converged > 0;
@@ -322,6 +404,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
         double f0 = sh.vals[0];
         for (int j = tid; j < d; j += NT) pv[j] = -g[j];  // H_0 = I
         bool ident = true, corr = false;
+        int npair = 0, head = 0;  // L-BFGS pairs stored, oldest slot
         int k = 0, feval = 0, status = ZEUS_RUN_MAX_ITER;
         unsigned long long n_read = 0, n_write = 0;  // H passes through HBM
         double gnorm = 0.0;
@@ -360,6 +443,8 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
             if (!(ddir < 0.0)) {  // restart from H = I
                 ident = true;
                 corr = false;
+                npair = 0;
+                head = 0;
                 double v1[1] = {0.0};
                 for (int j = tid; j < d; j += NT) {
                     pv[j] = -g[j];
@@ -406,6 +491,18 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
                 fn = sh.vals[0];
             }
             block_gradient<OBJ, GRAD>(xn, gn, d, sh.red);
+            if (LB) {
+                lbfgs_step<T>(x, xn, g, gn, pv, u, Sm, Ym, rho_m, gam_m, al_m, lm, npair, head, d,
+                              sh.red);
+                for (int j = tid; j < d; j += NT) {
+                    x[j] = xn[j];
+                    g[j] = gn[j];
+                }
+                f0 = fn;
+                ++k;
+                __syncthreads();
+                continue;
+            }
             // ---- the pass: H_k = H_{k-1} + C_{k-1}, u = H_k g_{k+1}
             if (ident && !corr) {
                 for (int j = tid; j < d; j += NT) u[j] = gn[j];
@@ -503,6 +600,11 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
 
 size_t stream_smem(int d, size_t tsize) { return 10 * (size_t)d * tsize; }
 
+size_t lbfgs_smem(int d, int m, size_t tsize) {
+    return ((((size_t)10 * d + 2 * (size_t)m * d) * tsize + 7) & ~size_t(7)) +
+           3 * (size_t)m * sizeof(double);
+}
+
 // About four blocks per SM, and the starts spread evenly over the rounds
 // (each block takes a start, runs it to the end, takes the next).
 int stream_blocks(const zeus_problem& p) {
@@ -517,7 +619,16 @@ template <int OBJ, int GRAD, class T>
 static cudaError_t stream_go(const zeus_problem& p, const double* x0, double* x_out, double* f_out,
                              double* gnorm_out, int32_t* status_out, int32_t* iters_out,
                              Ctrl* ctrl, void* hslots, cudaStream_t st) {
-    auto kern = bfgs_stream_kernel<OBJ, GRAD, T>;
+    if (p.lbfgs_m > 0) {
+        auto kl = bfgs_stream_kernel<OBJ, GRAD, T, true>;
+        const size_t sl = lbfgs_smem(p.dim, p.lbfgs_m, sizeof(T));
+        cudaError_t e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+        if (e != cudaSuccess) return e;
+        kl<<<stream_blocks(p), kStreamThreads, sl, st>>>(p, x0, x_out, f_out, gnorm_out, status_out,
+                                                         iters_out, ctrl, nullptr);
+        return cudaGetLastError();
+    }
+    auto kern = bfgs_stream_kernel<OBJ, GRAD, T, false>;
     const size_t sm = stream_smem(p.dim, sizeof(T));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

@@ -77,6 +77,7 @@ def test_defaults(z):
     dict(required_converged=-2), dict(grad_tol=-1.0), dict(grad_tol=float("nan")), dict(w=float("inf")),
     dict(armijo_c=0.0), dict(armijo_c=1.0), dict(backtrack=1.0), dict(backtrack=0.0), dict(grad_mode=2),
     dict(start_from_pbest=2), dict(threads_per_start=3), dict(threads_per_start=32), dict(threads_per_start=512), dict(precision=5),
+    dict(lbfgs_m=-1), dict(lbfgs_m=65),
 ])
 def test_validation_rejects(z, kw):
     assert z.zeus_validate(z.Problem(**kw)) == z._capi.ZEUS_EINVAL
@@ -86,6 +87,7 @@ def test_validation_rejects(z, kw):
     dict(objective="rastrigin", dim=1), dict(objective="quadratic", dim=1), dict(objective="ackley", dim=4096),
     dict(n_starts=1), dict(pso_iters=0), dict(bfgs_max_iters=0), dict(grad_mode="adjoint"),
     dict(threads_per_start=128), dict(threads_per_start=1), dict(start_from_pbest=1), dict(precision="fp32_guarded"), dict(required_converged=3), dict(target_f=1e-6),
+    dict(lbfgs_m=1), dict(lbfgs_m=64, dim=1000),
 ])
 def test_validation_accepts(z, kw):
     assert z.zeus_validate(z.Problem(**kw)) == 0
@@ -213,3 +215,21 @@ def test_batch_rejects(z):
                               None, None, None, None) == EINVAL
     assert L.zeus_batch_solve(C.byref(pl), None, 0, C.c_void_p(256), C.c_void_p(256), None, None,
                               None, None, None) == EWS
+
+
+def test_lbfgs_plan(z):
+    p = z.Problem(objective="rosenbrock", dim=1024, n_starts=2048, lbfgs_m=8, precision="fp32_guarded")
+    pl = z.zeus_plan_info(p)
+    assert pl["lbfgs"] == 1 and pl["stream"] == 0 and pl["narrow"] == 0 and pl["h_bytes"] == 0
+    dense = z.zeus_plan_info(p.replace(lbfgs_m=0))
+    assert dense["stream"] == 1 and dense["lbfgs"] == 0
+    # no H slots: the workspace is far smaller than the dense streamed one
+    assert z.zeus_workspace_size(p) * 50 < z.zeus_workspace_size(p.replace(lbfgs_m=0))
+    for bad in (dict(objective="goldstein_price", dim=2), dict(threads_per_start=128),
+                dict(threads_per_start=1), dict(dim=4096, precision="fp64", lbfgs_m=64)):
+        with pytest.raises(z.ZeusError) as e:
+            z.zeus_plan_info(p.replace(**bad))
+        assert e.value.code == z._capi.ZEUS_EUNSUPPORTED
+    assert z.zeus_plan_info(p.replace(threads_per_start=256))["lbfgs"] == 1
+    with pytest.raises(z.ZeusError):  # not batched
+        z.zeus_batch_plan_make([z.Problem(), p.replace(precision="fp64", dim=20, n_starts=8)])
