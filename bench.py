@@ -53,6 +53,8 @@ def _args():
     ap.add_argument("--grad-mode", default="forward", choices=["forward", "adjoint"])
     ap.add_argument("--lanes", type=int, default=0, help="threads per start (0 = automatic)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_guarded"])
+    ap.add_argument("--lbfgs-m", type=int, default=0,
+                    help="L-BFGS with this many pairs instead of the dense inverse Hessian")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--form-seeds", type=int, default=5)
@@ -188,6 +190,8 @@ def run_zeus(a):
         return run_batch_main(a, z, dev, world, rank, local)
     fields = workloads.workload(a.workload, grad_mode=a.grad_mode, threads_per_start=a.lanes,
                                 precision=a.precision)
+    if a.lbfgs_m:
+        fields["lbfgs_m"] = a.lbfgs_m
     if a.starts:
         fields["n_starts"] = a.starts
     if a.iters:
@@ -278,7 +282,23 @@ def run_zeus(a):
     # events around zeus_solve_from on its stream
     plan = z.zeus_plan_info(pc)
     bfgs_s = statistics.mean(bfgs_ms) / 1e3
-    if plan["stream"]:
+    if plan["lbfgs"]:
+        # L-BFGS: per start-iteration the two loops over the m pairs (a dot
+        # product and an update of length d each, FMA = 2: 8 m d) plus the
+        # O(d) work of the dense model's linear terms; no H traffic.  FP32
+        # peak: 152 SMs x 128 lanes x 2 x 2.07 GHz (nominal unit count and
+        # clock); FP64: measured.
+        m = a.lbfgs_m
+        flops = iters_per_step * (8.0 * m * d + 65.0 * d + 10.0) + feval_per_step * (30.0 * d + 3.0)
+        peak = 80.5 if a.precision == "fp32_guarded" else FP64_PEAK_TFLOPS
+        achieved = flops / bfgs_s / 1e12
+        roof = {"kernel": "bfgs_stream_kernel, L-BFGS variant (+ argmin)", "bound": "alu",
+                "achieved": round(achieved, 5), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 5), "traffic": None,
+                "peak_source": ("FP32: nominal 152 SMs x 128 lanes x 2 x 2.07 GHz" if peak != FP64_PEAK_TFLOPS
+                                else "FP64 FMA rate measured on this GB300"),
+                "flops_per_launch": flops, "launch_ms": round(bfgs_s * 1e3, 3)}
+    elif plan["stream"]:
         # H streamed from HBM: one H of d^2 sizeof(T) bytes per pass that
         # read or wrote it (the kernel counts them; at most 2 per
         # start-iteration, none while H = I)
@@ -324,7 +344,7 @@ def run_zeus(a):
         "data": "synthetic (seeded Philox draws of the method itself; no dataset)",
         "config": {"workload": a.workload, "objective": p.objective, "dim": d, "n_starts": n,
                    "pso_iters": p.pso_iters, "bfgs_max_iters": p.bfgs_max_iters,
-                   "grad_mode": a.grad_mode, "precision": a.precision,
+                   "grad_mode": a.grad_mode, "precision": a.precision, "lbfgs_m": a.lbfgs_m,
                    "start_iters_per_step": iters_per_step, "feval_per_step": feval_per_step,
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "parallelism": f"replicas x{world}"},
