@@ -53,6 +53,10 @@ def _args():
     ap.add_argument("--grad-mode", default="forward", choices=["forward", "adjoint"])
     ap.add_argument("--lanes", type=int, default=0, help="threads per start (0 = automatic)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_guarded"])
+    ap.add_argument("--study", action="store_true",
+                    help="the early-stop study instead of the benchmark: PSO updates vs time and "
+                         "correct solutions (5-D Rastrigin, Rosenbrock), correct solutions vs d")
+    ap.add_argument("--study-runs", type=int, default=10)
     ap.add_argument("--lbfgs-m", type=int, default=0,
                     help="L-BFGS with this many pairs instead of the dense inverse Hessian")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -777,8 +781,72 @@ def run_reference(a):
     }), flush=True)
 
 
+def _study_run(z, fields, dev, xstar):
+    """One early-stopped solve: (ms, correct starts).  Correct: the start
+    converged (||g|| < tol) within Euclidean distance 0.5 of the global
+    minimiser, the paper's N_correct (Section V)."""
+    import torch
+    p = z.Problem(**{k: v for k, v in fields.items() if k in z.Problem.__dataclass_fields__})
+    pc = p.to_c()
+    ws = z.new_workspace(pc, dev)
+    x = torch.empty(p.n_starts, p.dim, dtype=torch.float64, device=dev)
+    st = torch.empty(p.n_starts, dtype=torch.int32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    z.zeus_solve(pc, ws, x, None, None, st, None, None)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    dist = torch.linalg.norm(x - torch.tensor(xstar, dtype=torch.float64, device=dev), dim=1)
+    correct = int(((st == 1) & (dist < 0.5)).sum().item())
+    return e0.elapsed_time(e1), correct
+
+
+def run_study(a):
+    """The early-stop study on synthetic inputs (the shapes of the paper's
+    PSO-iteration and dimension experiments, Section V): every run stops
+    once 100 starts have converged (required_c, Alg. 10).  Prints one JSON
+    line of medians and quartiles over the runs."""
+    import torch
+    import paper_2603_28770_gb300 as z
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    runs = a.study_runs
+
+    def quart(v):
+        q = np.percentile(np.asarray(v, dtype=np.float64), [25, 50, 75])
+        return [round(float(t), 3) for t in q]
+
+    out = {"study": "early stop at 100 converged starts", "runs": runs, "pso_iters": {}, "dims": {}}
+    for obj, box, xs in (("rastrigin", (-5.12, 5.12), 0.0), ("rosenbrock", (-5.0, 5.0), 1.0)):
+        rows = []
+        for T in (0, 1, 2, 5, 10, 20):
+            ts, nc = [], []
+            for r in range(runs + 1):  # the first run warms up
+                f = dict(objective=obj, dim=5, lower=box[0], upper=box[1], n_starts=16384,
+                         pso_iters=T, bfgs_max_iters=1000, required_converged=100, seed=500 + r)
+                ms, c = _study_run(z, f, dev, [xs] * 5)
+                if r:
+                    ts.append(ms)
+                    nc.append(c)
+            rows.append({"T": T, "time_ms_q": quart(ts), "n_correct_q": quart(nc)})
+        out["pso_iters"][f"{obj}5d_n16384"] = rows
+    rows = []
+    for d in range(1, 11):
+        nc = []
+        for r in range(runs):
+            f = dict(objective="rastrigin", dim=d, lower=-5.12, upper=5.12, n_starts=100000,
+                     pso_iters=5, bfgs_max_iters=1000, required_converged=100, seed=900 + r)
+            nc.append(_study_run(z, f, dev, [0.0] * d)[1])
+        rows.append({"d": d, "n_correct_q": quart(nc)})
+    out["dims"]["rastrigin_n100000_T5"] = rows
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     args = _args()
+    if args.study:
+        run_study(args)
+        sys.exit(0)
     if args.impl == "reference":
         run_reference(args)
     else:
