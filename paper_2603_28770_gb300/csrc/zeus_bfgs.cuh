@@ -475,8 +475,13 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             pv[r] = -a;
         }
         const int bad = __syncthreads_or(b);
+        // g'g and g'p on roles 0 and 1 (one warp, one instruction stream:
+        // an FP64 warp instruction costs the same for one lane or two)
+        double dot01 = 0.0;
+        if (tid < 2) dot01 = ordered_dot(g, tid == 0 ? g : pv, d);
+        if (tid == 1) sh.red[0] = dot01;
         if (tid == 0) {
-            gnorm = sqrt(ordered_dot(g, g, d));
+            gnorm = sqrt(dot01);
             sh.red[1] = gnorm;
             int st = -1;
             if (k >= K) {
@@ -499,8 +504,6 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 atomicExch(&ctrl->stop, 1);
             }
             sh.status = st;
-        } else if (tid == 32) {  // g'p, on another warp
-            sh.red[0] = ordered_dot(g, pv, d);
         }
         __syncthreads();
         gnorm = sh.red[1];
@@ -577,11 +580,8 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             g[j] = gn[j] - g[j];
         }
         __syncthreads();
-        if (tid < 96 && (tid & 31) == 0) {  // y's, s's, y'y on three warps
-            const int w = tid >> 5;
-            sh.red[w] = w == 0 ? ordered_dot(g, sv, d)
-                               : (w == 1 ? ordered_dot(sv, sv, d) : ordered_dot(g, g, d));
-        }
+        if (tid < 3)  // y's, s's, y'y on roles 0-2 (one warp, one instruction stream)
+            sh.red[tid] = ordered_dot(tid == 1 ? sv : g, tid == 2 ? g : sv, d);
         for (int r = row_of(tid, NT); r < d; r += NT) {  // Hy into p (the direction is spent)
             const T* Hr = H + r * d;
             T a = T(0);
