@@ -262,6 +262,10 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
                 for (int e = 0; e < d * d; ++e) Hq[e] = H[e];
                 T* xq = reinterpret_cast<T*>(x_out + s * d);  // the row holds x until the end
                 for (int j = 0; j < d; ++j) xq[j] = x[j];
+                if (q.ready) {  // a consumer running alongside may take the entry now
+                    __threadfence();
+                    atomicExch(q.ready + slot, 1);
+                }
                 return;
             }
         }
@@ -412,7 +416,8 @@ template <int OBJ, int GRAD, class T>
 __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, const long long s,
                                          int k, int feval, const T* Hq, const T* xq,
                                          const RunIO& io, WideShared& sh,
-                                         unsigned char* smem_raw, const int tid) {
+                                         unsigned char* smem_raw, const int tid,
+                                         const bool peer = false) {
     const int NT = blockDim.x;
     const int d = p.dim;
     T* H = reinterpret_cast<T*>(smem_raw);
@@ -444,13 +449,13 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         }
         sh.adj.c1 = sh.adj.c2 = 0.0;
     }
-    if (xq) {
-        for (int j = tid; j < d; j += NT) x[j] = xq[j];
+    if (xq) {  // peer: written by another block of this launch, read past L1
+        for (int j = tid; j < d; j += NT) x[j] = peer ? __ldcg(xq + j) : xq[j];
     } else {
         for (int j = tid; j < d; j += NT) x[j] = T(io.x0[s * d + j]);
     }
     if (Hq) {
-        for (int e = tid; e < d * d; e += NT) H[e] = Hq[e];
+        for (int e = tid; e < d * d; e += NT) H[e] = peer ? __ldcg(Hq + e) : Hq[e];
     } else {
         for (int e = tid; e < d * d; e += NT) H[e] = (e / d == e % d) ? T(1) : T(0);
     }

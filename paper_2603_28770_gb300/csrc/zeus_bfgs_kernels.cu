@@ -56,11 +56,134 @@ __global__ void __launch_bounds__(kWideThreads)
     }
 }
 
+// Narrow and wide in one cooperative launch.  Every block first takes lane
+// tiles (tile starts, one lane each, with the hand-over budget); once no
+// tile is left it serves the hand-over queue, so the starts that exceed
+// the budget early run on blocks that have no tile while the tiles are
+// still in progress.  A server waits for a queue entry only while a tile
+// may still produce it; the launch is cooperative, so every block is
+// resident and the waits end.  Each wait is bounded (then the error word
+// is set and the block stops serving).
+constexpr unsigned kFusedSpinLimit = 1u << 23;  // polls of 256 ns: about 2 s
+
+template <int OBJ, int GRAD, class T>
+__global__ void __launch_bounds__(kWideThreads)
+    bfgs_fused_kernel(const zeus_problem p, const int stride, const int budget, const int tile,
+                      const int n_tiles, const int W, const double* x0, double* x_out,
+                      double* __restrict__ f_out, double* __restrict__ gnorm_out,
+                      int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
+                      Ctrl* __restrict__ ctrl, const Queue q) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ WideShared sh;
+    const int tid = wide_role(blockDim.x);
+    const RunIO io{x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl};
+    T* smem = reinterpret_cast<T*>(smem_raw);
+    for (;;) {  // lane tiles
+        __syncthreads();
+        if (threadIdx.x == 0) sh.item = (int)atomicAdd(&ctrl->tile_head, 1u);
+        __syncthreads();
+        const int t = sh.item;
+        if (t >= n_tiles) break;
+        const long long s = (long long)t * tile + threadIdx.x;
+        if ((int)threadIdx.x < tile && s < p.n_starts)
+            narrow_run<OBJ, GRAD, T>(p, s, smem + (size_t)threadIdx.x * stride, budget, io, ctrl, q,
+                                     0);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&ctrl->tiles_done, 1u);
+        }
+    }
+    for (;;) {  // the hand-over queue
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int item = (int)atomicAdd(&ctrl->q_head, 1u);
+            int go = 0;
+            if (item < q.cap) {
+                volatile int* rd = q.ready + item;
+                for (unsigned spin = 0;; ++spin) {
+                    if (*rd) {
+                        go = 1;
+                        break;
+                    }
+                    if (*((volatile unsigned*)&ctrl->tiles_done) >= (unsigned)n_tiles) {
+                        __threadfence();
+                        if (*rd) {
+                            go = 1;
+                            break;
+                        }
+                        const unsigned cnt = *((volatile unsigned*)&ctrl->q_count);
+                        if ((unsigned)item >= min(cnt, (unsigned)q.cap)) break;  // never written
+                    }
+                    if (spin >= kFusedSpinLimit) {
+                        atomicExch(&ctrl->error, 1);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+            sh.item = go ? item : -1;
+        }
+        __syncthreads();
+        const int item = sh.item;
+        if (item < 0) break;
+        __threadfence();
+        const long long s = __ldcg(q.start + item);
+        const T* Hq = reinterpret_cast<const T*>(q.H) + (size_t)item * p.dim * p.dim;
+        const T* xq = reinterpret_cast<const T*>(x_out + s * p.dim);
+        wide_run<OBJ, GRAD, T>(p, W, s, __ldcg(q.k + item), __ldcg(q.feval + item), Hq, xq, io, sh,
+                               smem_raw, tid, true);
+    }
+}
+
+// Cooperative fused launch of the narrow and wide kernels, if the device
+// offers cooperative launches; returns cudaErrorNotSupported otherwise.
+template <int OBJ, int GRAD, class T>
+static cudaError_t fused_go(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
+                            double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
+                            int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st) {
+    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (!coop) return cudaErrorNotSupported;
+    // tiles of 32..128 lanes: as many as keep a block within 56 KB of shared
+    // memory (four blocks per SM), at least one warp
+    const size_t row = (size_t)L.stride * sizeof(T);
+    int tile = (int)((56u << 10) / row) / 32 * 32;
+    if (tile > kWideThreads) tile = kWideThreads;
+    if (tile < 32) tile = 32;
+    const size_t smem = (size_t)tile * row > L.wide_smem ? (size_t)tile * row : L.wide_smem;
+    auto kf = bfgs_fused_kernel<OBJ, GRAD, T>;
+    e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, kWideThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorNotSupported;
+    zeus_problem pp = p;
+    int stride = L.stride, budget = L.budget, W = L.W;
+    int n_tiles = (int)((p.n_starts + tile - 1) / tile);
+    const double* xin = x0;
+    double *xo = x_out, *fo = f_out, *go = gnorm_out;
+    int32_t *so = status_out, *io = iters_out;
+    Ctrl* c = ctrl;
+    Queue qq = q;
+    void* args[] = {&pp, &stride, &budget, &tile, &n_tiles, &W, &xin, &xo, &fo, &go, &so, &io, &c, &qq};
+    return cudaLaunchCooperativeKernel((const void*)kf, dim3(sms * per_sm), dim3(kWideThreads), args,
+                                       smem, st);
+}
+
 template <int OBJ, int GRAD, class T>
 static cudaError_t bfgs_go(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
                            double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
                            int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st) {
     cudaError_t e;
+    if (L.narrow && L.budget > 0 && q.ready) {
+        e = fused_go<OBJ, GRAD, T>(p, L, x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl,
+                                   q, st);
+        if (e != cudaErrorNotSupported) return e;
+        cudaGetLastError();  // not offered: the two launches below
+    }
     if (L.narrow) {
         auto kn = bfgs_narrow_kernel<OBJ, GRAD, T>;
         e = cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize,

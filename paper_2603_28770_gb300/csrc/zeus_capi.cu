@@ -64,6 +64,8 @@ Layout layout_for(const zeus_problem& p, const BfgsLaunch& L) {
     size_t off = 0;
     lay.ctrl = off;
     off += align256(sizeof(Ctrl));
+    lay.q_ready = off;  // zeroed with the control block
+    off += align256(qc * sizeof(int));
     lay.partials = off;
     off += align256(nparts * sizeof(ArgPair));
     lay.f_tmp = off;
@@ -113,6 +115,7 @@ Queue queue_for(void* ws, const Layout& lay, const BfgsLaunch& L) {
     q.H = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + lay.q_h);
     q.cap = L.q_cap;
     q.hslots = reinterpret_cast<char*>(ws) + lay.hslots;
+    q.ready = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + lay.q_ready);
     return q;
 }
 
@@ -231,7 +234,8 @@ int zeus_solve(const zeus_problem* p, void* workspace, size_t workspace_bytes, d
     double* pf = at<double>(workspace, lay.pf);
     double* gx = at<double>(workspace, lay.gx);
     double* f = f_out ? f_out : at<double>(workspace, lay.f_tmp);
-    cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
+    // the control block and the hand-over queue's ready flags start at zero
+    cudaError_t e = cudaMemsetAsync(ctrl, 0, lay.partials - lay.ctrl, st);
     if (e != cudaSuccess) return ZEUS_ECUDA;
     e = launch_pso(*p, lanes_for_dim(p->dim), x_out, vv, px, pf, gx, ctrl, parts, result, st);
     if (e != cudaSuccess) return ZEUS_ECUDA;
@@ -257,7 +261,7 @@ int zeus_solve_from(const zeus_problem* p, const double* x0, void* workspace,
     cudaStream_t st = as_stream(stream);
     Ctrl* ctrl = at<Ctrl>(workspace, lay.ctrl);
     double* f = f_out ? f_out : at<double>(workspace, lay.f_tmp);
-    cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
+    cudaError_t e = cudaMemsetAsync(ctrl, 0, lay.partials - lay.ctrl, st);  // control, ready flags
     if (e != cudaSuccess) return ZEUS_ECUDA;
     e = launch_bfgs(*p, L, x0, x_out, f, gnorm_out, status_out, iters_out, ctrl,
                     queue_for(workspace, lay, L), st);

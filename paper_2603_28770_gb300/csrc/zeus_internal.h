@@ -19,7 +19,7 @@ struct Ctrl {
     int error;                       // device error word
     unsigned int q_count;            // starts handed from the narrow to the wide kernel
     unsigned int q_head;             // next queue item the wide kernel takes
-    unsigned int pad0;
+    unsigned int tile_head;          // next lane tile of the fused kernel
     unsigned long long n_conv;       // starts that converged
     unsigned long long total_iters;  // sum of completed BFGS iterations
     unsigned long long total_feval;  // sum of line-search evaluations
@@ -27,7 +27,9 @@ struct Ctrl {
     long long gbest_idx;             // and its particle
     unsigned long long h_reads;      // H passes that read a start's H from HBM (streamed H)
     unsigned long long h_writes;     // H passes that wrote it back
-    unsigned long long pad1[22];
+    unsigned int tiles_done;         // lane tiles the fused kernel has finished
+    unsigned int pad2;
+    unsigned long long pad1[21];
 };
 static_assert(sizeof(Ctrl) == 256, "control block is one 256-byte segment");
 
@@ -43,7 +45,7 @@ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Workspace carve-up (offsets in bytes from the workspace base).
 struct Layout {
-    size_t ctrl, partials, f_tmp, v, px, pf, gx, q_start, q_k, q_feval, q_h, hslots, total;
+    size_t ctrl, q_ready, partials, f_tmp, v, px, pf, gx, q_start, q_k, q_feval, q_h, hslots, total;
 };
 
 // Per-problem inputs and outputs of a BFGS run (pointers already offset to
@@ -68,6 +70,7 @@ struct Queue {
     int cap;
     void* hslots; // H slots of the streaming kernel
     long long hstride = 0;  // elements per H entry (0: d*d of the run's problem)
+    int* ready = nullptr;   // [cap] 1 once entry i is written (fused kernel); zeroed per call
 };
 
 constexpr int kNarrowThreads = 128;
