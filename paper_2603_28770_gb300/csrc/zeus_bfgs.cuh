@@ -213,6 +213,7 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
     double f0 = seq_value<OBJ>(AtPoint<T>{x}, d);
 
     int k = 0, status = ZEUS_RUN_MAX_ITER, feval = 0;
+    bool ls_failed = false;  // the previous iteration's search accepted no trial
     double gnorm;
     for (;;) {
         double gg = 0.0;
@@ -249,10 +250,25 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
             atomicExch(&ctrl->stop, 1);
             break;
         }
-        if (budget > 0 && k + feval >= budget) {
+        if (budget > 0 && (k + feval >= budget || ls_failed)) {
             // hand the start over to the wide kernel at the top of iteration k
-            const unsigned slot = atomicAdd(&qc->q_count, 1u);
-            if (slot < (unsigned)q.cap) {
+            // (work budget spent, or the last line search exhausted its
+            // trials: such a start usually keeps failing, and each failing
+            // search costs L sweeps on one lane)
+            // a start whose searches take many trials (the last one failed,
+            // or more than two evaluations per iteration so far) likely
+            // keeps failing: it goes to the long entries when the consumer
+            // keeps them apart (fused kernel)
+            unsigned slot = ~0u;
+            if (q.long_cap > 0 && (ls_failed || feval > 2 * k)) {
+                const unsigned h = atomicAdd(&qc->q_count_long, 1u);
+                if (h < (unsigned)q.long_cap) slot = (unsigned)(q.cap - q.long_cap) + h;
+            }
+            if (slot == ~0u) {  // the other entries (also when the long ones are full)
+                const unsigned h = atomicAdd(&qc->q_count, 1u);
+                if (h < (unsigned)(q.cap - q.long_cap)) slot = h;
+            }
+            if (slot != ~0u) {
                 q.start[slot] = (int)s;
                 if (q.prob) q.prob[slot] = prob;
                 q.k[slot] = k;
@@ -304,6 +320,7 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
             for (int j = 0; j < d; ++j) xn[j] = x[j] + a * pv[j];
             fn = seq_value<OBJ>(AtPoint<T>{xn}, d);
         }
+        ls_failed = !accepted;
         {
             const AdjShared a = grad_prep<OBJ, GRAD>(xn, d);
             for (int i = 0; i < d; ++i) gn[i] = grad_component<OBJ, GRAD>(xn, d, i, a);

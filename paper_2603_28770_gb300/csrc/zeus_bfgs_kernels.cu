@@ -58,13 +58,50 @@ __global__ void __launch_bounds__(kWideThreads)
 
 // Narrow and wide in one cooperative launch.  Every block first takes lane
 // tiles (tile starts, one lane each, with the hand-over budget); once no
-// tile is left it serves the hand-over queue, so the starts that exceed
-// the budget early run on blocks that have no tile while the tiles are
-// still in progress.  A server waits for a queue entry only while a tile
-// may still produce it; the launch is cooperative, so every block is
-// resident and the waits end.  Each wait is bounded (then the error word
-// is set and the block stops serving).
+// tile is left it serves the hand-over queue, so the starts handed over
+// early run on blocks that have no tile while the tiles are still in
+// progress.  Servers poll for entries while a tile may still produce one;
+// the launch is cooperative, so every block is resident and the polls
+// end.  Each poll loop is bounded (then the error word is set and the
+// block stops serving).
 constexpr unsigned kFusedSpinLimit = 1u << 23;  // polls of 256 ns: about 2 s
+
+__device__ __forceinline__ int smid_of() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return (int)r;
+}
+
+// waits (bounded) until entry `slot` is marked written
+__device__ __forceinline__ bool wait_ready(const Queue& q, int slot, Ctrl* ctrl) {
+    volatile int* rd = q.ready + slot;
+    for (unsigned spin = 0; !*rd; ++spin) {
+        if (spin >= kFusedSpinLimit) {
+            atomicExch(&ctrl->error, 1);
+            return false;
+        }
+        __nanosleep(256);
+    }
+    return true;
+}
+
+// Takes the next entry of the region [base, base + cap_r) counted by
+// *count if a producer has claimed it (it is then written shortly: waits
+// for its flag); -1 if there is none now.  Never waits for production.
+__device__ __forceinline__ int claim_now(unsigned* head, unsigned* count, int base, int cap_r,
+                                         const Queue& q, Ctrl* ctrl) {
+    for (;;) {
+        const unsigned h = *((volatile unsigned*)head);
+        const unsigned c = min(*((volatile unsigned*)count), (unsigned)cap_r);
+        if (h >= c) return -1;
+        if (atomicCAS(head, h, h + 1) == h) return wait_ready(q, base + (int)h, ctrl) ? base + (int)h : -1;
+    }
+}
+
+// region exhausted: every entry a producer claimed has been taken
+__device__ __forceinline__ bool drained(const unsigned* head, const unsigned* count, int cap_r) {
+    return *((volatile const unsigned*)head) >= min(*((volatile const unsigned*)count), (unsigned)cap_r);
+}
 
 template <int OBJ, int GRAD, class T>
 __global__ void __launch_bounds__(kWideThreads)
@@ -94,35 +131,48 @@ __global__ void __launch_bounds__(kWideThreads)
             atomicAdd(&ctrl->tiles_done, 1u);
         }
     }
-    for (;;) {  // the hand-over queue
+    // the hand-over queue.  Servers poll both regions and take only
+    // entries already claimed by a producer; an SM serves at most one long
+    // entry at a time until the tiles are done, so long runs spread over
+    // the SMs.  Every poll loop is bounded.
+    const int sm = smid_of();
+    const int ncap = q.cap - q.long_cap, lbase = q.cap - q.long_cap;
+    for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            const int item = (int)atomicAdd(&ctrl->q_head, 1u);
-            int go = 0;
-            if (item < q.cap) {
-                volatile int* rd = q.ready + item;
-                for (unsigned spin = 0;; ++spin) {
-                    if (*rd) {
-                        go = 1;
+            int item = -1, held = 0;
+            for (unsigned spin = 0;; ++spin) {
+                if (q.long_cap > 0 && sm < kMaxSMs && atomicCAS(q.sm_long + sm, 0, 1) == 0) {
+                    item = claim_now(&ctrl->q_head_long, &ctrl->q_count_long, lbase, q.long_cap, q,
+                                     ctrl);
+                    if (item >= 0) {
+                        held = 1;
                         break;
                     }
-                    if (*((volatile unsigned*)&ctrl->tiles_done) >= (unsigned)n_tiles) {
-                        __threadfence();
-                        if (*rd) {
-                            go = 1;
-                            break;
-                        }
-                        const unsigned cnt = *((volatile unsigned*)&ctrl->q_count);
-                        if ((unsigned)item >= min(cnt, (unsigned)q.cap)) break;  // never written
-                    }
-                    if (spin >= kFusedSpinLimit) {
-                        atomicExch(&ctrl->error, 1);
-                        break;
-                    }
-                    __nanosleep(256);
+                    atomicExch(q.sm_long + sm, 0);
                 }
+                item = claim_now(&ctrl->q_head, &ctrl->q_count, 0, ncap, q, ctrl);
+                if (item >= 0) break;
+                if (*((volatile unsigned*)&ctrl->tiles_done) >= (unsigned)n_tiles) {
+                    __threadfence();  // the counts are final now
+                    if (q.long_cap > 0) {
+                        item = claim_now(&ctrl->q_head_long, &ctrl->q_count_long, lbase, q.long_cap,
+                                         q, ctrl);
+                        if (item >= 0) break;
+                    }
+                    if (drained(&ctrl->q_head, &ctrl->q_count, ncap) &&
+                        (q.long_cap == 0 ||
+                         drained(&ctrl->q_head_long, &ctrl->q_count_long, q.long_cap)))
+                        break;
+                }
+                if (spin >= kFusedSpinLimit) {
+                    atomicExch(&ctrl->error, 1);
+                    break;
+                }
+                __nanosleep(256);
             }
-            sh.item = go ? item : -1;
+            sh.item = item;
+            sh.status = held;
         }
         __syncthreads();
         const int item = sh.item;
@@ -131,8 +181,10 @@ __global__ void __launch_bounds__(kWideThreads)
         const long long s = __ldcg(q.start + item);
         const T* Hq = reinterpret_cast<const T*>(q.H) + (size_t)item * p.dim * p.dim;
         const T* xq = reinterpret_cast<const T*>(x_out + s * p.dim);
+        const int held = sh.status;
         wide_run<OBJ, GRAD, T>(p, W, s, __ldcg(q.k + item), __ldcg(q.feval + item), Hq, xq, io, sh,
                                smem_raw, tid, true);
+        if (threadIdx.x == 0 && held) atomicExch(q.sm_long + sm, 0);
     }
 }
 
@@ -168,6 +220,8 @@ static cudaError_t fused_go(const zeus_problem& p, const BfgsLaunch& L, const do
     int32_t *so = status_out, *io = iters_out;
     Ctrl* c = ctrl;
     Queue qq = q;
+    // long entries: half of the queue (and the per-SM table)
+    qq.long_cap = (q.sm_long && sms <= kMaxSMs) ? q.cap / 2 : 0;
     void* args[] = {&pp, &stride, &budget, &tile, &n_tiles, &W, &xin, &xo, &fo, &go, &so, &io, &c, &qq};
     return cudaLaunchCooperativeKernel((const void*)kf, dim3(sms * per_sm), dim3(kWideThreads), args,
                                        smem, st);

@@ -64,8 +64,10 @@ Layout layout_for(const zeus_problem& p, const BfgsLaunch& L) {
     size_t off = 0;
     lay.ctrl = off;
     off += align256(sizeof(Ctrl));
-    lay.q_ready = off;  // zeroed with the control block
+    lay.q_ready = off;  // zeroed with the control block, as is the per-SM table
     off += align256(qc * sizeof(int));
+    lay.q_smlong = off;
+    off += align256(kMaxSMs * sizeof(int));
     lay.partials = off;
     off += align256(nparts * sizeof(ArgPair));
     lay.f_tmp = off;
@@ -116,6 +118,7 @@ Queue queue_for(void* ws, const Layout& lay, const BfgsLaunch& L) {
     q.cap = L.q_cap;
     q.hslots = reinterpret_cast<char*>(ws) + lay.hslots;
     q.ready = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + lay.q_ready);
+    q.sm_long = reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + lay.q_smlong);
     return q;
 }
 

@@ -28,8 +28,10 @@ struct Ctrl {
     unsigned long long h_reads;      // H passes that read a start's H from HBM (streamed H)
     unsigned long long h_writes;     // H passes that wrote it back
     unsigned int tiles_done;         // lane tiles the fused kernel has finished
+    unsigned int q_count_long;       // entries handed over after a failed line search
+    unsigned int q_head_long;        // next such entry a server takes
     unsigned int pad2;
-    unsigned long long pad1[21];
+    unsigned long long pad1[20];
 };
 static_assert(sizeof(Ctrl) == 256, "control block is one 256-byte segment");
 
@@ -44,8 +46,10 @@ constexpr int kMaxReduceBlocks = 4096;  // argmin partials kept in the workspace
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Workspace carve-up (offsets in bytes from the workspace base).
+constexpr int kMaxSMs = 1024;  // size of the per-SM table of the fused kernel
+
 struct Layout {
-    size_t ctrl, q_ready, partials, f_tmp, v, px, pf, gx, q_start, q_k, q_feval, q_h, hslots, total;
+    size_t ctrl, q_ready, q_smlong, partials, f_tmp, v, px, pf, gx, q_start, q_k, q_feval, q_h, hslots, total;
 };
 
 // Per-problem inputs and outputs of a BFGS run (pointers already offset to
@@ -71,6 +75,9 @@ struct Queue {
     void* hslots; // H slots of the streaming kernel
     long long hstride = 0;  // elements per H entry (0: d*d of the run's problem)
     int* ready = nullptr;   // [cap] 1 once entry i is written (fused kernel); zeroed per call
+    int long_cap = 0;       // fused kernel: entries [cap - long_cap, cap) take the starts
+                            // whose last line search failed (likely long runs)
+    int* sm_long = nullptr; // [kMaxSMs] long entries in service per SM (fused kernel)
 };
 
 constexpr int kNarrowThreads = 128;
