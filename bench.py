@@ -333,7 +333,10 @@ def run_zeus(a):
         flops = fp64_flops(d, iters_per_step, feval_per_step)
         achieved = flops / bfgs_s / 1e12
         peak = FP64_PEAK_TFLOPS
-        roof = {"kernel": "bfgs_narrow_kernel + bfgs_wide_kernel (+ argmin)", "bound": "alu",
+        kname = ("bfgs_fused_kernel (lane tiles and hand-over service in one cooperative launch)"
+                 if plan["handover"] else
+                 ("bfgs_narrow_kernel" if plan["narrow"] else "bfgs_wide_kernel"))
+        roof = {"kernel": kname + " (+ argmin)", "bound": "alu",
                 "achieved": round(achieved, 5), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 5), "traffic": None,
                 "peak_source": "FP64 FMA rate measured on this GB300 (1.25 TFLOP/s, equal to "
