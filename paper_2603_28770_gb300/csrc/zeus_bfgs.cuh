@@ -571,19 +571,15 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 sh.ok[tid] = (m0 + tid < L && ft <= f0 + cA * al[m0 + tid] * ddir) ? 1 : 0;
             }
             __syncthreads();
-            if (tid == 0) {
-                int am = -1;
-                for (int mm = 0; mm < nw; ++mm)
-                    if (sh.ok[mm]) {
-                        am = m0 + mm;
-                        break;
-                    }
-                sh.accepted_m = am;
-                if (am >= 0) sh.red[2] = fb[am - m0];
-                else if (m0 + nw == L + 1) sh.red[2] = fb[L - m0];  // every trial failed
-            }
-            __syncthreads();
-            acc_m = sh.accepted_m;
+            // every thread finds the first accepted trial itself (no further
+            // barrier: the next chunk writes ok and fb only after its terms)
+            for (int mm = 0; mm < nw; ++mm)
+                if (sh.ok[mm]) {
+                    acc_m = m0 + mm;
+                    break;
+                }
+            if (acc_m >= 0) fn = fb[acc_m - m0];
+            else if (m0 + nw == L + 1) fn = fb[L - m0];  // every trial failed
             feval += (acc_m >= 0) ? (acc_m - m0 + 1) : min(nw, L - m0);
             m0 += nw;
         }
@@ -594,7 +590,6 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         // ---- gradient at x_new
         wide_gradient<OBJ, GRAD>(xn, gn, d, tid, sh);
         __syncthreads();
-        fn = sh.red[2];
         // ---- curvature pair; H y formed alongside its sums (used only if
         // the pair passes the curvature test)
         for (int j = tid; j < d; j += NT) {  // s into sv, y over g
@@ -629,7 +624,8 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 H[e] = mv_fma(sv[c], T(sc0[r]), mv_fma(pv[c], T(sc1[r]), H[e]));
             }
         }
-        __syncthreads();
+        // x, g <- x_new, g_new in the same phase (the update reads neither;
+        // y, kept in g, was last read by y'Hy before the previous barrier)
         for (int j = tid; j < d; j += NT) {
             x[j] = xn[j];
             g[j] = gn[j];
