@@ -421,3 +421,32 @@ def test_stream_fp32_ends_where_fp64_ends(z, ora, obj, d, n, lo, hi, fmin):
     err = np.abs(g["f"] - o["f"])  # per-start error against the FP64 oracle
     same = err <= 1e-5 * np.maximum(1.0, np.abs(o["f"]))
     assert same.mean() >= 0.85, f"{(~same).sum()} of {n}; errors {np.sort(err)[-5:]}"
+
+
+def test_single_problem_solve_replays_from_a_cuda_graph(z):
+    # zeus_solve enqueues kernels and memsets only (the fused BFGS launch is
+    # a cooperative kernel node): a captured solve replays to the same bits
+    p = zeus_problem(z, workloads.workload("rastrigin10d_n16384"), n_starts=4096, bfgs_max_iters=300)
+    pc = p.to_c()
+    ws = z.new_workspace(pc)
+    x = torch.empty(p.n_starts, p.dim, dtype=torch.float64, device="cuda")
+    f = torch.empty(p.n_starts, dtype=torch.float64, device="cuda")
+    it = torch.empty(p.n_starts, dtype=torch.int32, device="cuda")
+    res = z.new_result()
+    z.zeus_solve(pc, ws, x, f, None, None, it, res)
+    torch.cuda.synchronize()
+    ref = (x.clone(), f.clone(), it.clone(), res.clone())
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        g.capture_begin()
+        z.zeus_solve(pc, ws, x, f, None, None, it, res, side)
+        g.capture_end()
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(2):
+        x.zero_(); f.zero_(); it.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(x, ref[0]) and torch.equal(f, ref[1]) and torch.equal(it, ref[2])
+        assert torch.equal(res, ref[3])
