@@ -131,19 +131,36 @@ class ClockSampler:
 
 # --------------------------------------------------------- roofline model
 
-def fp64_flops(d: int, iters: int, fevals: int) -> float:
-    """Algorithmic FP64 operations of a 10-D Rastrigin BFGS phase in forward
-    mode (FMA = 2, every other FP64 arithmetic instruction = 1), counted from
-    the operations the method needs as implemented:
-      per start-iteration  gradient d x (sin/cos of 2 pi x: 40, tangent: 4),
+def objective_flops(objective, d: int):
+    """FP64 operations of one forward-mode gradient (Alg. 5) and of one
+    value sweep at a trial point (trial coordinates included).  Rastrigin:
+    per coordinate sin/cos of 2 pi x 40 + tangent 4, and trial point 2 +
+    cos of 2 pi x 24 + term 4; the same count stands in for the other
+    built-in objectives.  A user objective's passes each evaluate the whole
+    function on duals (the plug-in's code cannot skip zero tangents):
+    Griewank d passes x d coordinates x (dual square 4, sum 2, scaled
+    argument 2, dual cosine 42, product 4) and a value sweep of d x 28;
+    Himmelblau 2 passes x 20 and 14."""
+    if objective == "griewank":
+        return 54.0 * d * d, 28.0 * d
+    if objective == "himmelblau":
+        return 40.0, 14.0
+    return 44.0 * d, 30.0 * d
+
+
+def fp64_flops(d: int, iters: int, fevals: int, objective="rastrigin") -> float:
+    """Algorithmic FP64 operations of a BFGS phase in forward mode (FMA = 2,
+    every other FP64 arithmetic instruction = 1), counted from the
+    operations the method needs as implemented:
+      per start-iteration  the gradient (objective_flops),
                            ||g|| 2d + 1, p = -H g 2d^2 + d, g'p 2d, x_new 2d,
                            s, y, y's, |s|^2, |y|^2 8d, curvature test 5,
                            H y 2d^2, y'Hy 2d, rho and its factor 4,
                            rank-two update 8 per element of the symmetric H
-                           -> 8 d^2 + 65 d + 10
-      per line-search evaluation  d x (trial point 2, cos of 2 pi x: 24,
-                           term 4) + Armijo test 3 -> 30 d + 3"""
-    return iters * (8.0 * d * d + 65.0 * d + 10.0) + fevals * (30.0 * d + 3.0)
+                           -> 8 d^2 + 21 d + 10 + gradient
+      per line-search evaluation  the value sweep + Armijo test 3"""
+    grad, val = objective_flops(objective, d)
+    return iters * (8.0 * d * d + 21.0 * d + 10.0 + grad) + fevals * (val + 3.0)
 
 
 def _peaks():
@@ -330,7 +347,7 @@ def run_zeus(a):
                             hbm={"achieved_gbs": round(achieved, 1),
                                  "frac": round(achieved / peak, 4)})
     else:
-        flops = fp64_flops(d, iters_per_step, feval_per_step)
+        flops = fp64_flops(d, iters_per_step, feval_per_step, fields["objective"])
         achieved = flops / bfgs_s / 1e12
         peak = FP64_PEAK_TFLOPS
         kname = ("bfgs_fused_kernel (lane tiles and hand-over service in one cooperative launch)"
@@ -504,7 +521,7 @@ def _tuned_summary(b) -> dict:
 
 def batch_flops(b) -> float:
     """FP64-model operations of one batched solve (per-problem counters)."""
-    return float(sum(fp64_flops(p.dim, s["total_iters"], s["total_feval"])
+    return float(sum(fp64_flops(p.dim, s["total_iters"], s["total_feval"], p.objective)
                      for p, s in zip(b.problems, b.summaries())))
 
 

@@ -56,6 +56,16 @@ typedef enum {
     ZEUS_OBJ_QUADRATIC = 100
 } zeus_objective;
 
+/* User-defined objectives (Section IV-A: f is written once for any scalar
+ * type and differentiated on dual numbers).  Objective ZEUS_OBJ_USER + k,
+ * 0 <= k < zeus_user_objective_count(), is the k-th objective of the
+ * plug-in header compiled into the library (contract and limits in
+ * include/zeus_user.cuh): forward-mode gradients only, and H held in shared
+ * memory (a plan that would stream it, or L-BFGS, returns
+ * ZEUS_EUNSUPPORTED). */
+#define ZEUS_OBJ_USER 200
+#define ZEUS_USER_MAX 4
+
 typedef enum {
     ZEUS_FP64 = 0,           /* every step in FP64 (the paper's precision) */
     ZEUS_FP32_GUARDED = 1    /* objective, gradient and H in FP32; y^T s, rho,
@@ -211,6 +221,18 @@ int zeus_objective_eval_f32(int32_t objective, int32_t dim, int64_t n,
                             const float *x, float *f_out, float *g_out,
                             int32_t grad_mode, void *stream);
 
+/* Number of user objectives compiled into the library (0..ZEUS_USER_MAX).
+ * Host only. */
+int32_t zeus_user_objective_count(void);
+
+/* Name and dimension range of user objective k (objective id
+ * ZEUS_OBJ_USER + k).  name: host buffer of name_len bytes, written
+ * NUL-terminated (truncated to fit; may be NULL); min_dim, max_dim: host
+ * int32 (may be NULL; max_dim 0 = no limit beyond the library's).  Host
+ * only.  ZEUS_EINVAL if k is out of range. */
+int zeus_user_objective_info(int32_t k, char *name, int32_t name_len,
+                             int32_t *min_dim, int32_t *max_dim);
+
 /* Best-of-swarm reduction (Alg. 7 ParallelReduction): writes
  * result->best_f / best_index for device f[n] (NaN as +inf, ties to the
  * lowest index); the other result fields are zeroed.  Needs
@@ -271,6 +293,9 @@ typedef struct {
     int32_t precision, grad_mode;
     int32_t n_classes;        /* BFGS launches over the work list */
     int32_t handover_smem;    /* dynamic shared memory of the hand-over launch */
+    int32_t n_user;           /* problems with a user objective (their kernels
+                                 are compiled apart from the built-in ones) */
+    int32_t pad;              /* 0 */
     int32_t class_first[ZEUS_BATCH_MAX_CLASSES];  /* work-list range and dynamic */
     int32_t class_count[ZEUS_BATCH_MAX_CLASSES];  /* shared memory of each BFGS */
     int32_t class_smem[ZEUS_BATCH_MAX_CLASSES];   /* launch */

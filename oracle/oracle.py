@@ -22,7 +22,9 @@ _SO = os.path.join(_BUILD_DIR, "libzeus_oracle.so")
 
 # Section V-B test functions; QUADRATIC is a test objective 0.5*sum (i+1) x_i^2.
 OBJECTIVES = {"rosenbrock": 0, "rastrigin": 1, "ackley": 2,
-              "goldstein_price": 3, "quadratic": 100}
+              "goldstein_price": 3, "quadratic": 100,
+              # objectives a user adds to the library (not built in there)
+              "griewank": 200, "himmelblau": 201}
 
 
 def build(force: bool = False) -> str:

@@ -35,7 +35,12 @@ enum {
     ZO_RASTRIGIN = 1,       /* Section V-B, Rastrigin (A = 10) */
     ZO_ACKLEY = 2,          /* Section V-B, Ackley (a=20, b=0.2, c=2*pi) */
     ZO_GOLDSTEIN_PRICE = 3, /* Section V-B, Goldstein-Price (d = 2) */
-    ZO_QUADRATIC = 100      /* test objective: 0.5 * sum (i+1) x_i^2 */
+    ZO_QUADRATIC = 100,     /* test objective: 0.5 * sum (i+1) x_i^2 */
+    /* Objectives supplied by a user of the library rather than built in
+     * (Section IV-A: any f written for a generic scalar type): the two of
+     * the library's default plug-in, written here on their own. */
+    ZO_GRIEWANK = 200,      /* 1 + sum x_i^2 / 4000 - prod cos(x_i / sqrt(i)) */
+    ZO_HIMMELBLAU = 201     /* (x^2 + y - 11)^2 + (x + y^2 - 7)^2, d = 2 */
 };
 
 typedef struct {
@@ -309,6 +314,19 @@ double zo_f(int obj, int d, const double *x)
         for (int i = 0; i < d; ++i)
             s = s + 0.5 * (double)(i + 1) * (x[i] * x[i]);
         return s;
+    case ZO_GRIEWANK: {
+        double prod = 1.0;
+        for (int i = 0; i < d; ++i) {
+            s = s + x[i] * x[i];
+            prod = prod * cos(x[i] / sqrt((double)(i + 1)));
+        }
+        return (1.0 + s / 4000.0) - prod;
+    }
+    case ZO_HIMMELBLAU: {
+        double a = (x[0] * x[0] + x[1]) - 11.0;
+        double b = (x[0] + x[1] * x[1]) - 7.0;
+        return a * a + b * b;
+    }
     default:
         return NAN;
     }
@@ -367,6 +385,19 @@ static zo_dual zo_f_dual(int obj, int d, const zo_dual *x)
         for (int i = 0; i < d; ++i)
             s = dadd(s, dscale(0.5 * (double)(i + 1), dmul(x[i], x[i])));
         return s;
+    case ZO_GRIEWANK: {
+        zo_dual prod = dconst(1.0);
+        for (int i = 0; i < d; ++i) {
+            s = dadd(s, dmul(x[i], x[i]));
+            prod = dmul(prod, dcos(ddiv(x[i], dconst(sqrt((double)(i + 1))))));
+        }
+        return dsub(dadd(dconst(1.0), ddiv(s, dconst(4000.0))), prod);
+    }
+    case ZO_HIMMELBLAU: {
+        zo_dual a = dsub(dadd(dmul(x[0], x[0]), x[1]), dconst(11.0));
+        zo_dual b = dsub(dadd(x[0], dmul(x[1], x[1])), dconst(7.0));
+        return dadd(dmul(a, a), dmul(b, b));
+    }
     default:
         return dconst(NAN);
     }

@@ -18,6 +18,7 @@ import torch
 
 from . import _capi
 from ._capi import (GRAD_MODES, OBJECTIVES, PRECISIONS, RUN_STATUS, ZeusError, check, lib,
+                    objective_code, user_objectives,
                     library_path, strerror, zeus_problem, zeus_result)
 
 __all__ = [
@@ -26,7 +27,7 @@ __all__ = [
     "zeus_workspace_size", "zeus_plan_info", "zeus_validate", "zeus_default_problem", "zeus_strerror",
     "zeus_abi_version", "zeus_math_eval", "Context", "solve", "solve_from", "pso", "objective", "ObjectiveFn",
     "decode_result", "library_path", "lib", "zeus_batch_plan_make", "zeus_batch_prepare",
-    "zeus_batch_solve", "Batch",
+    "zeus_batch_solve", "Batch", "user_objectives",
 ]
 
 
@@ -62,7 +63,7 @@ class Problem:
         def code(v, table):
             return table[v] if isinstance(v, str) else int(v)
         return zeus_problem(
-            code(self.objective, OBJECTIVES), self.dim, self.lower, self.upper, self.n_starts,
+            objective_code(self.objective), self.dim, self.lower, self.upper, self.n_starts,
             self.pso_iters, self.bfgs_max_iters, self.ls_max_iters, self.required_converged,
             self.grad_tol, self.w, self.c1, self.c2, self.armijo_c, self.backtrack,
             self.target_f, self.seed & (2**64 - 1), code(self.precision, PRECISIONS),
@@ -204,7 +205,7 @@ def zeus_pso(problem, workspace, x_out, v_out, px_out, pf_out, gx_out, result=No
 
 
 def _obj_code(o) -> int:
-    return OBJECTIVES[o] if isinstance(o, str) else int(o)
+    return objective_code(o)
 
 
 def _grad_code(g) -> int:

@@ -21,6 +21,7 @@ ZEUS_EUNSUPPORTED = -5
 ZEUS_EWORKSPACE = -6
 
 OBJECTIVES = {"rosenbrock": 0, "rastrigin": 1, "ackley": 2, "goldstein_price": 3, "quadratic": 100}
+OBJ_USER = 200  # objective id of user objective k: OBJ_USER + k (include/zeus_user.cuh)
 PRECISIONS = {"fp64": 0, "fp32_guarded": 1}
 GRAD_MODES = {"forward": 0, "adjoint": 1}
 RUN_STATUS = {0: "max_iter", 1: "converged", 2: "stopped", 3: "nonfinite"}
@@ -67,7 +68,7 @@ class zeus_batch_plan(C.Structure):
     _fields_ = [("n_problems", C.c_int32), ("pso_blocks", C.c_int32), ("items", C.c_int32),
                 ("pso_iters_max", C.c_int32), ("q_cap", C.c_int32), ("d_max_handover", C.c_int32),
                 ("precision", C.c_int32), ("grad_mode", C.c_int32), ("n_classes", C.c_int32),
-                ("handover_smem", C.c_int32),
+                ("handover_smem", C.c_int32), ("n_user", C.c_int32), ("pad", C.c_int32),
                 ("class_first", C.c_int32 * BATCH_MAX_CLASSES),
                 ("class_count", C.c_int32 * BATCH_MAX_CLASSES),
                 ("class_smem", C.c_int32 * BATCH_MAX_CLASSES),
@@ -108,6 +109,9 @@ SIGNATURES = {
     "zeus_uniform": (C.c_int, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int32, _VP,
                                _VP]),
     "zeus_math_eval": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, _VP, _VP]),
+    "zeus_user_objective_count": (C.c_int32, []),
+    "zeus_user_objective_info": (C.c_int, [C.c_int32, C.c_char_p, C.c_int32,
+                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "zeus_batch_plan_make": (C.c_int, [C.POINTER(zeus_problem), C.c_int32,
                                        C.POINTER(zeus_batch_plan)]),
     "zeus_batch_prepare": (C.c_int, [C.POINTER(zeus_problem), C.c_int32,
@@ -155,3 +159,29 @@ def strerror(code: int) -> str:
 def check(code: int, where: str) -> None:
     if code != ZEUS_OK:
         raise ZeusError(code, where)
+
+
+def user_objectives() -> dict:
+    """The user objectives compiled into libzeus.so (its plug-in header):
+    name -> (objective id, min_dim, max_dim); max_dim 0 = no limit."""
+    L = lib()
+    out = {}
+    buf = C.create_string_buffer(64)
+    lo, hi = C.c_int32(), C.c_int32()
+    for k in range(L.zeus_user_objective_count()):
+        check(L.zeus_user_objective_info(k, buf, 64, C.byref(lo), C.byref(hi)),
+              "zeus_user_objective_info")
+        out[buf.value.decode()] = (OBJ_USER + k, lo.value, hi.value)
+    return out
+
+
+def objective_code(o) -> int:
+    """Objective id of a built-in or user objective name (ids pass through)."""
+    if not isinstance(o, str):
+        return int(o)
+    if o in OBJECTIVES:
+        return OBJECTIVES[o]
+    user = user_objectives()
+    if o in user:
+        return user[o][0]
+    raise KeyError(f"unknown objective {o!r}: built in {sorted(OBJECTIVES)}, user {sorted(user)}")

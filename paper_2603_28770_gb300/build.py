@@ -25,7 +25,9 @@ _PAIRS = [("-DZEUS_KGRAD=%d" % g, "-DZEUS_KF32=%d" % f) for g in (0, 1) for f in
 SOURCES = ([(s, ()) for s in ("zeus_capi.cu", "zeus_pso.cu", "zeus_bfgs.cu", "zeus_objective.cu",
                               "zeus_noalloc.cu", "zeus_stream.cu", "zeus_batch.cu")]
            + [("zeus_bfgs_kernels.cu", d) for d in _PAIRS]
-           + [("zeus_batch_kernels.cu", d) for d in _PAIRS])
+           + [("zeus_batch_kernels.cu", d) for d in _PAIRS]
+           + [("zeus_batch_kernels.cu", ("-DZEUS_KGRAD=0", "-DZEUS_KF32=%d" % f, "-DZEUS_KUSER=1"))
+              for f in (0, 1)])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -43,11 +45,30 @@ def _flags(extra=()):
                    "-I", INCLUDE, "-I", CSRC, *extra]
 
 
-def _deps():
+STAMP = os.path.join(BUILD, "user_plugin.txt")
+
+
+def user_plugin(path: str | None = None) -> str:
+    """The plug-in header of user objectives compiled into the library
+    (contract in include/zeus_user.cuh): ``path``, else the environment's
+    ZEUS_USER_OBJECTIVES, else the package's default plug-in."""
+    p = path or os.environ.get("ZEUS_USER_OBJECTIVES")
+    return os.path.abspath(p) if p else os.path.join(CSRC, "zeus_user_objectives.cuh")
+
+
+def _deps(plugin: str):
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(INCLUDE, "zeus.h"))
-    files.append(os.path.abspath(__file__))
+    files += [os.path.join(INCLUDE, f) for f in ("zeus.h", "zeus_user.cuh")]
+    files += [os.path.abspath(__file__), plugin]
     return max(os.path.getmtime(f) for f in files)
+
+
+def _stamp() -> str:
+    try:
+        with open(STAMP) as fh:
+            return fh.read().strip()
+    except OSError:
+        return ""
 
 
 def _obj_name(src: str, defines) -> str:
@@ -62,11 +83,17 @@ def _compile(src: str, obj: str, extra=()) -> None:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile and link libzeus.so if any source changed; return its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
+def build(force: bool = False, verbose: bool = False, extra=(), user_objectives: str | None = None) -> str:
+    """Compile and link libzeus.so if any source changed (or another plug-in
+    of user objectives is asked for); return its path."""
+    plugin = user_plugin(user_objectives)
+    if not os.path.exists(plugin):
+        raise FileNotFoundError(f"user-objective plug-in {plugin} not found")
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps(plugin)
+            and _stamp() == plugin):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    extra = (*extra, f'-DZEUS_USER_PLUGIN="{plugin}"')
     objs = [_obj_name(s, d) for s, d in SOURCES]
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         futs = [ex.submit(_compile, s, o, (*d, *extra)) for (s, d), o in zip(SOURCES, objs)]
@@ -78,6 +105,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(plugin + "\n")
     if verbose:
         print(f"built {LIB}", file=sys.stderr)
     return LIB

@@ -25,7 +25,7 @@
 
 namespace zeus {
 
-cudaError_t launch_batch_bfgs(const BatchDev& bd, int precision, int grad_mode, int cls,
+cudaError_t launch_batch_bfgs(const BatchDev& bd, int precision, int grad_mode, bool user, int cls,
                               int first, int count, size_t smem, double* x_out, double* f_out,
                               double* gnorm_out, int32_t* status_out, int32_t* iters_out,
                               cudaStream_t st) {
@@ -35,10 +35,13 @@ cudaError_t launch_batch_bfgs(const BatchDev& bd, int precision, int grad_mode, 
                       st);
     };
     if (grad_mode == ZEUS_GRAD_ADJOINT)
-        return f32 ? go(batch_launch_gt<ZEUS_GRAD_ADJOINT, float>)
-                   : go(batch_launch_gt<ZEUS_GRAD_ADJOINT, double>);
-    return f32 ? go(batch_launch_gt<ZEUS_GRAD_FORWARD, float>)
-               : go(batch_launch_gt<ZEUS_GRAD_FORWARD, double>);
+        return f32 ? go(batch_launch_gt<ZEUS_GRAD_ADJOINT, float, false>)
+                   : go(batch_launch_gt<ZEUS_GRAD_ADJOINT, double, false>);
+    if (user)
+        return f32 ? go(batch_launch_gt<ZEUS_GRAD_FORWARD, float, true>)
+                   : go(batch_launch_gt<ZEUS_GRAD_FORWARD, double, true>);
+    return f32 ? go(batch_launch_gt<ZEUS_GRAD_FORWARD, float, false>)
+               : go(batch_launch_gt<ZEUS_GRAD_FORWARD, double, false>);
 }
 
 }  // namespace zeus
@@ -71,7 +74,7 @@ struct BatchHost {
     std::vector<int> pblk0, pblk, plane, pso_table, stride, budget;
     std::vector<int4> items;
     Sizes sz;
-    int pso_iters_max = 0, handover_smem = 0, n_classes = 0;
+    int pso_iters_max = 0, handover_smem = 0, n_classes = 0, n_user = 0;
     int class_first[ZEUS_BATCH_MAX_CLASSES], class_count[ZEUS_BATCH_MAX_CLASSES],
         class_smem[ZEUS_BATCH_MAX_CLASSES];
 };
@@ -108,6 +111,7 @@ int build_host(const zeus_problem* probs, int n, BatchHost& B) {
         const int r = plan_bfgs(p, &L);
         if (r != ZEUS_OK) return r;
         if (L.stream) return ZEUS_EUNSUPPORTED;  // H on chip (and no L-BFGS) in a batch
+        if (p.objective >= ZEUS_OBJ_USER) ++B.n_user;
         const int d = p.dim;
         const int G = lanes_for_dim(d);
         const int nb = pso_blocks(p, G);
@@ -286,6 +290,8 @@ void fill_plan(const BatchHost& B, const BatchLayout& l, zeus_batch_plan* plan) 
     plan->grad_mode = B.probs[0].grad_mode;
     plan->n_classes = B.n_classes;
     plan->handover_smem = B.handover_smem;
+    plan->n_user = B.n_user;
+    plan->pad = 0;
     for (int c = 0; c < B.n_classes; ++c) {
         plan->class_first[c] = B.class_first[c];
         plan->class_count[c] = B.class_count[c];
@@ -318,6 +324,8 @@ bool plan_sane(const zeus_batch_plan& p) {
     if (next != p.items) return false;
     if (p.precision != ZEUS_FP64 && p.precision != ZEUS_FP32_GUARDED) return false;
     if (p.grad_mode != ZEUS_GRAD_FORWARD && p.grad_mode != ZEUS_GRAD_ADJOINT) return false;
+    if (p.n_user < 0 || p.n_user > p.n_problems || p.pad != 0) return false;
+    if (p.n_user > 0 && p.grad_mode != ZEUS_GRAD_FORWARD) return false;
     const BatchLayout l = batch_layout(plan_sizes(p));
     return l.total == p.workspace_bytes && l.pctrl == p.table_bytes;
 }
@@ -387,11 +395,12 @@ int zeus_batch_solve(const zeus_batch_plan* plan, void* workspace, size_t worksp
     for (int t = -1; t < plan->pso_iters_max && e == cudaSuccess; ++t)
         e = launch_batch_pso(bd, t, x_out, st);
     for (int c = 0; c < plan->n_classes && e == cudaSuccess; ++c)
-        e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, c, plan->class_first[c],
+        e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, c,
+                              plan->class_first[c],
                               plan->class_count[c], (size_t)plan->class_smem[c], x_out, f_out,
                               gnorm_out, status_out, iters_out, st);
     if (e == cudaSuccess && plan->q_cap > 0)
-        e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, -1, 0, 0,
+        e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, -1, 0, 0,
                               (size_t)plan->handover_smem, x_out, f_out, gnorm_out, status_out,
                               iters_out, st);
     if (e == cudaSuccess) e = launch_batch_argmin(bd, f_out, results, st);

@@ -7,14 +7,35 @@
 #if !defined(ZEUS_KGRAD) || !defined(ZEUS_KF32)
 #error "compile with -DZEUS_KGRAD=0|1 -DZEUS_KF32=0|1"
 #endif
+// ZEUS_KUSER=1: the variant whose objective switch also holds the user
+// objectives (forward mode only).  It is compiled apart so that the kernel
+// of the built-in objectives keeps its own registers and compile time.
+#ifndef ZEUS_KUSER
+#define ZEUS_KUSER 0
+#endif
+#if ZEUS_KUSER && ZEUS_KGRAD
+#error "user objectives have forward-mode gradients only"
+#endif
 
 namespace zeus {
 
-template <int GRAD, class T>
+template <int GRAD, class T, bool U>
 __device__ __forceinline__ void batch_narrow(const zeus_problem& p, int P, long long s, T* slot,
                                              const BatchDev& bd, const RunIO& io) {
     const int b = bd.budget[P];
     Ctrl* qc = bd.gctrl;
+    if constexpr (U && GRAD == ZEUS_GRAD_FORWARD) {  // user objectives: forward mode only
+        switch (p.objective) {
+#define ZEUS_UCASE(O)                                                \
+    case O:                                                          \
+        narrow_run<O, GRAD, T>(p, s, slot, b, io, qc, bd.q, P);      \
+        return;
+            ZEUS_USER_EACH(ZEUS_UCASE)
+#undef ZEUS_UCASE
+            default:
+                break;
+        }
+    }
     switch (p.objective) {
         case ZEUS_OBJ_ROSENBROCK:
             narrow_run<ZEUS_OBJ_ROSENBROCK, GRAD, T>(p, s, slot, b, io, qc, bd.q, P);
@@ -34,10 +55,22 @@ __device__ __forceinline__ void batch_narrow(const zeus_problem& p, int P, long 
     }
 }
 
-template <int GRAD, class T>
+template <int GRAD, class T, bool U>
 __device__ __forceinline__ void batch_wide(const zeus_problem& p, int W, long long s, int k,
                                            int fe, const T* Hq, const T* xq, const RunIO& io,
                                            WideShared& sh, unsigned char* smem_raw, int tid) {
+    if constexpr (U && GRAD == ZEUS_GRAD_FORWARD) {  // user objectives: forward mode only
+        switch (p.objective) {
+#define ZEUS_UCASE(O)                                                            \
+    case O:                                                                      \
+        wide_run<O, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);     \
+        return;
+            ZEUS_USER_EACH(ZEUS_UCASE)
+#undef ZEUS_UCASE
+            default:
+                break;
+        }
+    }
     switch (p.objective) {
         case ZEUS_OBJ_ROSENBROCK:
             wide_run<ZEUS_OBJ_ROSENBROCK, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);
@@ -76,7 +109,7 @@ __device__ __forceinline__ RunIO batch_io(const BatchDev& bd, const zeus_problem
 // over the hand-over queue (cls < 0).  Item (P, s, c, 0): a tile of c
 // starts s.. of problem P, one lane each; item (P, s, W, 1): start s on the
 // whole block with W line-search trials at once.
-template <int GRAD, class T>
+template <int GRAD, class T, bool U>
 __global__ void __launch_bounds__(kWideThreads)
     batch_bfgs_kernel(const BatchDev bd, const int cls, const int first, const int count,
                       double* x_out, double* __restrict__ f_out, double* __restrict__ gnorm_out,
@@ -102,10 +135,10 @@ __global__ void __launch_bounds__(kWideThreads)
             if (w.w == 0) {
                 if ((int)threadIdx.x < w.z) {
                     T* slot = reinterpret_cast<T*>(smem_raw) + (size_t)threadIdx.x * bd.stride[P];
-                    batch_narrow<GRAD, T>(p, P, (long long)w.y + threadIdx.x, slot, bd, io);
+                    batch_narrow<GRAD, T, U>(p, P, (long long)w.y + threadIdx.x, slot, bd, io);
                 }
             } else {
-                batch_wide<GRAD, T>(p, w.z, w.y, 0, 0, nullptr, nullptr, io, sh, smem_raw, tid);
+                batch_wide<GRAD, T, U>(p, w.z, w.y, 0, 0, nullptr, nullptr, io, sh, smem_raw, tid);
             }
         } else {
             const int P = bd.q.prob[item];
@@ -114,17 +147,17 @@ __global__ void __launch_bounds__(kWideThreads)
             const long long s = bd.q.start[item];
             const T* Hq = reinterpret_cast<const T*>(bd.q.H) + (size_t)item * bd.q.hstride;
             const T* xq = reinterpret_cast<const T*>(io.x_out + s * p.dim);
-            batch_wide<GRAD, T>(p, wide_trials(p.dim, p.ls_max_iters), s, bd.q.k[item],
+            batch_wide<GRAD, T, U>(p, wide_trials(p.dim, p.ls_max_iters), s, bd.q.k[item],
                                 bd.q.feval[item], Hq, xq, io, sh, smem_raw, tid);
         }
     }
 }
 
-template <int GRAD, class T>
+template <int GRAD, class T, bool U>
 cudaError_t batch_launch_gt(const BatchDev& bd, int cls, int first, int count, size_t smem,
                             double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
                             int32_t* iters_out, cudaStream_t st) {
-    auto k = batch_bfgs_kernel<GRAD, T>;
+    auto k = batch_bfgs_kernel<GRAD, T, U>;
     // The launches of one solve use different shared memory sizes, and a
     // captured graph launches its kernel nodes later: allow the largest
     // size the device offers once, rather than the size of the launch at
@@ -153,13 +186,13 @@ cudaError_t batch_launch_gt(const BatchDev& bd, int cls, int first, int count, s
 }
 
 #if ZEUS_KF32
-template cudaError_t batch_launch_gt<ZEUS_KGRAD, float>(const BatchDev&, int, int, int, size_t,
-                                                        double*, double*, double*, int32_t*,
-                                                        int32_t*, cudaStream_t);
+template cudaError_t batch_launch_gt<ZEUS_KGRAD, float, ZEUS_KUSER != 0>(
+    const BatchDev&, int, int, int, size_t, double*, double*, double*, int32_t*, int32_t*,
+    cudaStream_t);
 #else
-template cudaError_t batch_launch_gt<ZEUS_KGRAD, double>(const BatchDev&, int, int, int, size_t,
-                                                         double*, double*, double*, int32_t*,
-                                                         int32_t*, cudaStream_t);
+template cudaError_t batch_launch_gt<ZEUS_KGRAD, double, ZEUS_KUSER != 0>(
+    const BatchDev&, int, int, int, size_t, double*, double*, double*, int32_t*, int32_t*,
+    cudaStream_t);
 #endif
 
 }  // namespace zeus

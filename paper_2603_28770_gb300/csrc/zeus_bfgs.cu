@@ -47,9 +47,11 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
     const size_t cap = 226 * 1024;  // 227 KB per block, less the kernels' static shared memory
     const size_t ts = p.precision == ZEUS_FP32_GUARDED ? sizeof(float) : sizeof(double);
     const int req = p.threads_per_start;
+    // user objectives run in the forms that hold H in shared memory
+    const bool user = p.objective >= ZEUS_OBJ_USER;
     L->lbfgs = p.lbfgs_m > 0;
     if (L->lbfgs) {  // one 256-thread block per start, the pairs in shared memory
-        if (p.objective == ZEUS_OBJ_GOLDSTEIN_PRICE || (req != 0 && req != 256))
+        if (p.objective == ZEUS_OBJ_GOLDSTEIN_PRICE || user || (req != 0 && req != 256))
             return ZEUS_EUNSUPPORTED;
         L->narrow = false;
         L->stride = 0;
@@ -84,7 +86,7 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
     L->stream_blocks = stream_blocks(p);
     L->stream_smem = stream_smem(d, ts);
     L->hslot_bytes = L->stream ? (size_t)L->stream_blocks * d * d * ts : 0;
-    if (L->stream && L->stream_smem > cap) return ZEUS_EUNSUPPORTED;
+    if (L->stream && (user || L->stream_smem > cap)) return ZEUS_EUNSUPPORTED;
     L->wide_blocks = 152 * 4;
     // hand-over budget (iterations + line-search evaluations) of the narrow
     // kernel; 0 = every start runs to its end in the narrow kernel.  Only

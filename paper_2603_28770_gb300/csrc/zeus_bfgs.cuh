@@ -72,19 +72,26 @@ __device__ __forceinline__ double val_finish(const Part<double>& acc, int d) {
     return value_finish<OBJ, double>(acc, d);
 }
 
+// a user objective is a single term (f at the whole point)
 template <int OBJ>
 __device__ __forceinline__ int val_nterms(int d) {
     if (OBJ == ZEUS_OBJ_ROSENBROCK) return d - 1;
-    if (OBJ == ZEUS_OBJ_GOLDSTEIN_PRICE) return 1;
+    if (OBJ == ZEUS_OBJ_GOLDSTEIN_PRICE || OBJ >= ZEUS_OBJ_USER) return 1;
     return d;
 }
 
 // term j of the sweep in the accessor's type V, returned as FP64 (the sums
 // of the FP32 form are FP64 sums of FP32 terms)
 template <int OBJ, class X>
-__device__ __forceinline__ void val_term(const X& xa, int j, double& t0, double& t1) {
+__device__ __forceinline__ void val_term(const X& xa, int j, int d, double& t0, double& t1) {
     using V = decltype(xa(0));
     t1 = 0.0;
+    if constexpr (OBJ >= ZEUS_OBJ_USER) {
+        (void)j;
+        t0 = (double)UserObjective<OBJ>::template eval<V>(xa, d);
+        return;
+    }
+    (void)d;
     if (OBJ == ZEUS_OBJ_ROSENBROCK) {
         const V xj = xa(j);
         const V a = V(1) - xj;
@@ -126,7 +133,7 @@ __device__ __forceinline__ void val_term(const X& xa, int j, double& t0, double&
 
 template <int OBJ>
 __device__ __forceinline__ void val_add(Part<double>& acc, double t0, double t1) {
-    if (OBJ == ZEUS_OBJ_GOLDSTEIN_PRICE) {
+    if (OBJ == ZEUS_OBJ_GOLDSTEIN_PRICE || OBJ >= ZEUS_OBJ_USER) {
         acc.s0 = t0;
     } else {
         acc.s0 = acc.s0 + t0;
@@ -142,7 +149,7 @@ __device__ __forceinline__ double seq_value(const X& xa, int d) {
     const int nt = val_nterms<OBJ>(d);
     for (int j = 0; j < nt; ++j) {
         double t0, t1;
-        val_term<OBJ>(xa, j, t0, t1);
+        val_term<OBJ>(xa, j, d, t0, t1);
         val_add<OBJ>(acc, t0, t1);
     }
     return val_finish<OBJ, V>(acc, d);
@@ -557,7 +564,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             for (int e = tid; e < nw * nt; e += NT) {
                 const int mm = e / nt, j = e - mm * nt;
                 double t0, t1;
-                val_term<OBJ>(AtTrial<T>{x, pv, T(al[m0 + mm])}, j, t0, t1);
+                val_term<OBJ>(AtTrial<T>{x, pv, T(al[m0 + mm])}, j, d, t0, t1);
                 tb0[mm * d + j] = t0;
                 tb1[mm * d + j] = t1;
             }

@@ -262,6 +262,18 @@ template <int GRAD, class T>
 cudaError_t bfgs_launch_gt(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
                            double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
                            int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st) {
+    if constexpr (GRAD == ZEUS_GRAD_FORWARD) {  // user objectives: forward mode only
+        switch (p.objective) {
+#define ZEUS_UCASE(O)                                                                       \
+    case O:                                                                                 \
+        return bfgs_go<O, GRAD, T>(p, L, x0, x_out, f_out, gnorm_out, status_out, iters_out, \
+                                   ctrl, q, st);
+            ZEUS_USER_EACH(ZEUS_UCASE)
+#undef ZEUS_UCASE
+            default:
+                break;
+        }
+    }
     switch (p.objective) {
         case ZEUS_OBJ_ROSENBROCK:
             return bfgs_go<ZEUS_OBJ_ROSENBROCK, GRAD, T>(p, L, x0, x_out, f_out, gnorm_out,

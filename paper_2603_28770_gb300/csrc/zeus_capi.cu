@@ -31,8 +31,14 @@ int validate(const zeus_problem* p) {
         case ZEUS_OBJ_ACKLEY:
         case ZEUS_OBJ_QUADRATIC:
             break;
-        default:
-            return ZEUS_EINVAL;
+        default: {  // a user objective of the plug-in, within its dimension range
+            const char* name;
+            int lo, hi;
+            if (p->objective < ZEUS_OBJ_USER ||
+                !user_objective_meta(p->objective - ZEUS_OBJ_USER, &name, &lo, &hi))
+                return ZEUS_EINVAL;
+            if (p->dim < lo || (hi > 0 && p->dim > hi)) return ZEUS_EINVAL;
+        }
     }
     if (p->dim < 1 || p->dim > 4096) return ZEUS_EINVAL;
     if (!isfinite(p->lower) || !isfinite(p->upper) || !(p->lower < p->upper)) return ZEUS_EINVAL;
@@ -51,6 +57,9 @@ int validate(const zeus_problem* p) {
     if (!valid_lanes(p->threads_per_start)) return ZEUS_EINVAL;
     if (p->lbfgs_m < 0 || p->lbfgs_m > 64 || p->pad != 0) return ZEUS_EINVAL;
     if (p->precision != ZEUS_FP64 && p->precision != ZEUS_FP32_GUARDED) return ZEUS_EINVAL;
+    // a user objective has no hand-written reverse sweep
+    if (p->objective >= ZEUS_OBJ_USER && p->grad_mode == ZEUS_GRAD_ADJOINT)
+        return ZEUS_EUNSUPPORTED;
     return ZEUS_OK;
 }
 
@@ -348,6 +357,22 @@ int zeus_uniform(uint64_t seed, uint64_t problem, uint64_t phase, int64_t n, int
                  double* out, void* stream) {
     if (n < 0 || dim < 1 || (n > 0 && !out)) return ZEUS_EINVAL;
     return cuda_status(launch_uniform(seed, problem, phase, n, dim, out, as_stream(stream)));
+}
+
+int32_t zeus_user_objective_count(void) { return user_objective_count(); }
+
+int zeus_user_objective_info(int32_t k, char* name, int32_t name_len, int32_t* min_dim,
+                             int32_t* max_dim) {
+    const char* nm;
+    int lo, hi;
+    if (!user_objective_meta(k, &nm, &lo, &hi)) return ZEUS_EINVAL;
+    if (name && name_len > 0) {
+        strncpy(name, nm, (size_t)name_len - 1);
+        name[name_len - 1] = '\0';
+    }
+    if (min_dim) *min_dim = lo;
+    if (max_dim) *max_dim = hi;
+    return ZEUS_OK;
 }
 
 int zeus_math_eval(int32_t fn, int64_t n, const double* x, double* y0, double* y1, void* stream) {

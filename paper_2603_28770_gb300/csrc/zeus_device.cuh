@@ -9,6 +9,40 @@
 
 #include "zeus.h"
 
+// User objectives: the plug-in header named at build time, else the
+// default one of the package (contract in zeus_user.cuh).
+#ifndef ZEUS_USER_PLUGIN
+#define ZEUS_USER_PLUGIN "zeus_user_objectives.cuh"
+#endif
+#include ZEUS_USER_PLUGIN
+#if !defined(ZEUS_USER_COUNT) || ZEUS_USER_COUNT < 0 || ZEUS_USER_COUNT > ZEUS_USER_MAX
+#error "the user-objective plug-in must define ZEUS_USER_COUNT in 0..ZEUS_USER_MAX"
+#endif
+
+// M(id) once for each user objective id of the plug-in (case labels and
+// template arguments at the objective switches)
+#define ZEUS_USER_EACH(M) ZEUS_USER_E0(M) ZEUS_USER_E1(M) ZEUS_USER_E2(M) ZEUS_USER_E3(M)
+#if ZEUS_USER_COUNT > 0
+#define ZEUS_USER_E0(M) M(ZEUS_OBJ_USER + 0)
+#else
+#define ZEUS_USER_E0(M)
+#endif
+#if ZEUS_USER_COUNT > 1
+#define ZEUS_USER_E1(M) M(ZEUS_OBJ_USER + 1)
+#else
+#define ZEUS_USER_E1(M)
+#endif
+#if ZEUS_USER_COUNT > 2
+#define ZEUS_USER_E2(M) M(ZEUS_OBJ_USER + 2)
+#else
+#define ZEUS_USER_E2(M)
+#endif
+#if ZEUS_USER_COUNT > 3
+#define ZEUS_USER_E3(M) M(ZEUS_OBJ_USER + 3)
+#else
+#define ZEUS_USER_E3(M)
+#endif
+
 namespace zeus {
 
 // ---------------------------------------------------------------------------
@@ -254,8 +288,28 @@ struct Part {
     A s0, s1;
 };
 
+// A user objective is one term: f at the whole point, evaluated by one
+// thread in the plug-in's own order.  Coordinates reach it through an
+// accessor, x(j); duals carry the tangent seeded on coordinate i.
+template <int OBJ>
+using UserObjective = zeus_user::objective<OBJ - ZEUS_OBJ_USER>;
+
+template <class T>
+struct UserAt {
+    const T* x;
+    __device__ __forceinline__ T operator()(int j) const { return x[j]; }
+};
+template <class T>
+struct UserSeed {
+    const T* x;
+    int i;
+    __device__ __forceinline__ zeus_user::dual<T> operator()(int j) const {
+        return zeus_user::dual<T>(x[j], j == i ? T(1) : T(0));
+    }
+};
+
 template <int OBJ, class T, class A>
-__device__ __forceinline__ Part<A> value_partial(const T* x, int d, int lane, int G) {
+__device__ __forceinline__ Part<A> builtin_value_partial(const T* x, int d, int lane, int G) {
     Part<A> p;
     p.s0 = A(0);
     p.s1 = A(0);
@@ -300,6 +354,19 @@ __device__ __forceinline__ Part<A> value_partial(const T* x, int d, int lane, in
     return p;
 }
 
+template <int OBJ, class T, class A>
+__device__ __forceinline__ Part<A> value_partial(const T* x, int d, int lane, int G) {
+    if constexpr (OBJ >= ZEUS_OBJ_USER) {
+        Part<A> p;
+        p.s0 = A(0);
+        p.s1 = A(0);
+        if (lane == 0) p.s0 = A(UserObjective<OBJ>::template eval<T>(UserAt<T>{x}, d));
+        return p;
+    } else {
+        return builtin_value_partial<OBJ, T, A>(x, d, lane, G);
+    }
+}
+
 template <int OBJ, class A>
 __device__ __forceinline__ A value_finish(Part<A> p, int d) {
     if (OBJ == ZEUS_OBJ_ACKLEY) {
@@ -312,7 +379,7 @@ __device__ __forceinline__ A value_finish(Part<A> p, int d) {
 
 // Alg. 5, one pass: f on duals with seed e_i.  Returns (value, df/dx_i).
 template <int OBJ, class T>
-__device__ __forceinline__ Dual<T> forward_pass(const T* x, int d, int i) {
+__device__ __forceinline__ Dual<T> builtin_forward_pass(const T* x, int d, int i) {
     if (OBJ == ZEUS_OBJ_ROSENBROCK) {
         T val = T(0), tan = T(0);
         for (int j = 0; j < d - 1; ++j) {
@@ -401,6 +468,17 @@ __device__ __forceinline__ Dual<T> forward_pass(const T* x, int d, int i) {
             if (j == i) tan += c * (xj + xj);
         }
         return dmk(val, tan);
+    }
+}
+
+template <int OBJ, class T>
+__device__ __forceinline__ Dual<T> forward_pass(const T* x, int d, int i) {
+    if constexpr (OBJ >= ZEUS_OBJ_USER) {
+        const zeus_user::dual<T> r =
+            UserObjective<OBJ>::template eval<zeus_user::dual<T>>(UserSeed<T>{x, i}, d);
+        return dmk(r.v, r.t);
+    } else {
+        return builtin_forward_pass<OBJ, T>(x, d, i);
     }
 }
 

@@ -157,7 +157,8 @@ cudaError_t launch_batch_argmin(const BatchDev& bd, const double* f_out, zeus_re
                                 cudaStream_t st);
 // one persistent launch over work items [first, first + count) with class
 // counter `cls`; cls < 0: the hand-over queue
-cudaError_t launch_batch_bfgs(const BatchDev& bd, int precision, int grad_mode, int cls,
+// user: the batch holds user objectives (the kernel variant that has them)
+cudaError_t launch_batch_bfgs(const BatchDev& bd, int precision, int grad_mode, bool user, int cls,
                               int first, int count, size_t smem, double* x_out, double* f_out,
                               double* gnorm_out, int32_t* status_out, int32_t* iters_out,
                               cudaStream_t st);
@@ -168,7 +169,7 @@ template <int GRAD, class T>
 cudaError_t bfgs_launch_gt(const zeus_problem& p, const BfgsLaunch& L, const double* x0,
                            double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
                            int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st);
-template <int GRAD, class T>
+template <int GRAD, class T, bool U>
 cudaError_t batch_launch_gt(const BatchDev& bd, int cls, int first, int count, size_t smem,
                             double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
                             int32_t* iters_out, cudaStream_t st);
@@ -181,6 +182,10 @@ cudaError_t launch_objective(int obj, int d, long long n, const double* x, doubl
                              int grad_mode, cudaStream_t st);
 cudaError_t launch_objective_f32(int obj, int d, long long n, const float* x, float* f, float* g,
                                  int grad_mode, cudaStream_t st);
+
+// plug-in metadata of user objective k (zeus_user.cuh): 0 if k is not one
+int user_objective_meta(int k, const char** name, int* min_dim, int* max_dim);
+int user_objective_count();
 
 cudaError_t launch_math(int fn, long long n, const double* x, double* y0, double* y1,
                         cudaStream_t st);

@@ -63,7 +63,14 @@ static cudaError_t objective_go(int obj, int d, long long n, const T* x, T* f, T
             objective_kernel<O, ZEUS_GRAD_FORWARD, T><<<blocks, kObjThreads, 0, st>>>(d, n, G, x, \
                                                                                    f, g);   \
         break;
+    // user objectives: forward mode only (the entry points reject the adjoint)
+#define ZEUS_UCASE(O)                                                                          \
+    case O:                                                                                    \
+        objective_kernel<O, ZEUS_GRAD_FORWARD, T><<<blocks, kObjThreads, 0, st>>>(d, n, G, x, f, \
+                                                                                 g);           \
+        break;
     switch (obj) {
+        ZEUS_USER_EACH(ZEUS_UCASE)
         ZEUS_OBJ_CASE(ZEUS_OBJ_ROSENBROCK)
         ZEUS_OBJ_CASE(ZEUS_OBJ_RASTRIGIN)
         ZEUS_OBJ_CASE(ZEUS_OBJ_ACKLEY)
@@ -72,6 +79,7 @@ static cudaError_t objective_go(int obj, int d, long long n, const T* x, T* f, T
             ZEUS_OBJ_CASE(ZEUS_OBJ_QUADRATIC)
     }
 #undef ZEUS_OBJ_CASE
+#undef ZEUS_UCASE
     return cudaGetLastError();
 }
 
@@ -102,6 +110,28 @@ cudaError_t launch_math(int fn, long long n, const double* x, double* y0, double
     math_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(fn, n, x, y0, y1);
     return cudaGetLastError();
 }
+
+template <int K>
+static void user_meta_of(const char** name, int* min_dim, int* max_dim) {
+    *name = zeus_user::objective<K>::name;
+    *min_dim = zeus_user::objective<K>::min_dim;
+    *max_dim = zeus_user::objective<K>::max_dim;
+}
+
+int user_objective_meta(int k, const char** name, int* min_dim, int* max_dim) {
+    switch (ZEUS_OBJ_USER + k) {
+#define ZEUS_UCASE(O)                                                \
+    case O:                                                          \
+        user_meta_of<O - ZEUS_OBJ_USER>(name, min_dim, max_dim);     \
+        return 1;
+        ZEUS_USER_EACH(ZEUS_UCASE)
+#undef ZEUS_UCASE
+        default:
+            return 0;
+    }
+}
+
+int user_objective_count() { return ZEUS_USER_COUNT; }
 
 cudaError_t launch_objective(int obj, int d, long long n, const double* x, double* f, double* g,
                              int grad_mode, cudaStream_t st) {

@@ -147,6 +147,12 @@ __global__ void __launch_bounds__(kPsoThreads)
     Ctrl* ctrl = bd.pctrl + P;
     const int G = bd.plane[P], nb = bd.pblk[P];
     switch (p.objective) {
+#define ZEUS_UCASE(O)                                                                 \
+    case O:                                                                           \
+        pso_block<O>(p, t, G, lb, nb, x, v, px, pf, gx, ctrl, parts, nullptr);        \
+        break;
+        ZEUS_USER_EACH(ZEUS_UCASE)
+#undef ZEUS_UCASE
         case ZEUS_OBJ_ROSENBROCK:
             pso_block<ZEUS_OBJ_ROSENBROCK>(p, t, G, lb, nb, x, v, px, pf, gx, ctrl, parts, nullptr);
             break;
@@ -194,6 +200,11 @@ cudaError_t launch_pso(const zeus_problem& p, int G, double* x, double* v, doubl
                        double* gx, Ctrl* ctrl, ArgPair* partials, zeus_result* res,
                        cudaStream_t st) {
     switch (p.objective) {
+#define ZEUS_UCASE(O) \
+    case O:           \
+        return pso_run<O>(p, G, x, v, px, pf, gx, ctrl, partials, res, st);
+        ZEUS_USER_EACH(ZEUS_UCASE)
+#undef ZEUS_UCASE
         case ZEUS_OBJ_ROSENBROCK:
             return pso_run<ZEUS_OBJ_ROSENBROCK>(p, G, x, v, px, pf, gx, ctrl, partials, res, st);
         case ZEUS_OBJ_RASTRIGIN:

@@ -40,6 +40,12 @@ WORKLOADS = {
                                   n_starts=2048, pso_iters=10, bfgs_max_iters=500, ls_max_iters=20,
                                   grad_tol=1e-8, w=0.7, c1=1.5, c2=1.5, armijo_c=1e-4,
                                   backtrack=0.5, seed=0),
+    # a user objective (the default plug-in's Griewank, not built in): 16384
+    # particles in its usual box [-600,600]^10, 20 PSO updates, 1000 iterations
+    "griewank10d_n16384": dict(objective="griewank", dim=10, lower=-600.0, upper=600.0,
+                               n_starts=16384, pso_iters=20, bfgs_max_iters=1000, ls_max_iters=20,
+                               grad_tol=1e-8, w=0.7, c1=1.5, c2=1.5, armijo_c=1e-4, backtrack=0.5,
+                               seed=0),
 }
 
 # batched form: many independent problems, each with its own swarm

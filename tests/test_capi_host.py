@@ -233,3 +233,57 @@ def test_lbfgs_plan(z):
     assert z.zeus_plan_info(p.replace(threads_per_start=256))["lbfgs"] == 1
     with pytest.raises(z.ZeusError):  # not batched
         z.zeus_batch_plan_make([z.Problem(), p.replace(precision="fp64", dim=20, n_starts=8)])
+
+
+def test_user_objectives_of_the_default_plugin(z):
+    L = z.lib()
+    assert L.zeus_user_objective_count() == 2
+    assert z.user_objectives() == {"griewank": (200, 1, 0), "himmelblau": (201, 2, 2)}
+    buf = C.create_string_buffer(4)  # truncated to fit, NUL-terminated
+    lo, hi = C.c_int32(), C.c_int32()
+    assert L.zeus_user_objective_info(0, buf, 4, C.byref(lo), C.byref(hi)) == 0
+    assert buf.value == b"gri" and (lo.value, hi.value) == (1, 0)
+    assert L.zeus_user_objective_info(1, None, 0, None, None) == 0
+    for k in (-1, 2, 4, 200):
+        assert L.zeus_user_objective_info(k, buf, 4, None, None) == z._capi.ZEUS_EINVAL
+    assert z.Problem(objective="himmelblau").to_c().objective == 201
+    with pytest.raises(KeyError):
+        z.Problem(objective="no_such_function").to_c()
+
+
+def test_user_objective_validation_and_plans(z):
+    EINVAL, EUNS = z._capi.ZEUS_EINVAL, z._capi.ZEUS_EUNSUPPORTED
+    g = z.Problem(objective="griewank", dim=8, n_starts=64)
+    assert z.zeus_validate(g) == 0 and z.zeus_validate(g.replace(dim=1)) == 0
+    assert z.zeus_validate(g.replace(objective="himmelblau", dim=2)) == 0
+    # the plug-in's dimension range; ids past the plug-in's objectives
+    assert z.zeus_validate(g.replace(objective="himmelblau", dim=3)) == EINVAL
+    assert z.zeus_validate(g.replace(objective=202)) == EINVAL
+    assert z.zeus_validate(g.replace(objective=199)) == EINVAL
+    # forward mode only
+    assert z.zeus_validate(g.replace(grad_mode="adjoint")) == EUNS
+    # lane, block and hand-over forms as for a built-in objective
+    assert z.zeus_plan_info(g)["narrow"] == 1 and z.zeus_plan_info(g)["handover"] == 1
+    assert z.zeus_plan_info(g.replace(dim=64))["block"] == 1
+    # no form that streams H, and no L-BFGS
+    for bad in (dict(dim=512), dict(threads_per_start=256), dict(lbfgs_m=4)):
+        with pytest.raises(z.ZeusError) as e:
+            z.zeus_plan_info(g.replace(**bad))
+        assert e.value.code == EUNS
+
+
+def test_user_objectives_in_a_batch_plan(z):
+    probs = _mixed(z, 4) + [z.Problem(objective="griewank", dim=6, n_starts=100),
+                            z.Problem(objective="himmelblau", dim=2, n_starts=300, seed=3)]
+    pl = z.zeus_batch_plan_make(probs)
+    assert pl.n_user == 2 and pl.pad == 0
+    assert z.zeus_batch_plan_make(probs[:4]).n_user == 0
+    with pytest.raises(z.ZeusError) as e:
+        z.zeus_batch_plan_make([p.replace(grad_mode="adjoint") for p in probs])
+    assert e.value.code == z._capi.ZEUS_EUNSUPPORTED
+    # a plan whose user count was altered is refused before any launch
+    L = z.lib()
+    bad = z._capi.zeus_batch_plan.from_buffer_copy(bytes(pl))
+    bad.n_user = len(probs) + 1
+    assert L.zeus_batch_solve(C.byref(bad), C.c_void_p(4096), 1 << 40, C.c_void_p(256),
+                              C.c_void_p(256), None, None, None, None, None) == z._capi.ZEUS_EINVAL
