@@ -80,31 +80,63 @@ def test_himmelblau_whole_method_bit_exact(z, ora):
     assert set(np.argmin(dist, axis=1).tolist()) == {0, 1, 2, 3}
 
 
+def _n_apart(a, b):
+    """Starts whose runs differ: status, iteration count, f beyond 1e-9
+    relative or a coordinate beyond 1e-9 relative."""
+    dx = np.abs(a["x"] - b["x"]).max(axis=1) / np.maximum(1.0, np.abs(b["x"]).max(axis=1))
+    df = np.abs(a["f"] - b["f"]) / np.maximum(1.0, np.abs(b["f"]))
+    return int(((a["status"] != b["status"]) | (a["iters"] != b["iters"]) | (df > 1e-9)
+                | (dx > 1e-9)).sum())
+
+
+def _ulp_spread(ora, fields, x0):
+    """How far the oracle moves from itself when every start coordinate is
+    moved by one unit in the last place (up, then down): the scale of the
+    disagreement that last-bit differences alone cause along these runs."""
+    prob = oracle_problem(ora, fields)
+    o = ora.bfgs_many(prob, x0)
+    up = ora.bfgs_many(prob, np.nextafter(x0, np.inf))
+    down = ora.bfgs_many(prob, np.nextafter(x0, -np.inf))
+    return o, max(_n_apart(up, o), _n_apart(down, o))
+
+
 @pytest.mark.parametrize("d,n,mode", [(8, 700, 0), (8, 300, 1), (8, 96, 128), (40, 48, 0)])
-def test_griewank_forms_against_oracle(z, ora, d, n, mode):
-    # mode 0: the automatic plan (lane tiles with hand-over through the fused
-    # launch for d = 8, one block per start for d = 40); 1: lanes only;
-    # 128: one block per start
+@pytest.mark.parametrize("iters", [5, 20, 60])
+def test_griewank_forms_against_oracle(z, ora, d, n, mode, iters):
+    # mode 0: the automatic plan (lane tiles for d = 8, one block per start
+    # for d = 40); 1: lanes only; 128: one block per start.  The cosines of
+    # CUDA's and the host's math libraries differ in the last bit, and
+    # BFGS on this flat, coupled function amplifies last-bit differences
+    # (the curvature y's is small against |y||s|): the CUDA path may be as
+    # far from the oracle as the oracle is from itself after a one-ulp move
+    # of the starts, and no farther
     x0 = workloads.start_points(n, d, -20.0, 20.0, seed=d + n)
-    fields = dict(objective="griewank", dim=d, n_starts=n, bfgs_max_iters=60,
+    fields = dict(objective="griewank", dim=d, n_starts=n, bfgs_max_iters=iters,
                   threads_per_start=mode)
     g = to_np(z.solve_from(zeus_problem(z, fields), torch.from_numpy(x0).cuda()))
-    o = ora.bfgs_many(oracle_problem(ora, fields), x0)
-    compare_runs(g, o, rtol=1e-9, max_flip_frac=0.05)
+    o, spread = _ulp_spread(ora, fields, x0)
+    apart = _n_apart(g, o)
+    assert apart <= 2 * spread + max(2, n // 100), (apart, spread)
     assert g["summary"]["best_index"] == ora.argmin(g["f"])
 
 
 def test_griewank_long_runs_through_the_handover(z, ora):
-    # enough iterations that lane starts pass the hand-over budget; the
-    # kernel choice keeps the oracle's results within the tolerance
-    d, n = 6, 400
+    # whole runs, with starts that pass the lane kernel's budget of 160
+    # iterations and line-search evaluations (the fused launch serves them):
+    # the same bar, and every start that converged to the same point on
+    # both sides has the same f to 1e-12
+    d, n = 12, 400
     x0 = workloads.start_points(n, d, -60.0, 60.0, seed=5)
     fields = dict(objective="griewank", dim=d, n_starts=n, bfgs_max_iters=400)
     assert z.zeus_plan_info(zeus_problem(z, fields))["handover"] == 1
     g = to_np(z.solve_from(zeus_problem(z, fields), torch.from_numpy(x0).cuda()))
-    o = ora.bfgs_many(oracle_problem(ora, fields), x0)
-    n_cmp, flips = compare_runs(g, o, rtol=1e-8, max_flip_frac=0.1)
-    assert n_cmp > 0.9 * n
+    o, spread = _ulp_spread(ora, fields, x0)
+    assert ((o["iters"] + o["n_feval"]) > 160).sum() >= 40
+    apart = _n_apart(g, o)
+    assert apart <= 2 * spread + 4, (apart, spread)
+    both = (g["status"] == 1) & (o["status"] == 1) & (np.abs(g["x"] - o["x"]).max(axis=1) <= 1e-6)
+    assert both.sum() > n // 2
+    assert np.all(np.abs(g["f"][both] - o["f"][both]) <= 1e-12)
 
 
 @pytest.mark.parametrize("obj,d", [("griewank", 10), ("himmelblau", 2)])
