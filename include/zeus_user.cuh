@@ -23,10 +23,15 @@
  *
  * In eval, x(j) returns coordinate j (0 <= j < d) as S, where S is
  *   float or double            for values (the FP32 and FP64 forms), and
- *   zeus_user::dual<float> or zeus_user::dual<double> for derivatives.
+ *   zeus_user::dual<T>, zeus_user::duals<T, N>  for derivatives (T float
+ *                              or double; duals carries N tangents, so
+ *                              that one evaluation gives N components of
+ *                              the gradient: each tangent goes through the
+ *                              same operations as in its own pass of
+ *                              Alg. 5, and the results are the same bits).
  * Write f with + - * / between two S or an S and its scalar type
  * (scalar_t<S>), S(c) for constants, and the functions below, which are
- * defined for all four types.  Branch on value(s) only.  eval is called by
+ * defined for all of these types.  Branch on value(s) only.  eval is called by
  * one thread for the whole point: its loops run in index order.
  *
  * Limits: gradients are forward-mode only (ZEUS_GRAD_ADJOINT needs a
@@ -83,6 +88,102 @@ struct dual {
     __host__ __device__ dual& operator/=(dual b) { return *this = *this / b; }
 };
 
+// value and N tangents (N seeded directions in one evaluation)
+template <class T, int N>
+struct duals {
+    T v;
+    T t[N];
+
+    duals() = default;
+    __host__ __device__ duals(T value) : v(value) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) t[q] = T(0);
+    }
+
+    friend __host__ __device__ duals operator+(duals a, duals b) {
+        a.v = a.v + b.v;
+#pragma unroll
+        for (int q = 0; q < N; ++q) a.t[q] = a.t[q] + b.t[q];
+        return a;
+    }
+    friend __host__ __device__ duals operator-(duals a, duals b) {
+        a.v = a.v - b.v;
+#pragma unroll
+        for (int q = 0; q < N; ++q) a.t[q] = a.t[q] - b.t[q];
+        return a;
+    }
+    friend __host__ __device__ duals operator*(duals a, duals b) {
+        duals r;
+        r.v = a.v * b.v;
+#pragma unroll
+        for (int q = 0; q < N; ++q) r.t[q] = a.t[q] * b.v + a.v * b.t[q];
+        return r;
+    }
+    friend __host__ __device__ duals operator/(duals a, duals b) {
+        duals r;
+        r.v = a.v / b.v;
+        const T bb = b.v * b.v;
+#pragma unroll
+        for (int q = 0; q < N; ++q) r.t[q] = (a.t[q] * b.v - a.v * b.t[q]) / bb;
+        return r;
+    }
+    friend __host__ __device__ duals operator-(duals a) {
+        a.v = -a.v;
+#pragma unroll
+        for (int q = 0; q < N; ++q) a.t[q] = -a.t[q];
+        return a;
+    }
+    friend __host__ __device__ duals operator+(duals a, T s) {
+        a.v = a.v + s;
+        return a;
+    }
+    friend __host__ __device__ duals operator+(T s, duals a) {
+        a.v = s + a.v;
+        return a;
+    }
+    friend __host__ __device__ duals operator-(duals a, T s) {
+        a.v = a.v - s;
+        return a;
+    }
+    friend __host__ __device__ duals operator-(T s, duals a) {
+        a.v = s - a.v;
+#pragma unroll
+        for (int q = 0; q < N; ++q) a.t[q] = -a.t[q];
+        return a;
+    }
+    friend __host__ __device__ duals operator*(duals a, T s) {
+        a.v = a.v * s;
+#pragma unroll
+        for (int q = 0; q < N; ++q) a.t[q] = a.t[q] * s;
+        return a;
+    }
+    friend __host__ __device__ duals operator*(T s, duals a) {
+        a.v = s * a.v;
+#pragma unroll
+        for (int q = 0; q < N; ++q) a.t[q] = s * a.t[q];
+        return a;
+    }
+    friend __host__ __device__ duals operator/(duals a, T s) {
+        a.v = a.v / s;
+#pragma unroll
+        for (int q = 0; q < N; ++q) a.t[q] = a.t[q] / s;
+        return a;
+    }
+    friend __host__ __device__ duals operator/(T s, duals a) {
+        duals r;
+        r.v = s / a.v;
+        const T aa = a.v * a.v;
+#pragma unroll
+        for (int q = 0; q < N; ++q) r.t[q] = -(s * a.t[q]) / aa;
+        return r;
+    }
+
+    __host__ __device__ duals& operator+=(duals b) { return *this = *this + b; }
+    __host__ __device__ duals& operator-=(duals b) { return *this = *this - b; }
+    __host__ __device__ duals& operator*=(duals b) { return *this = *this * b; }
+    __host__ __device__ duals& operator/=(duals b) { return *this = *this / b; }
+};
+
 // the scalar type under S
 template <class S>
 struct scalar_of {
@@ -92,6 +193,10 @@ template <class T>
 struct scalar_of<dual<T>> {
     using type = T;
 };
+template <class T, int N>
+struct scalar_of<duals<T, N>> {
+    using type = T;
+};
 template <class S>
 using scalar_t = typename scalar_of<S>::type;
 
@@ -99,6 +204,10 @@ __host__ __device__ inline float value(float a) { return a; }
 __host__ __device__ inline double value(double a) { return a; }
 template <class T>
 __host__ __device__ inline T value(dual<T> a) {
+    return a.v;
+}
+template <class T, int N>
+__host__ __device__ inline T value(const duals<T, N>& a) {
     return a.v;
 }
 
@@ -150,6 +259,58 @@ template <class T>
 __device__ inline dual<T> tanh(dual<T> a) {
     const T h = tanh(a.v);
     return dual<T>(h, (T(1) - h * h) * a.t);
+}
+
+// ... and on N tangents at once, each as in its own pass
+template <class T, int N>
+__device__ inline duals<T, N> sin(duals<T, N> a) {
+    T s, c;
+    sincos(a.v, &s, &c);
+    a.v = s;
+#pragma unroll
+    for (int q = 0; q < N; ++q) a.t[q] = c * a.t[q];
+    return a;
+}
+template <class T, int N>
+__device__ inline duals<T, N> cos(duals<T, N> a) {
+    T s, c;
+    sincos(a.v, &s, &c);
+    a.v = c;
+#pragma unroll
+    for (int q = 0; q < N; ++q) a.t[q] = -s * a.t[q];
+    return a;
+}
+template <class T, int N>
+__device__ inline duals<T, N> exp(duals<T, N> a) {
+    const T e = exp(a.v);
+    a.v = e;
+#pragma unroll
+    for (int q = 0; q < N; ++q) a.t[q] = e * a.t[q];
+    return a;
+}
+template <class T, int N>
+__device__ inline duals<T, N> log(duals<T, N> a) {
+    const T v = a.v;
+    a.v = log(v);
+#pragma unroll
+    for (int q = 0; q < N; ++q) a.t[q] = a.t[q] / v;
+    return a;
+}
+template <class T, int N>
+__device__ inline duals<T, N> sqrt(duals<T, N> a) {
+    const T r = sqrt(a.v);
+    a.v = r;
+#pragma unroll
+    for (int q = 0; q < N; ++q) a.t[q] = r > T(0) ? a.t[q] / (T(2) * r) : T(0);
+    return a;
+}
+template <class T, int N>
+__device__ inline duals<T, N> tanh(duals<T, N> a) {
+    const T h = tanh(a.v);
+    a.v = h;
+#pragma unroll
+    for (int q = 0; q < N; ++q) a.t[q] = (T(1) - h * h) * a.t[q];
+    return a;
 }
 
 // a^n for n >= 0 by repeated multiplication (any S)

@@ -171,6 +171,18 @@ __device__ __forceinline__ T grad_component(const T* x, int d, int i, const AdjS
     return adjoint_component<OBJ>(x, d, i, a);
 }
 
+// The whole gradient on one thread (the lane kernel): component by
+// component, or a user objective's chunked passes
+template <int OBJ, int GRAD, class T>
+__device__ __forceinline__ void grad_all(const T* x, int d, T* g) {
+    if constexpr (OBJ >= ZEUS_OBJ_USER && GRAD == ZEUS_GRAD_FORWARD) {
+        user_gradient<OBJ, T>(x, d, g);
+    } else {
+        const AdjShared a = grad_prep<OBJ, GRAD>(x, d);
+        for (int i = 0; i < d; ++i) g[i] = grad_component<OBJ, GRAD>(x, d, i, a);
+    }
+}
+
 // final f and its output: FP64 value at the point (FP32 points promoted)
 template <int OBJ>
 __device__ __forceinline__ double final_value(const double* x, int d, double f0) {
@@ -214,8 +226,7 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
     for (int r = 0; r < d; ++r)
         for (int c = 0; c < d; ++c) H[r * d + c] = (c == r) ? T(1) : T(0);
     {
-        const AdjShared a = grad_prep<OBJ, GRAD>(x, d);
-        for (int i = 0; i < d; ++i) g[i] = grad_component<OBJ, GRAD>(x, d, i, a);
+        grad_all<OBJ, GRAD>(x, d, g);
     }
     double f0 = seq_value<OBJ>(AtPoint<T>{x}, d);
 
@@ -329,8 +340,7 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
         }
         ls_failed = !accepted;
         {
-            const AdjShared a = grad_prep<OBJ, GRAD>(xn, d);
-            for (int i = 0; i < d; ++i) gn[i] = grad_component<OBJ, GRAD>(xn, d, i, a);
+            grad_all<OBJ, GRAD>(xn, d, gn);
         }
         // curvature pair
         double sy = 0.0, ss = 0.0, yy = 0.0;

@@ -308,6 +308,37 @@ struct UserSeed {
     }
 };
 
+// N tangents per evaluation: seeds e_{i0} .. e_{i0+N-1} (those past d
+// match no coordinate and stay zero)
+template <class T, int N>
+struct UserSeeds {
+    const T* x;
+    int i0;
+    __device__ __forceinline__ zeus_user::duals<T, N> operator()(int j) const {
+        zeus_user::duals<T, N> r(x[j]);
+#pragma unroll
+        for (int q = 0; q < N; ++q) r.t[q] = (j - i0 == q) ? T(1) : T(0);
+        return r;
+    }
+};
+
+// The whole gradient of a user objective on one thread: the d passes of
+// Alg. 5 taken kUserChunk at a time (vector forward mode).  Each tangent
+// goes through the operations of its own pass, so g is the same bits as d
+// single passes, while the value part (and its elementary functions) is
+// evaluated once per chunk instead of once per pass.
+constexpr int kUserChunk = 4;
+template <int OBJ, class T>
+__device__ __forceinline__ void user_gradient(const T* x, int d, T* g) {
+    using V = zeus_user::duals<T, kUserChunk>;
+    for (int i0 = 0; i0 < d; i0 += kUserChunk) {
+        const V r = UserObjective<OBJ>::template eval<V>(UserSeeds<T, kUserChunk>{x, i0}, d);
+#pragma unroll
+        for (int q = 0; q < kUserChunk; ++q)
+            if (i0 + q < d) g[i0 + q] = r.t[q];
+    }
+}
+
 template <int OBJ, class T, class A>
 __device__ __forceinline__ Part<A> builtin_value_partial(const T* x, int d, int lane, int G) {
     Part<A> p;
