@@ -377,6 +377,64 @@ int zeus_solve_host(zeus_context *ctx, const zeus_problem *p, double *x_out,
                     double *f_out, double *gnorm_out, int32_t *status_out,
                     int32_t *iters_out, zeus_result *result, void *stream);
 
+/* ---- Solution clustering (Section VI names it as future work: cluster
+ * the candidate solutions of the multistart by function value or by
+ * coordinates, and take confidence in the region of the lowest f from the
+ * number of starts that reached it) ----
+ *
+ * Candidates: starts whose f is finite (and, with only_converged, whose
+ * status is ZEUS_RUN_CONVERGED).  Leader clustering in the order of
+ * increasing (f, start index): each candidate joins the first existing
+ * leader it is within tol of, else it becomes the next leader.  Cluster k
+ * is the k-th leader's; cluster 0 holds the start of the lowest f.  "Within
+ * tol" of leader L:
+ *   ZEUS_CLUSTER_BY_F  |f_i - f_L| <= tol * max(1, |f_L|)
+ *   ZEUS_CLUSTER_BY_X  sum_j (x_ij - x_Lj)^2 <= tol^2, the sum formed in
+ *                      index order, one rounding per term (fused
+ *                      multiply-add), in FP64
+ * Only the first max_clusters clusters are formed; the candidates left then
+ * are reported as unclustered. */
+#define ZEUS_CLUSTER_BY_F 0
+#define ZEUS_CLUSTER_BY_X 1
+#define ZEUS_CLUSTER_MAX 4096     /* largest max_clusters */
+#define ZEUS_LABEL_NONE (-1)      /* not a candidate */
+#define ZEUS_LABEL_LEFT (-2)      /* candidate left after max_clusters clusters */
+
+typedef struct {
+    int32_t method;           /* ZEUS_CLUSTER_BY_F or ZEUS_CLUSTER_BY_X */
+    int32_t max_clusters;     /* 1 .. ZEUS_CLUSTER_MAX */
+    int32_t only_converged;   /* 0 or 1 (needs status) */
+    int32_t pad;              /* 0 */
+    double tol;               /* >= 0, finite */
+} zeus_cluster_params;
+
+typedef struct {
+    int64_t n_candidates;
+    int64_t n_clusters;       /* clusters formed */
+    int64_t n_left;           /* candidates in no cluster (max_clusters reached) */
+    int64_t best_count;       /* members of cluster 0, the region of the lowest f */
+    int64_t best_leader;      /* start index of its leader (lowest f); -1 if none */
+    double best_f;            /* f of that leader (NaN if none) */
+    double best_spread;       /* largest distance (BY_X: sqrt of the sum above) or
+                                 |f_i - f_L| (BY_F) of a member of cluster 0 */
+    int32_t error;            /* 0 */
+    int32_t pad;
+} zeus_cluster_result;
+
+/* Clusters the n final points of one problem (zeus_solve outputs).
+ *   x: device double [n][dim]; f: device double [n]; status: device int32
+ *   [n] (may be NULL unless only_converged); label_out: device int32 [n]
+ *   (cluster id, ZEUS_LABEL_NONE or ZEUS_LABEL_LEFT); leader_out, count_out:
+ *   device int32 [max_clusters] (leader start index and member count of
+ *   each cluster formed, -1 / 0 past n_clusters; may be NULL); result:
+ *   device zeus_cluster_result (may be NULL).
+ * One block on `stream`; n < 2^31.  ZEUS_EINVAL for bad parameters or
+ * pointers, before any launch. */
+int zeus_cluster(const zeus_cluster_params *cp, int64_t n, int32_t dim, const double *x,
+                 const double *f, const int32_t *status, int32_t *label_out,
+                 int32_t *leader_out, int32_t *count_out, zeus_cluster_result *result,
+                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,6 +106,12 @@ class Problem:
                         self.n_threads, self.lbfgs_m, 0)
 
 
+class _ClusterResult(C.Structure):
+    _fields_ = [("n_candidates", C.c_int64), ("n_clusters", C.c_int64), ("n_left", C.c_int64),
+                ("best_count", C.c_int64), ("best_leader", C.c_int64), ("best_f", C.c_double),
+                ("best_spread", C.c_double), ("error", C.c_int32), ("pad", C.c_int32)]
+
+
 _lib = None
 _D = C.POINTER(C.c_double)
 _U64 = C.POINTER(C.c_uint64)
@@ -129,6 +135,8 @@ def lib():
     L.zo_f.argtypes = [C.c_int, C.c_int, _D]
     L.zo_f.restype = C.c_double
     L.zo_grad_forward.argtypes = [C.c_int, C.c_int, _D, _D, _D]
+    L.zo_cluster.argtypes = [C.c_int, C.c_double, C.c_int32, C.c_int, C.c_int64, C.c_int, _D,
+                             _D, _I32, _I32, _I32, _I32, C.POINTER(_ClusterResult)]
     L.zo_argmin.argtypes = [_D, C.c_int64]
     L.zo_argmin.restype = C.c_int64
     L.zo_pso.argtypes = [C.POINTER(_Problem), _D, _D, _D, _D, _D, _D, _I64]
@@ -330,3 +338,29 @@ def lbfgs_direction(S, Y, g):
     lib().zo_lbfgs_direction(d, n, _dp(S if n else np.zeros(1)), _dp(Y if n else np.zeros(1)),
                              _dp(rho if n else np.zeros(1)), _dp(g), _dp(p))
     return p
+
+
+CLUSTER_METHODS = {"f": 0, "x": 1}
+
+
+def cluster(x, f, status=None, method="x", tol=1e-3, max_clusters=256, only_converged=False):
+    """Leader clustering of final points (the reading of Section VI's
+    clustering in zeus_oracle.c): labels [n] (cluster id, -1 not a
+    candidate, -2 left), leaders and counts [max_clusters], summary."""
+    f = _f64(f)
+    n = f.size
+    x = _f64(x).reshape(n, -1) if x is not None else np.zeros((n, 1))
+    d = x.shape[1]
+    st = (np.ascontiguousarray(status, dtype=np.int32) if status is not None
+          else np.ones(n, dtype=np.int32))
+    lab = np.zeros(max(n, 1), dtype=np.int32)
+    lead = np.zeros(max_clusters, dtype=np.int32)
+    cnt = np.zeros(max_clusters, dtype=np.int32)
+    r = _ClusterResult()
+    m = CLUSTER_METHODS[method] if isinstance(method, str) else int(method)
+    p32 = C.POINTER(C.c_int)
+    lib().zo_cluster(m, float(tol), int(max_clusters), int(only_converged), n, d, _dp(x), _dp(f),
+                     st.ctypes.data_as(p32), lab.ctypes.data_as(p32), lead.ctypes.data_as(p32),
+                     cnt.ctypes.data_as(p32), C.byref(r))
+    summary = {k: getattr(r, k) for k, _ in _ClusterResult._fields_}
+    return dict(labels=lab[:n], leaders=lead, counts=cnt, summary=summary)

@@ -855,6 +855,112 @@ int zo_bfgs_quadratic_exact(int d, const double *A, const double *x0,
     return k;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Solution clustering (Section VI, future work: group the candidate         */
+/* solutions by function value or by coordinates; the number of starts in   */
+/* the region of the lowest f measures the confidence in it).               */
+/* Reading: leader clustering.  The candidates (finite f; with               */
+/* only_converged, status 1 only) are visited in order of increasing         */
+/* (f, start index).  A candidate joins the first leader, in the order the  */
+/* leaders were made, that it is within tol of; if there is none it becomes */
+/* a new leader, unless max_clusters leaders exist already, in which case  */
+/* it is left out (label -2).  Non-candidates get label -1.                 */
+/* "Within tol" of leader L: method 0 (by f) |f_i - f_L| <= tol max(1,|f_L|);*/
+/* method 1 (by x) sum_j (x_ij - x_Lj)^2 <= tol^2, summed in index order    */
+/* with one rounding per term (fma), the FMA reading of the dot products.  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t n_candidates, n_clusters, n_left, best_count, best_leader;
+    double best_f, best_spread;
+    int32_t error, pad;
+} zo_cluster_result;
+
+typedef struct {
+    double f;
+    int64_t i;
+} zo_key;
+
+static int zo_key_cmp(const void *a, const void *b)
+{
+    const zo_key *p = (const zo_key *)a, *q = (const zo_key *)b;
+    if (p->f < q->f) return -1;
+    if (p->f > q->f) return 1;
+    return (p->i > q->i) - (p->i < q->i);
+}
+
+/* distance of start i to leader l (by x: the Euclidean norm of the sum
+ * above; by f: |f_i - f_l|) and whether it is within tol */
+static int zo_within(int method, double tol, int d, const double *x, const double *f,
+                     int64_t i, int64_t l, double *dist)
+{
+    if (method == 1) {
+        double acc = 0.0;
+        for (int j = 0; j < d; ++j) {
+            double del = x[i * d + j] - x[l * d + j];
+            acc = fma(del, del, acc);
+        }
+        *dist = sqrt(acc);
+        return acc <= tol * tol;
+    }
+    *dist = fabs(f[i] - f[l]);
+    return *dist <= tol * fmax(1.0, fabs(f[l]));
+}
+
+int zo_cluster(int method, double tol, int32_t max_clusters, int only_converged, int64_t n,
+               int d, const double *x, const double *f, const int32_t *status, int32_t *label,
+               int32_t *leader, int32_t *count, zo_cluster_result *res)
+{
+    zo_key *keys = (zo_key *)malloc(sizeof(zo_key) * (size_t)(n > 0 ? n : 1));
+    int64_t m = 0, left = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        label[i] = -1;
+        if (isfinite(f[i]) && (!only_converged || status[i] == 1)) {
+            keys[m].f = f[i];
+            keys[m].i = i;
+            ++m;
+        }
+    }
+    qsort(keys, (size_t)m, sizeof(zo_key), zo_key_cmp);
+    for (int k = 0; k < max_clusters; ++k) { leader[k] = -1; count[k] = 0; }
+    int K = 0;
+    double spread0 = 0.0;
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t i = keys[q].i;
+        int joined = 0;
+        for (int k = 0; k < K && !joined; ++k) {
+            double dist;
+            if (zo_within(method, tol, d, x, f, i, leader[k], &dist)) {
+                label[i] = k;
+                count[k] += 1;
+                if (k == 0 && dist > spread0) spread0 = dist;
+                joined = 1;
+            }
+        }
+        if (joined) continue;
+        if (K < max_clusters) {
+            leader[K] = (int32_t)i;
+            count[K] = 1;
+            label[i] = K;
+            ++K;
+        } else {
+            label[i] = -2;
+            ++left;
+        }
+    }
+    res->n_candidates = m;
+    res->n_clusters = K;
+    res->n_left = left;
+    res->best_count = K > 0 ? count[0] : 0;
+    res->best_leader = K > 0 ? leader[0] : -1;
+    res->best_f = K > 0 ? f[leader[0]] : NAN;
+    res->best_spread = K > 0 ? spread0 : NAN;
+    res->error = 0;
+    res->pad = 0;
+    free(keys);
+    return 0;
+}
+
 int zo_sizeof_problem(void) { return (int)sizeof(zo_problem); }
 int zo_sizeof_result(void) { return (int)sizeof(zo_result); }
 int zo_max_threads(void)

@@ -27,7 +27,7 @@ __all__ = [
     "zeus_workspace_size", "zeus_plan_info", "zeus_validate", "zeus_default_problem", "zeus_strerror",
     "zeus_abi_version", "zeus_math_eval", "Context", "solve", "solve_from", "pso", "objective", "ObjectiveFn",
     "decode_result", "library_path", "lib", "zeus_batch_plan_make", "zeus_batch_prepare",
-    "zeus_batch_solve", "Batch", "user_objectives",
+    "zeus_batch_solve", "Batch", "user_objectives", "zeus_cluster", "cluster", "solve_until_confident",
 ]
 
 
@@ -487,6 +487,64 @@ class ObjectiveFn(torch.autograd.Function):
     def backward(ctx, grad_out):
         (g,) = ctx.saved_tensors
         return grad_out.unsqueeze(1) * g, None, None
+
+
+# ------------------------------------------------ solution clustering
+
+def zeus_cluster(params, n, dim, x, f, status, label_out, leader_out=None, count_out=None,
+                 result=None, stream=None) -> None:
+    mc = params.max_clusters
+    check(lib().zeus_cluster(
+        C.byref(params), n, dim, _ptr(x, torch.float64, n * dim, "x"), _ptr(f, torch.float64, n, "f"),
+        _ptr(status, torch.int32, n, "status"), _ptr(label_out, torch.int32, n, "label_out"),
+        _ptr(leader_out, torch.int32, mc, "leader_out"), _ptr(count_out, torch.int32, mc, "count_out"),
+        _ptr(result, torch.uint8, C.sizeof(_capi.zeus_cluster_result), "result"), _stream(stream)),
+        "zeus_cluster")
+
+
+def cluster(x: torch.Tensor, f: torch.Tensor, status: torch.Tensor | None = None, method="x",
+            tol: float = 1e-3, max_clusters: int = 256, only_converged: bool = False,
+            stream=None) -> dict:
+    """Clusters final points on the device (leader clustering in order of
+    increasing f, by f or by coordinates; include/zeus.h): labels [n],
+    leaders and member counts [max_clusters], and the summary (synchronizes)."""
+    n = f.numel()
+    dim = x.shape[1] if x is not None and x.dim() == 2 else 1
+    cp = _capi.zeus_cluster_params(_capi.CLUSTER_METHODS[method] if isinstance(method, str) else int(method),
+                                   int(max_clusters), int(bool(only_converged)), 0, float(tol))
+    dev = f.device
+    out = {"labels": torch.empty(n, dtype=torch.int32, device=dev),
+           "leaders": torch.empty(max_clusters, dtype=torch.int32, device=dev),
+           "counts": torch.empty(max_clusters, dtype=torch.int32, device=dev),
+           "result": torch.empty(C.sizeof(_capi.zeus_cluster_result), dtype=torch.uint8, device=dev)}
+    zeus_cluster(cp, n, dim, x.contiguous() if x is not None else None, f.contiguous(),
+                 status.contiguous() if status is not None else None, out["labels"], out["leaders"],
+                 out["counts"], out["result"], stream)
+    raw = bytes(out["result"].cpu().numpy().tobytes())
+    r = _capi.zeus_cluster_result.from_buffer_copy(raw)
+    out["summary"] = {k: getattr(r, k) for k, _ in _capi.zeus_cluster_result._fields_}
+    return out
+
+
+def solve_until_confident(problem: Problem, required: int, tol: float = 1e-3, method="x",
+                          max_rounds: int = 10, device="cuda") -> dict:
+    """The iterative process Section VI proposes: solve the problem again
+    with fresh seeds (seed, seed + 1, ...), cluster the converged points of
+    all rounds so far, and stop once the region of the lowest f holds at
+    least `required` starts (or after max_rounds).  Returns the clustering
+    of the pooled points, the pooled outputs and the number of rounds."""
+    xs, fs, ss = [], [], []
+    for r in range(max_rounds):
+        out = solve(problem.replace(seed=problem.seed + r), device=device)
+        xs.append(out["x"])
+        fs.append(out["f"])
+        ss.append(out["status"])
+        x, f, st = torch.cat(xs), torch.cat(fs), torch.cat(ss)
+        c = cluster(x, f, st, method=method, tol=tol, max_clusters=1, only_converged=True)
+        if c["summary"]["best_count"] >= required:
+            break
+    c.update(x=x, f=f, status=st, rounds=r + 1)
+    return c
 
 
 def status_names(status: torch.Tensor):

@@ -76,6 +76,22 @@ class zeus_batch_plan(C.Structure):
                 ("workspace_bytes", C.c_uint64), ("table_bytes", C.c_uint64)]
 
 
+CLUSTER_METHODS = {"f": 0, "x": 1}
+CLUSTER_MAX = 4096
+LABEL_NONE, LABEL_LEFT = -1, -2
+
+
+class zeus_cluster_params(C.Structure):
+    _fields_ = [("method", C.c_int32), ("max_clusters", C.c_int32), ("only_converged", C.c_int32),
+                ("pad", C.c_int32), ("tol", C.c_double)]
+
+
+class zeus_cluster_result(C.Structure):
+    _fields_ = [("n_candidates", C.c_int64), ("n_clusters", C.c_int64), ("n_left", C.c_int64),
+                ("best_count", C.c_int64), ("best_leader", C.c_int64), ("best_f", C.c_double),
+                ("best_spread", C.c_double), ("error", C.c_int32), ("pad", C.c_int32)]
+
+
 class ZeusError(RuntimeError):
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {strerror(code)} ({code})")
@@ -109,6 +125,8 @@ SIGNATURES = {
     "zeus_uniform": (C.c_int, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int32, _VP,
                                _VP]),
     "zeus_math_eval": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, _VP, _VP]),
+    "zeus_cluster": (C.c_int, [C.POINTER(zeus_cluster_params), C.c_int64, C.c_int32, _VP, _VP, _VP,
+                               _VP, _VP, _VP, _VP, _VP]),
     "zeus_user_objective_count": (C.c_int32, []),
     "zeus_user_objective_info": (C.c_int, [C.c_int32, C.c_char_p, C.c_int32,
                                            C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),

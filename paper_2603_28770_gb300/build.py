@@ -23,7 +23,7 @@ LIB = os.path.join(BUILD, "libzeus.so")
 # pair are compiled as translation units of their own, in parallel
 _PAIRS = [("-DZEUS_KGRAD=%d" % g, "-DZEUS_KF32=%d" % f) for g in (0, 1) for f in (0, 1)]
 SOURCES = ([(s, ()) for s in ("zeus_capi.cu", "zeus_pso.cu", "zeus_bfgs.cu", "zeus_objective.cu",
-                              "zeus_noalloc.cu", "zeus_stream.cu", "zeus_batch.cu")]
+                              "zeus_noalloc.cu", "zeus_stream.cu", "zeus_batch.cu", "zeus_cluster.cu")]
            + [("zeus_bfgs_kernels.cu", d) for d in _PAIRS]
            + [("zeus_batch_kernels.cu", d) for d in _PAIRS]
            + [("zeus_batch_kernels.cu", ("-DZEUS_KGRAD=0", "-DZEUS_KF32=%d" % f, "-DZEUS_KUSER=1"))

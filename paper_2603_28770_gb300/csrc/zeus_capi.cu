@@ -359,6 +359,22 @@ int zeus_uniform(uint64_t seed, uint64_t problem, uint64_t phase, int64_t n, int
     return cuda_status(launch_uniform(seed, problem, phase, n, dim, out, as_stream(stream)));
 }
 
+int zeus_cluster(const zeus_cluster_params* cp, int64_t n, int32_t dim, const double* x,
+                 const double* f, const int32_t* status, int32_t* label_out, int32_t* leader_out,
+                 int32_t* count_out, zeus_cluster_result* result, void* stream) {
+    if (!cp) return ZEUS_EINVAL;
+    if (cp->method != ZEUS_CLUSTER_BY_F && cp->method != ZEUS_CLUSTER_BY_X) return ZEUS_EINVAL;
+    if (cp->max_clusters < 1 || cp->max_clusters > ZEUS_CLUSTER_MAX) return ZEUS_EINVAL;
+    if (cp->only_converged != 0 && cp->only_converged != 1) return ZEUS_EINVAL;
+    if (cp->pad != 0 || !isfinite(cp->tol) || !(cp->tol >= 0.0)) return ZEUS_EINVAL;
+    if (n < 0 || n > 0x7fffffffll || dim < 1 || dim > 4096) return ZEUS_EINVAL;
+    if (n > 0 && (!f || !label_out)) return ZEUS_EINVAL;
+    if (n > 0 && cp->method == ZEUS_CLUSTER_BY_X && !x) return ZEUS_EINVAL;
+    if (n > 0 && cp->only_converged && !status) return ZEUS_EINVAL;
+    return cuda_status(launch_cluster(*cp, (int)n, dim, x, f, status, label_out, leader_out,
+                                      count_out, result, as_stream(stream)));
+}
+
 int32_t zeus_user_objective_count(void) { return user_objective_count(); }
 
 int zeus_user_objective_info(int32_t k, char* name, int32_t name_len, int32_t* min_dim,

@@ -43,7 +43,9 @@ def test_struct_layouts_match_header(z, tmp_path):
     import subprocess
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "zeus.h"', 'int main(void){']
     structs = (("zeus_problem", _capi.zeus_problem), ("zeus_result", _capi.zeus_result),
-               ("zeus_plan", _capi.zeus_plan), ("zeus_batch_plan", _capi.zeus_batch_plan))
+               ("zeus_plan", _capi.zeus_plan), ("zeus_batch_plan", _capi.zeus_batch_plan),
+               ("zeus_cluster_params", _capi.zeus_cluster_params),
+               ("zeus_cluster_result", _capi.zeus_cluster_result))
     for cname, cls in structs:
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for f, _ in cls._fields_:
@@ -287,3 +289,23 @@ def test_user_objectives_in_a_batch_plan(z):
     bad.n_user = len(probs) + 1
     assert L.zeus_batch_solve(C.byref(bad), C.c_void_p(4096), 1 << 40, C.c_void_p(256),
                               C.c_void_p(256), None, None, None, None, None) == z._capi.ZEUS_EINVAL
+
+
+def test_cluster_argument_errors(z):
+    L = z.lib()
+    EINVAL = z._capi.ZEUS_EINVAL
+    P = z._capi.zeus_cluster_params
+    ok = dict(method=1, max_clusters=8, only_converged=1, pad=0, tol=0.1)
+    fake = C.c_void_p(4096)
+
+    def call(n=10, dim=2, x=fake, f=fake, st=fake, lab=fake, **kw):
+        cp = P(**dict(ok, **kw))
+        return L.zeus_cluster(C.byref(cp), n, dim, x, f, st, lab, None, None, None, None)
+
+    for bad in (dict(method=2), dict(method=-1), dict(max_clusters=0), dict(max_clusters=4097),
+                dict(only_converged=2), dict(pad=1), dict(tol=-1.0), dict(tol=float("nan")),
+                dict(tol=float("inf")), dict(n=-1), dict(n=1 << 31), dict(dim=0), dict(f=None),
+                dict(lab=None), dict(x=None), dict(st=None)):
+        assert call(**bad) == EINVAL, bad
+    assert L.zeus_cluster(None, 10, 2, fake, fake, fake, fake, None, None, None, None) == EINVAL
+    assert C.sizeof(z._capi.zeus_cluster_result) == 64 and C.sizeof(P) == 24
