@@ -299,6 +299,31 @@ def run_zeus(a):
     e2e_value = iters_per_step * len(e2e_ms) / (sum(e2e_ms) / 1e3)
     d2h = n * d * 8 + n * 8 * 2 + n * 4 * 2 + 64
 
+    # solution clustering of the step's final points (Section VI proposes
+    # it), timed apart from the step: converged starts by coordinates,
+    # tol 1e-4, the first 256 regions
+    cluster = None
+    if rank == 0 and not a.lbfgs_m:
+        cp = z._capi.zeus_cluster_params(1, 256, 1, 0, 1e-4)
+        lab = torch.empty(n, dtype=torch.int32, device=dev)
+        lead = torch.empty(256, dtype=torch.int32, device=dev)
+        cnt = torch.empty(256, dtype=torch.int32, device=dev)
+        cres = torch.empty(64, dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            z.zeus_cluster(cp, n, d, x, f, st, lab, lead, cnt, cres, stream)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(5):
+            z.zeus_cluster(cp, n, d, x, f, st, lab, lead, cnt, cres, stream)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        cs = z._capi.zeus_cluster_result.from_buffer_copy(bytes(cres.cpu().numpy().tobytes()))
+        cluster = {"kernel": "cluster_kernel (one block of 1024 threads, one round per region)",
+                   "method": "x", "tol": 1e-4, "max_clusters": 256, "only_converged": True,
+                   "ms": round(c0.elapsed_time(c1) / 5, 4), "n_candidates": cs.n_candidates,
+                   "n_clusters": cs.n_clusters, "n_left": cs.n_left, "best_count": cs.best_count,
+                   "best_f": cs.best_f}
+
     # roofline of the dominant launch sequence, the BFGS phase, timed by the
     # events around zeus_solve_from on its stream
     plan = z.zeus_plan_info(pc)
@@ -377,6 +402,7 @@ def run_zeus(a):
                 "api": "zeus_solve_host (problem struct in, host outputs back, stream synchronized)"},
         "gpu_launches": a.steps * (p.pso_iters + 3),
         "roofline": roof,
+        "cluster": cluster,
         "best_f": summary["best_f"], "n_converged": summary["n_converged"],
         "wall_s_timed": round(t_wall, 3),
         "clocks": clk.summary(),
