@@ -309,16 +309,17 @@ def run_zeus(a):
         lead = torch.empty(256, dtype=torch.int32, device=dev)
         cnt = torch.empty(256, dtype=torch.int32, device=dev)
         cres = torch.empty(64, dtype=torch.uint8, device=dev)
+        cws = torch.empty(z.zeus_cluster_workspace_size(256), dtype=torch.uint8, device=dev)
         for _ in range(3):
-            z.zeus_cluster(cp, n, d, x, f, st, lab, lead, cnt, cres, stream)
+            z.zeus_cluster(cp, n, d, x, f, st, lab, lead, cnt, cres, cws, stream)
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record(stream)
         for _ in range(5):
-            z.zeus_cluster(cp, n, d, x, f, st, lab, lead, cnt, cres, stream)
+            z.zeus_cluster(cp, n, d, x, f, st, lab, lead, cnt, cres, cws, stream)
         c1.record(stream)
         torch.cuda.synchronize(dev)
         cs = z._capi.zeus_cluster_result.from_buffer_copy(bytes(cres.cpu().numpy().tobytes()))
-        cluster = {"kernel": "cluster_kernel (one block of 1024 threads, one round per region)",
+        cluster = {"kernel": "cluster_kernel (cooperative grid, one barrier per region)",
                    "method": "x", "tol": 1e-4, "max_clusters": 256, "only_converged": True,
                    "ms": round(c0.elapsed_time(c1) / 5, 4), "n_candidates": cs.n_candidates,
                    "n_clusters": cs.n_clusters, "n_left": cs.n_left, "best_count": cs.best_count,

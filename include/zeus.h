@@ -421,19 +421,27 @@ typedef struct {
     int32_t pad;
 } zeus_cluster_result;
 
+/* Device workspace of zeus_cluster for this max_clusters (host only). */
+int zeus_cluster_workspace_size(int32_t max_clusters, size_t *bytes);
+
 /* Clusters the n final points of one problem (zeus_solve outputs).
  *   x: device double [n][dim]; f: device double [n]; status: device int32
  *   [n] (may be NULL unless only_converged); label_out: device int32 [n]
  *   (cluster id, ZEUS_LABEL_NONE or ZEUS_LABEL_LEFT); leader_out, count_out:
  *   device int32 [max_clusters] (leader start index and member count of
  *   each cluster formed, -1 / 0 past n_clusters; may be NULL); result:
- *   device zeus_cluster_result (may be NULL).
- * One block on `stream`; n < 2^31.  ZEUS_EINVAL for bad parameters or
- * pointers, before any launch. */
+ *   device zeus_cluster_result (may be NULL); workspace: device,
+ *   zeus_cluster_workspace_size bytes, 256-byte aligned, not shared with a
+ *   call in flight.
+ * One memset and one cooperative launch on `stream` (graph-capturable);
+ * n < 2^31.  ZEUS_EINVAL for bad parameters or pointers and
+ * ZEUS_EWORKSPACE for a missing or small workspace, before any launch.  A
+ * grid barrier that does not complete within about two seconds ends the
+ * kernel with result->error = 1. */
 int zeus_cluster(const zeus_cluster_params *cp, int64_t n, int32_t dim, const double *x,
                  const double *f, const int32_t *status, int32_t *label_out,
                  int32_t *leader_out, int32_t *count_out, zeus_cluster_result *result,
-                 void *stream);
+                 void *workspace, size_t workspace_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,7 @@ __all__ = [
     "zeus_workspace_size", "zeus_plan_info", "zeus_validate", "zeus_default_problem", "zeus_strerror",
     "zeus_abi_version", "zeus_math_eval", "Context", "solve", "solve_from", "pso", "objective", "ObjectiveFn",
     "decode_result", "library_path", "lib", "zeus_batch_plan_make", "zeus_batch_prepare",
-    "zeus_batch_solve", "Batch", "user_objectives", "zeus_cluster", "cluster", "solve_until_confident",
+    "zeus_batch_solve", "Batch", "user_objectives", "zeus_cluster", "zeus_cluster_workspace_size", "cluster", "solve_until_confident",
 ]
 
 
@@ -491,14 +491,23 @@ class ObjectiveFn(torch.autograd.Function):
 
 # ------------------------------------------------ solution clustering
 
-def zeus_cluster(params, n, dim, x, f, status, label_out, leader_out=None, count_out=None,
-                 result=None, stream=None) -> None:
+def zeus_cluster_workspace_size(max_clusters: int) -> int:
+    b = C.c_size_t()
+    check(lib().zeus_cluster_workspace_size(int(max_clusters), C.byref(b)),
+          "zeus_cluster_workspace_size")
+    return b.value
+
+
+def zeus_cluster(params, n, dim, x, f, status, label_out, leader_out, count_out, result,
+                 workspace, stream=None) -> None:
     mc = params.max_clusters
     check(lib().zeus_cluster(
         C.byref(params), n, dim, _ptr(x, torch.float64, n * dim, "x"), _ptr(f, torch.float64, n, "f"),
         _ptr(status, torch.int32, n, "status"), _ptr(label_out, torch.int32, n, "label_out"),
         _ptr(leader_out, torch.int32, mc, "leader_out"), _ptr(count_out, torch.int32, mc, "count_out"),
-        _ptr(result, torch.uint8, C.sizeof(_capi.zeus_cluster_result), "result"), _stream(stream)),
+        _ptr(result, torch.uint8, C.sizeof(_capi.zeus_cluster_result), "result"),
+        _ptr(workspace, torch.uint8, None, "workspace"),
+        workspace.numel() if workspace is not None else 0, _stream(stream)),
         "zeus_cluster")
 
 
@@ -517,9 +526,10 @@ def cluster(x: torch.Tensor, f: torch.Tensor, status: torch.Tensor | None = None
            "leaders": torch.empty(max_clusters, dtype=torch.int32, device=dev),
            "counts": torch.empty(max_clusters, dtype=torch.int32, device=dev),
            "result": torch.empty(C.sizeof(_capi.zeus_cluster_result), dtype=torch.uint8, device=dev)}
+    ws = torch.empty(zeus_cluster_workspace_size(max_clusters), dtype=torch.uint8, device=dev)
     zeus_cluster(cp, n, dim, x.contiguous() if x is not None else None, f.contiguous(),
                  status.contiguous() if status is not None else None, out["labels"], out["leaders"],
-                 out["counts"], out["result"], stream)
+                 out["counts"], out["result"], ws, stream)
     raw = bytes(out["result"].cpu().numpy().tobytes())
     r = _capi.zeus_cluster_result.from_buffer_copy(raw)
     out["summary"] = {k: getattr(r, k) for k, _ in _capi.zeus_cluster_result._fields_}

@@ -125,8 +125,9 @@ SIGNATURES = {
     "zeus_uniform": (C.c_int, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int64, C.c_int32, _VP,
                                _VP]),
     "zeus_math_eval": (C.c_int, [C.c_int32, C.c_int64, _VP, _VP, _VP, _VP]),
+    "zeus_cluster_workspace_size": (C.c_int, [C.c_int32, C.POINTER(C.c_size_t)]),
     "zeus_cluster": (C.c_int, [C.POINTER(zeus_cluster_params), C.c_int64, C.c_int32, _VP, _VP, _VP,
-                               _VP, _VP, _VP, _VP, _VP]),
+                               _VP, _VP, _VP, _VP, _VP, C.c_size_t, _VP]),
     "zeus_user_objective_count": (C.c_int32, []),
     "zeus_user_objective_info": (C.c_int, [C.c_int32, C.c_char_p, C.c_int32,
                                            C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),

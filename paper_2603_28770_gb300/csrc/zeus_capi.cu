@@ -359,9 +359,16 @@ int zeus_uniform(uint64_t seed, uint64_t problem, uint64_t phase, int64_t n, int
     return cuda_status(launch_uniform(seed, problem, phase, n, dim, out, as_stream(stream)));
 }
 
+int zeus_cluster_workspace_size(int32_t max_clusters, size_t* bytes) {
+    if (!bytes || max_clusters < 1 || max_clusters > ZEUS_CLUSTER_MAX) return ZEUS_EINVAL;
+    *bytes = cluster_work_bytes(max_clusters);
+    return ZEUS_OK;
+}
+
 int zeus_cluster(const zeus_cluster_params* cp, int64_t n, int32_t dim, const double* x,
                  const double* f, const int32_t* status, int32_t* label_out, int32_t* leader_out,
-                 int32_t* count_out, zeus_cluster_result* result, void* stream) {
+                 int32_t* count_out, zeus_cluster_result* result, void* workspace,
+                 size_t workspace_bytes, void* stream) {
     if (!cp) return ZEUS_EINVAL;
     if (cp->method != ZEUS_CLUSTER_BY_F && cp->method != ZEUS_CLUSTER_BY_X) return ZEUS_EINVAL;
     if (cp->max_clusters < 1 || cp->max_clusters > ZEUS_CLUSTER_MAX) return ZEUS_EINVAL;
@@ -371,8 +378,11 @@ int zeus_cluster(const zeus_cluster_params* cp, int64_t n, int32_t dim, const do
     if (n > 0 && (!f || !label_out)) return ZEUS_EINVAL;
     if (n > 0 && cp->method == ZEUS_CLUSTER_BY_X && !x) return ZEUS_EINVAL;
     if (n > 0 && cp->only_converged && !status) return ZEUS_EINVAL;
+    if (!workspace || workspace_bytes < cluster_work_bytes(cp->max_clusters) ||
+        ((uintptr_t)workspace & 255u) != 0)
+        return ZEUS_EWORKSPACE;
     return cuda_status(launch_cluster(*cp, (int)n, dim, x, f, status, label_out, leader_out,
-                                      count_out, result, as_stream(stream)));
+                                      count_out, result, workspace, as_stream(stream)));
 }
 
 int32_t zeus_user_objective_count(void) { return user_objective_count(); }

@@ -298,14 +298,23 @@ def test_cluster_argument_errors(z):
     ok = dict(method=1, max_clusters=8, only_converged=1, pad=0, tol=0.1)
     fake = C.c_void_p(4096)
 
-    def call(n=10, dim=2, x=fake, f=fake, st=fake, lab=fake, **kw):
+    def call(n=10, dim=2, x=fake, f=fake, st=fake, lab=fake, ws=fake, wsb=1 << 30, **kw):
         cp = P(**dict(ok, **kw))
-        return L.zeus_cluster(C.byref(cp), n, dim, x, f, st, lab, None, None, None, None)
+        return L.zeus_cluster(C.byref(cp), n, dim, x, f, st, lab, None, None, None, ws, wsb, None)
 
     for bad in (dict(method=2), dict(method=-1), dict(max_clusters=0), dict(max_clusters=4097),
                 dict(only_converged=2), dict(pad=1), dict(tol=-1.0), dict(tol=float("nan")),
                 dict(tol=float("inf")), dict(n=-1), dict(n=1 << 31), dict(dim=0), dict(f=None),
                 dict(lab=None), dict(x=None), dict(st=None)):
         assert call(**bad) == EINVAL, bad
-    assert L.zeus_cluster(None, 10, 2, fake, fake, fake, fake, None, None, None, None) == EINVAL
+    assert L.zeus_cluster(None, 10, 2, fake, fake, fake, fake, None, None, None, fake, 1 << 30,
+                          None) == EINVAL
+    # the workspace: present, large enough for max_clusters, 256-byte aligned
+    need = z.zeus_cluster_workspace_size(8)
+    assert need % 256 == 0 and z.zeus_cluster_workspace_size(4096) > need
+    EWS = z._capi.ZEUS_EWORKSPACE
+    assert call(ws=None) == EWS and call(wsb=need - 1) == EWS
+    assert call(ws=C.c_void_p(4096 + 128), wsb=need) == EWS
+    with pytest.raises(z.ZeusError):
+        z.zeus_cluster_workspace_size(0)
     assert C.sizeof(z._capi.zeus_cluster_result) == 64 and C.sizeof(P) == 24
