@@ -137,6 +137,8 @@ def lib():
     L.zo_grad_forward.argtypes = [C.c_int, C.c_int, _D, _D, _D]
     L.zo_cluster.argtypes = [C.c_int, C.c_double, C.c_int32, C.c_int, C.c_int64, C.c_int, _D,
                              _D, _I32, _I32, _I32, _I32, C.POINTER(_ClusterResult)]
+    L.zo_dot_split.argtypes = [C.c_int, _D, _D]
+    L.zo_dot_split.restype = C.c_double
     L.zo_argmin.argtypes = [_D, C.c_int64]
     L.zo_argmin.restype = C.c_int64
     L.zo_pso.argtypes = [C.POINTER(_Problem), _D, _D, _D, _D, _D, _D, _I64]
@@ -364,3 +366,10 @@ def cluster(x, f, status=None, method="x", tol=1e-3, max_clusters=256, only_conv
                      cnt.ctypes.data_as(p32), C.byref(r))
     summary = {k: getattr(r, k) for k, _ in _ClusterResult._fields_}
     return dict(labels=lab[:n], leaders=lead, counts=cnt, summary=summary)
+
+
+def dot_split(a, b) -> float:
+    """The BFGS dot product as read in zeus_oracle.c (zo_bdot): one fma
+    chain for n <= 32, else 32 strided partial chains and a fixed tree."""
+    a, b = _f64(a), _f64(b)
+    return float(lib().zo_dot_split(a.size, _dp(a), _dp(b)))

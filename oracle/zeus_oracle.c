@@ -552,7 +552,31 @@ static double zo_dot(int n, const double *a, const double *b)
     return acc;
 }
 
-/* out = M v for row-major M [d][d] */
+/* The dot products of the BFGS step (||g||^2, g^T p, y^T s, s^T s, y^T y,
+ * y^T H y).  Reading: for n <= 32 as zo_dot; for n > 32, 32 partial sums,
+ * partial l over the indices j = l (mod 32) in increasing order, each term
+ * with one rounding (fma), then added pairwise in a fixed tree: partial l
+ * with partial l + 16 (l < 16), then l with l + 8 (l < 8), l + 4, l + 2,
+ * l + 1.  The paper fixes these sums only in exact terms; this order lets
+ * 32 lanes form one sum. */
+static double zo_bdot(int n, const double *a, const double *b)
+{
+    if (n <= 32) return zo_dot(n, a, b);
+    double p[32];
+    for (int l = 0; l < 32; ++l) {
+        double acc = 0.0;
+        for (int j = l; j < n; j += 32) acc = fma(a[j], b[j], acc);
+        p[l] = acc;
+    }
+    for (int w = 16; w >= 1; w >>= 1)
+        for (int l = 0; l < w; ++l) p[l] = p[l] + p[l + w];
+    return p[0];
+}
+
+/* zo_bdot for the tests */
+double zo_dot_split(int n, const double *a, const double *b) { return zo_bdot(n, a, b); }
+
+/* out = M v for row-major M [d][d] (rows as zo_dot) */
 static void zo_matvec(int d, const double *M, const double *v, double *out)
 {
     for (int r = 0; r < d; ++r) out[r] = zo_dot(d, M + (size_t)r * d, v);
@@ -573,13 +597,13 @@ static void zo_matvec(int d, const double *M, const double *v, double *out)
 
 int zo_bfgs_update(int d, double *H, const double *s, const double *y)
 {
-    const double sy = zo_dot(d, y, s), ss = zo_dot(d, s, s), yy = zo_dot(d, y, y);
+    const double sy = zo_bdot(d, y, s), ss = zo_bdot(d, s, s), yy = zo_bdot(d, y, y);
     if (!(sy > 1e-12 * sqrt(ss) * sqrt(yy))) return 0;
     double rho = 1.0 / sy;
     double *Hy = (double *)malloc(sizeof(double) * (size_t)d * 3);
     double *A = Hy + d, *B = Hy + 2 * d;
     zo_matvec(d, H, y, Hy);
-    const double yHy = zo_dot(d, y, Hy);
+    const double yHy = zo_bdot(d, y, Hy);
     const double beta = rho * rho * yHy + rho;
     for (int r = 0; r < d; ++r) {
         A[r] = fma(beta, s[r], -(rho * Hy[r]));
@@ -692,7 +716,7 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
     int k = 0, status = 0, n_feval = 0;
     double gnorm = NAN;
     for (;;) {
-        gnorm = sqrt(zo_dot(d, g, g));
+        gnorm = sqrt(zo_bdot(d, g, g));
         if (k >= pr->bfgs_max_iters) { status = 0; break; }
         if (stop && *stop) { status = 2; break; }
         if (!isfinite(f0) || !finite_vec(d, g)) { status = 3; break; }
@@ -720,7 +744,7 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
             zo_matvec(d, H, g, p);
             for (int r = 0; r < d; ++r) p[r] = -p[r];
         }
-        double ddir = zo_dot(d, g, p);
+        double ddir = zo_bdot(d, g, p);
         if (!(ddir < 0.0)) {
             /* Reading: non-descent direction -> restart from H = I (L-BFGS:
              * forget the stored pairs) */
@@ -730,7 +754,7 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
             }
             n_pairs = 0;
             for (int r = 0; r < d; ++r) p[r] = -g[r];
-            ddir = zo_dot(d, g, p);
+            ddir = zo_bdot(d, g, p);
         }
         int accepted = 0;
         double alpha = zo_line_search(obj, d, x, p, f0, ddir, pr->armijo_c,

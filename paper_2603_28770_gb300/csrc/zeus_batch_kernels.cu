@@ -109,8 +109,9 @@ __device__ __forceinline__ RunIO batch_io(const BatchDev& bd, const zeus_problem
 // over the hand-over queue (cls < 0).  Item (P, s, c, 0): a tile of c
 // starts s.. of problem P, one lane each; item (P, s, W, 1): start s on the
 // whole block with W line-search trials at once.
+// at least six blocks per SM: the lane-tile classes keep their residency
 template <int GRAD, class T, bool U>
-__global__ void __launch_bounds__(kWideThreads)
+__global__ void __launch_bounds__(kWideThreads, 6)
     batch_bfgs_kernel(const BatchDev bd, const int cls, const int first, const int count,
                       double* x_out, double* __restrict__ f_out, double* __restrict__ gnorm_out,
                       int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out) {

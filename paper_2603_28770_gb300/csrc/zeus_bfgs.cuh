@@ -44,6 +44,62 @@ __device__ __forceinline__ double dot_fma(float a, float b, double acc) {
 __device__ __forceinline__ double mv_fma(double a, double b, double acc) { return fma(a, b, acc); }
 __device__ __forceinline__ float mv_fma(float a, float b, float acc) { return fmaf(a, b, acc); }
 
+// The dot products of the BFGS step (||g||^2, g'p, y's, s's, y'y, y'Hy):
+// up to kDotSplit terms one chain in index order; past that 32 strided
+// chains (chain l over the indices l, l + 32, ...) added in a fixed tree,
+// l with l + 16, then l + 8, l + 4, l + 2, l + 1, so that one warp forms
+// the sum (a one-lane chain of d FP64 instructions holds its sub-partition's
+// FP64 pipe as long as d full-warp instructions would).
+constexpr int kDotSplit = 32;
+
+// the split order by one warp (lane = role mod 32); every lane gets the sum
+template <class T>
+__device__ __forceinline__ double warp_split_dot(const T* a, const T* b, int n, int lane) {
+    double acc = 0.0;
+#pragma unroll 1
+    for (int j = lane; j < n; j += 32) acc = dot_fma(a[j], b[j], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_down_sync(0xffffffffu, acc, o);
+    return __shfl_sync(0xffffffffu, acc, 0);
+}
+
+// the split order on one thread (the lane kernel meets d > kDotSplit only
+// when one lane per start is asked for).  The tree's leaves, left to right,
+// are the chains in bit-reversed order (0, 16, 8, 24, 4, ...); they are
+// formed one at a time and merged as a binary counter does, so that no
+// more than five partial sums are held.
+template <class T>
+__device__ __forceinline__ double lane_split_dot(const T* a, const T* b, int n) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, v = 0.0;
+#pragma unroll 1
+    for (int k = 0; k < 32; ++k) {
+        const int l = (int)(__brev((unsigned)k) >> 27);
+        v = 0.0;
+#pragma unroll 1
+        for (int j = l; j < n; j += 32) v = dot_fma(a[j], b[j], v);
+        if (!(k & 1)) { s0 = v; continue; }
+        v = s0 + v;
+        if (!(k & 2)) { s1 = v; continue; }
+        v = s1 + v;
+        if (!(k & 4)) { s2 = v; continue; }
+        v = s2 + v;
+        if (!(k & 8)) { s3 = v; continue; }
+        v = s3 + v;
+        if (!(k & 16)) { s4 = v; continue; }
+        v = s4 + v;
+    }
+    return v;
+}
+
+// one thread's BFGS dot product in the order above
+template <class T>
+__device__ __forceinline__ double lane_dot(const T* a, const T* b, int n) {
+    if (n > kDotSplit) return lane_split_dot(a, b, n);
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc = dot_fma(a[j], b[j], acc);
+    return acc;
+}
+
 // The FP32 form evaluates Rastrigin as sum (x^2 + 20 sin^2(pi x)) and the
 // cosine mean of Ackley through 1 - (2/d) sum sin^2(pi x): the same
 // functions in exact arithmetic, without the cancellation that the literal
@@ -240,6 +296,7 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
             gg = dot_fma(g[j], g[j], gg);
             bad |= !isfinite(g[j]);
         }
+        if (d > kDotSplit) gg = lane_split_dot(g, g, d);
         gnorm = sqrt(gg);
         if (k >= K) {
             status = ZEUS_RUN_MAX_ITER;
@@ -310,14 +367,12 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
             for (int c = 0; c < d; ++c) a = mv_fma(Hr[c], g[c], a);
             pv[r] = -a;
         }
-        double ddir = 0.0;
-        for (int r = 0; r < d; ++r) ddir = dot_fma(g[r], pv[r], ddir);
+        double ddir = lane_dot(g, pv, d);
         if (!(ddir < 0.0)) {  // not a descent direction: restart from H = I
             for (int r = 0; r < d; ++r)
                 for (int c = 0; c < d; ++c) H[r * d + c] = (c == r) ? T(1) : T(0);
             for (int r = 0; r < d; ++r) pv[r] = -g[r];
-            ddir = 0.0;
-            for (int r = 0; r < d; ++r) ddir = dot_fma(g[r], pv[r], ddir);
+            ddir = lane_dot(g, pv, d);
         }
         // backtracking Armijo line search (Alg. 6)
         double alpha = 1.0, fn = 0.0;
@@ -352,6 +407,11 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
             ss = dot_fma(sj, sj, ss);
             yy = dot_fma(yj, yj, yy);
         }
+        if (d > kDotSplit) {
+            sy = lane_split_dot(g, sv, d);
+            ss = lane_split_dot(sv, sv, d);
+            yy = lane_split_dot(g, g, d);
+        }
         const bool upd = sy > 1e-12 * sqrt(ss) * sqrt(yy);
         T rt = T(0), bt = T(0);
         if (upd) {
@@ -362,8 +422,7 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
                 for (int c = 0; c < d; ++c) a = mv_fma(Hr[c], g[c], a);
                 pv[r] = a;
             }
-            double yhy = 0.0;
-            for (int r = 0; r < d; ++r) yhy = dot_fma(g[r], pv[r], yhy);
+            const double yhy = lane_dot(g, pv, d);
             const double b2 = rho * rho * yhy + rho;
             rt = T(rho);
             bt = T(b2);
@@ -517,8 +576,13 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         // g'g and g'p on roles 0 and 1 (one warp, one instruction stream:
         // an FP64 warp instruction costs the same for one lane or two)
         double dot01 = 0.0;
-        if (tid < 2) dot01 = ordered_dot(g, tid == 0 ? g : pv, d);
-        if (tid == 1) sh.red[0] = dot01;
+        if (d > kDotSplit) {  // g'g on the warp of roles 0-31, g'p on the next
+            if (tid < 64) dot01 = warp_split_dot(g, tid < 32 ? g : pv, d, tid & 31);
+            if (tid == 32) sh.red[0] = dot01;
+        } else {
+            if (tid < 2) dot01 = ordered_dot(g, tid == 0 ? g : pv, d);
+            if (tid == 1) sh.red[0] = dot01;
+        }
         if (tid == 0) {
             gnorm = sqrt(dot01);
             sh.red[1] = gnorm;
@@ -556,7 +620,14 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             for (int e = tid; e < d * d; e += NT) H[e] = (e / d == e % d) ? T(1) : T(0);
             for (int r = tid; r < d; r += NT) pv[r] = -g[r];
             __syncthreads();
-            if (tid == 0) sh.red[0] = ordered_dot(g, pv, d);
+            if (d > kDotSplit) {
+                if (tid < 32) {
+                    const double v = warp_split_dot(g, pv, d, tid);
+                    if (tid == 0) sh.red[0] = v;
+                }
+            } else if (tid == 0) {
+                sh.red[0] = ordered_dot(g, pv, d);
+            }
             __syncthreads();
             ddir = sh.red[0];
         }
@@ -614,8 +685,15 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             g[j] = gn[j] - g[j];
         }
         __syncthreads();
-        if (tid < 3)  // y's, s's, y'y on roles 0-2 (one warp, one instruction stream)
+        if (d > kDotSplit) {  // y's, s's, y'y on the warps of roles 0-95
+            if (tid < 96) {
+                const int w = tid >> 5;
+                const double v = warp_split_dot(w == 1 ? sv : g, w == 2 ? g : sv, d, tid & 31);
+                if ((tid & 31) == 0) sh.red[w] = v;
+            }
+        } else if (tid < 3) {  // on roles 0-2 (one warp, one instruction stream)
             sh.red[tid] = ordered_dot(tid == 1 ? sv : g, tid == 2 ? g : sv, d);
+        }
         for (int r = row_of(tid, NT); r < d; r += NT) {  // Hy into p (the direction is spent)
             const T* Hr = H + r * d;
             T a = T(0);
@@ -626,7 +704,14 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         const double sy = sh.red[0], ss = sh.red[1], yy = sh.red[2];
         if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
             const double rho = 1.0 / sy;
-            if (tid == 0) sh.red[3] = ordered_dot(g, pv, d);
+            if (d > kDotSplit) {
+                if (tid < 32) {
+                    const double v = warp_split_dot(g, pv, d, tid);
+                    if (tid == 0) sh.red[3] = v;
+                }
+            } else if (tid == 0) {
+                sh.red[3] = ordered_dot(g, pv, d);
+            }
             __syncthreads();
             const double b2 = rho * rho * sh.red[3] + rho;
             const T rt = T(rho), bt = T(b2);
