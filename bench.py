@@ -804,9 +804,16 @@ def run_reference(a):
         }), flush=True)
         return
     fields = workloads.workload(a.workload)
-    n_sample = 256
+    # BFGS from as many of the swarm's particles as fit about 2 s per step
+    # (all of them for the 10-D workloads), so that the full PSO phase does
+    # not weigh on a small BFGS sample
+    n_sample = 64
+    _, dt = _oracle_sample(fields, n_sample, threads)
+    while dt < 0.5 and n_sample < fields["n_starts"]:
+        n_sample = min(fields["n_starts"], n_sample * 4)
+        _, dt = _oracle_sample(fields, n_sample, threads)
     for _ in range(a.warmup):
-        _oracle_sample(fields, 16, threads)
+        _oracle_sample(fields, n_sample, threads)
     times, iters = [], []
     for _ in range(a.steps):
         it, dt = _oracle_sample(fields, n_sample, threads)
