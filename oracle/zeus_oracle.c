@@ -609,9 +609,14 @@ int zo_bfgs_update(int d, double *H, const double *s, const double *y)
         A[r] = fma(beta, s[r], -(rho * Hy[r]));
         B[r] = -(rho * s[r]);
     }
+    /* Reading: H is symmetric in exact arithmetic; the elements r <= c are
+     * formed and mirrored, so H stays exactly symmetric */
     for (int r = 0; r < d; ++r)
-        for (int c = 0; c < d; ++c)
-            H[r * d + c] = fma(s[c], A[r], fma(Hy[c], B[r], H[r * d + c]));
+        for (int c = r; c < d; ++c) {
+            const double v = fma(s[c], A[r], fma(Hy[c], B[r], H[r * d + c]));
+            H[r * d + c] = v;
+            H[c * d + r] = v;
+        }
     free(Hy);
     return 1;
 }

@@ -438,10 +438,14 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
                 xn[r] = mv_fma(bt, sv[r], -(rt * pv[r]));
                 gn[r] = -(rt * sv[r]);
             }
-            for (int r = 0; r < d; ++r) {
+            for (int r = 0; r < d; ++r) {  // r <= c, mirrored (H stays symmetric)
                 const T ar = xn[r], br = gn[r];
                 T* Hr = H + r * d;
-                for (int c = 0; c < d; ++c) Hr[c] = mv_fma(sv[c], ar, mv_fma(pv[c], br, Hr[c]));
+                for (int c = r; c < d; ++c) {
+                    const T v = mv_fma(sv[c], ar, mv_fma(pv[c], br, Hr[c]));
+                    Hr[c] = v;
+                    H[c * d + r] = v;
+                }
             }
         }
         f0 = fn;
@@ -721,9 +725,23 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 sc1[r] = (double)(-(rt * sv[r]));
             }
             __syncthreads();
-            for (int e = tid; e < d * d; e += NT) {
-                const int r = e / d, c = e - r * d;
-                H[e] = mv_fma(sv[c], T(sc0[r]), mv_fma(pv[c], T(sc1[r]), H[e]));
+            // the elements r <= c, mirrored (H stays symmetric): rows r and
+            // d - 1 - r together hold d + 1 of them, so t = p (d + 1) + q
+            // numbers them without gaps
+            const int nu = d * (d + 1) / 2;
+            for (int t = tid; t < nu; t += NT) {
+                const int pr = t / (d + 1), q = t - pr * (d + 1);
+                int r, c;
+                if (q < d - pr) {
+                    r = pr;
+                    c = pr + q;
+                } else {
+                    r = d - 1 - pr;
+                    c = r + (q - (d - pr));
+                }
+                const T v = mv_fma(sv[c], T(sc0[r]), mv_fma(pv[c], T(sc1[r]), H[r * d + c]));
+                H[r * d + c] = v;
+                H[c * d + r] = v;
             }
         }
         // x, g <- x_new, g_new in the same phase (the update reads neither;

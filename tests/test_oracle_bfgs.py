@@ -50,7 +50,7 @@ def _spd(rng, d):
 
 def test_update_secant_symmetry_and_product_form(oracle_mod):
     rng = np.random.default_rng(3)
-    for d in (1, 2, 5, 8):
+    for d in (1, 2, 5, 8, 40):
         for _ in range(10):
             H = np.linalg.inv(_spd(rng, d))
             s = rng.normal(size=d)
@@ -59,7 +59,7 @@ def test_update_secant_symmetry_and_product_form(oracle_mod):
             assert ok
             # secant condition H+ y = s
             assert np.abs(Hn @ y - s).max() <= 1e-10 * max(1.0, np.abs(s).max())
-            assert np.allclose(Hn, Hn.T, rtol=0, atol=1e-12 * np.abs(Hn).max())
+            assert np.array_equal(Hn, Hn.T)  # the upper triangle, mirrored
             assert np.linalg.eigvalsh((Hn + Hn.T) / 2).min() > 0
             # the product form printed in Alg. 4
             rho = 1.0 / (y @ s)
