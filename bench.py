@@ -156,11 +156,12 @@ def fp64_flops(d: int, iters: int, fevals: int, objective="rastrigin") -> float:
                            ||g|| 2d + 1, p = -H g 2d^2 + d, g'p 2d, x_new 2d,
                            s, y, y's, |s|^2, |y|^2 8d, curvature test 5,
                            H y 2d^2, y'Hy 2d, rho and its factor 4,
-                           rank-two update 8 per element of the symmetric H
-                           -> 8 d^2 + 21 d + 10 + gradient
+                           rank-two update: two FMAs (4) per element of
+                           the upper triangle of the symmetric H, d(d+1)/2
+                           -> 6 d^2 + 23 d + 10 + gradient
       per line-search evaluation  the value sweep + Armijo test 3"""
     grad, val = objective_flops(objective, d)
-    return iters * (8.0 * d * d + 21.0 * d + 10.0 + grad) + fevals * (val + 3.0)
+    return iters * (6.0 * d * d + 23.0 * d + 10.0 + grad) + fevals * (val + 3.0)
 
 
 def _peaks():
