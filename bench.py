@@ -707,6 +707,25 @@ def run_batch_main(a, z, dev, world, rank, local):
         "roofline": roof,
         "clocks": clk.summary(),
     }
+    if rank == 0:
+        # every problem's final points clustered in one launch (converged
+        # starts by coordinates, tol 1e-4, the first 64 regions of each)
+        b.cluster(method="x", tol=1e-4, max_clusters=64)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream(dev)
+        c0.record(stream)
+        cl = None
+        for _ in range(3):
+            cl = b.cluster(method="x", tol=1e-4, max_clusters=64)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        sums = cl["summaries"]
+        out["cluster"] = {"kernel": "batch_cluster_kernel (one block per problem)", "method": "x",
+                          "tol": 1e-4, "max_clusters": 64, "only_converged": True,
+                          "ms": round(c0.elapsed_time(c1) / 3, 3),
+                          "note": "ms includes copying the summaries back",
+                          "regions_total": int(sum(s["n_clusters"] for s in sums)),
+                          "problems_with_best_count_ge_2": int(sum(s["best_count"] >= 2 for s in sums))}
     if rank == 0 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_batch(a.precision, budget_s=12.0)
     if rank == 0:

@@ -443,6 +443,21 @@ int zeus_cluster(const zeus_cluster_params *cp, int64_t n, int32_t dim, const do
                  int32_t *leader_out, int32_t *count_out, zeus_cluster_result *result,
                  void *workspace, size_t workspace_bytes, void *stream);
 
+/* Clusters the final points of every problem of a batch, each on its own
+ * (the definition of zeus_cluster), one block per problem; needs no memory
+ * beyond the batch's workspace.  plan, workspace: those of the
+ * zeus_batch_solve that wrote x_out, f_out and status_out (status_out may
+ * be NULL unless only_converged).  label_out: device int32 [total_starts],
+ * in the order of f_out; leader_out, count_out: device int32
+ * [n_problems][max_clusters] (may be NULL; leaders are start indices within
+ * their problem); results: device zeus_cluster_result [n_problems] (may be
+ * NULL).  ZEUS_EINVAL / ZEUS_EWORKSPACE before any launch. */
+int zeus_batch_cluster(const zeus_batch_plan *plan, const void *workspace,
+                       size_t workspace_bytes, const zeus_cluster_params *cp,
+                       const double *x_out, const double *f_out, const int32_t *status_out,
+                       int32_t *label_out, int32_t *leader_out, int32_t *count_out,
+                       zeus_cluster_result *results, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

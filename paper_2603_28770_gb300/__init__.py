@@ -403,6 +403,34 @@ class Batch:
                     gnorm=self.gnorm[so:so + n], status=self.status[so:so + n],
                     iters=self.iters[so:so + n], summary=decode_result(raw))
 
+    def cluster(self, method="x", tol: float = 1e-3, max_clusters: int = 64,
+                only_converged: bool = True, stream=None) -> dict:
+        """Clusters every problem's final points on its own (one launch;
+        the definition of ``cluster``): labels [total_starts] in the order
+        of ``f``, leaders and counts [n_problems, max_clusters] (leaders are
+        start indices within their problem), and one summary per problem."""
+        pl, dev = self.plan, self.f.device
+        cp = _capi.zeus_cluster_params(_capi.CLUSTER_METHODS[method] if isinstance(method, str)
+                                       else int(method), int(max_clusters),
+                                       int(bool(only_converged)), 0, float(tol))
+        n = pl.n_problems
+        lab = torch.empty(pl.total_starts, dtype=torch.int32, device=dev)
+        lead = torch.empty(n, max_clusters, dtype=torch.int32, device=dev)
+        cnt = torch.empty(n, max_clusters, dtype=torch.int32, device=dev)
+        rb = C.sizeof(_capi.zeus_cluster_result)
+        res = torch.empty(n * rb, dtype=torch.uint8, device=dev)
+        check(lib().zeus_batch_cluster(
+            C.byref(pl), _ptr(self.workspace, torch.uint8), self.workspace.numel(), C.byref(cp),
+            _ptr(self.x, torch.float64), _ptr(self.f, torch.float64),
+            _ptr(self.status, torch.int32), _ptr(lab, torch.int32), _ptr(lead, torch.int32),
+            _ptr(cnt, torch.int32), _ptr(res, torch.uint8), _stream(stream)), "zeus_batch_cluster")
+        raw = res.cpu().numpy().tobytes()
+        sums = []
+        for P in range(n):
+            r = _capi.zeus_cluster_result.from_buffer_copy(raw[P * rb:(P + 1) * rb])
+            sums.append({k: getattr(r, k) for k, _ in _capi.zeus_cluster_result._fields_})
+        return {"labels": lab, "leaders": lead, "counts": cnt, "summaries": sums}
+
     def summaries(self) -> list[dict]:
         raw = self.results.cpu().numpy().tobytes()
         out = []

@@ -128,6 +128,9 @@ SIGNATURES = {
     "zeus_cluster_workspace_size": (C.c_int, [C.c_int32, C.POINTER(C.c_size_t)]),
     "zeus_cluster": (C.c_int, [C.POINTER(zeus_cluster_params), C.c_int64, C.c_int32, _VP, _VP, _VP,
                                _VP, _VP, _VP, _VP, _VP, C.c_size_t, _VP]),
+    "zeus_batch_cluster": (C.c_int, [C.POINTER(zeus_batch_plan), _VP, C.c_size_t,
+                                     C.POINTER(zeus_cluster_params), _VP, _VP, _VP, _VP, _VP, _VP,
+                                     _VP, _VP]),
     "zeus_user_objective_count": (C.c_int32, []),
     "zeus_user_objective_info": (C.c_int, [C.c_int32, C.c_char_p, C.c_int32,
                                            C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),

@@ -14,6 +14,7 @@
 // zeus_bfgs.cu); larger problems run one block per start.  Every start runs
 // the same bodies as in a single-problem solve, so each problem's result
 // equals its zeus_solve result bit for bit.
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -404,6 +405,28 @@ int zeus_batch_solve(const zeus_batch_plan* plan, void* workspace, size_t worksp
                               (size_t)plan->handover_smem, x_out, f_out, gnorm_out, status_out,
                               iters_out, st);
     if (e == cudaSuccess) e = launch_batch_argmin(bd, f_out, results, st);
+    return e == cudaSuccess ? ZEUS_OK : ZEUS_ECUDA;
+}
+
+int zeus_batch_cluster(const zeus_batch_plan* plan, const void* workspace, size_t workspace_bytes,
+                       const zeus_cluster_params* cp, const double* x_out, const double* f_out,
+                       const int32_t* status_out, int32_t* label_out, int32_t* leader_out,
+                       int32_t* count_out, zeus_cluster_result* results, void* stream) {
+    if (!plan || !cp || !plan_sane(*plan)) return ZEUS_EINVAL;
+    if (cp->method != ZEUS_CLUSTER_BY_F && cp->method != ZEUS_CLUSTER_BY_X) return ZEUS_EINVAL;
+    if (cp->max_clusters < 1 || cp->max_clusters > ZEUS_CLUSTER_MAX) return ZEUS_EINVAL;
+    if (cp->only_converged != 0 && cp->only_converged != 1) return ZEUS_EINVAL;
+    if (cp->pad != 0 || !isfinite(cp->tol) || !(cp->tol >= 0.0)) return ZEUS_EINVAL;
+    if (!f_out || !label_out || (cp->method == ZEUS_CLUSTER_BY_X && !x_out)) return ZEUS_EINVAL;
+    if (cp->only_converged && !status_out) return ZEUS_EINVAL;
+    const Sizes z = plan_sizes(*plan);
+    const BatchLayout l = batch_layout(z);
+    const int v = check_ws(const_cast<void*>(workspace), workspace_bytes, l.total);
+    if (v != ZEUS_OK) return v;
+    const BatchDev bd = batch_dev(const_cast<void*>(workspace), l, z);
+    const cudaError_t e = launch_batch_cluster(*cp, bd, x_out, f_out, status_out, label_out,
+                                               leader_out, count_out, results,
+                                               reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? ZEUS_OK : ZEUS_ECUDA;
 }
 

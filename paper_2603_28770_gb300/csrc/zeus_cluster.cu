@@ -299,6 +299,149 @@ __global__ void __launch_bounds__(kClusterThreads)
     }
 }
 
+// Every problem of a batch: block P (grid-stride over the problems) runs
+// the rounds of problem P's starts with block barriers only; start i of the
+// problem belongs to thread i mod blockDim for the whole problem.
+constexpr int kBatchClusterThreads = 256;
+
+__global__ void __launch_bounds__(kBatchClusterThreads)
+    batch_cluster_kernel(const zeus_cluster_params cp, const BatchDev bd,
+                         const double* __restrict__ x_all, const double* __restrict__ f_all,
+                         const int32_t* __restrict__ st_all, int32_t* __restrict__ lab_all,
+                         int32_t* __restrict__ leader_all, int32_t* __restrict__ count_all,
+                         zeus_cluster_result* __restrict__ res_all) {
+    __shared__ ClusterShared sh;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const bool by_x = cp.method == ZEUS_CLUSTER_BY_X;
+    const double tol = cp.tol, tol2 = cp.tol * cp.tol;
+    const int mc = cp.max_clusters;
+    for (int P = blockIdx.x; P < bd.n; P += gridDim.x) {
+        const zeus_problem& pr = bd.probs[P];
+        const int n = (int)pr.n_starts, d = pr.dim;
+        const double* x = x_all + bd.xoff[P];
+        const double* f = f_all + bd.soff[P];
+        const int32_t* status = st_all ? st_all + bd.soff[P] : nullptr;
+        int32_t* label = lab_all + bd.soff[P];
+        int32_t* leader = leader_all ? leader_all + (size_t)P * mc : nullptr;
+        int32_t* count = count_all ? count_all + (size_t)P * mc : nullptr;
+
+        long long nc = 0;
+        for (int i = tid; i < n; i += NT) {
+            const bool c =
+                isfinite(f[i]) && (!cp.only_converged || status[i] == ZEUS_RUN_CONVERGED);
+            label[i] = c ? kOpen : ZEUS_LABEL_NONE;
+            nc += c ? 1 : 0;
+        }
+        double unused = 0.0;
+        block_count_max(nc, unused, sh);
+        int K = 0, L0 = -1;
+        long long c0 = 0;
+        double spread0 = 0.0;
+        for (int k = 0; k < mc; ++k) {
+            double bf = INFINITY;
+            int bi = -1;
+            for (int i = tid; i < n; i += NT) {
+                if (label[i] != kOpen) continue;
+                const double fi = f[i];
+                if (bi < 0 || fi < bf) {  // i grows: ties keep the lower index
+                    bf = fi;
+                    bi = i;
+                }
+            }
+            block_argmin(bf, bi, sh);
+            const int L = bi;
+            if (L < 0) break;
+            const double fL = f[L];
+            const double* xL = by_x ? x + (size_t)L * d : nullptr;
+            long long cnt = 0;
+            double sp = 0.0;
+            for (int i = tid; i < n; i += NT) {
+                if (label[i] != kOpen) continue;
+                double dist;
+                bool in;
+                if (by_x) {  // partial sums only grow: past tol^2 settles the test
+                    const double* xi = x + (size_t)i * d;
+                    double acc = 0.0;
+                    in = true;
+                    for (int j = 0; j < d; ++j) {
+                        const double del = xi[j] - xL[j];
+                        acc = fma(del, del, acc);
+                        if (acc > tol2) {
+                            in = false;
+                            break;
+                        }
+                    }
+                    dist = in ? sqrt(acc) : 0.0;
+                } else {
+                    dist = fabs(f[i] - fL);
+                    in = dist <= tol * fmax(1.0, fabs(fL));
+                }
+                if (in) {
+                    label[i] = k;
+                    ++cnt;
+                    sp = fmax(sp, dist);
+                }
+            }
+            block_count_max(cnt, sp, sh);
+            if (tid == 0) {
+                if (leader) leader[k] = L;
+                if (count) count[k] = (int)cnt;
+            }
+            if (k == 0) {
+                L0 = L;
+                c0 = cnt;
+                spread0 = sp;
+            }
+            K = k + 1;
+        }
+        long long left = 0;
+        for (int i = tid; i < n; i += NT) {
+            if (label[i] == kOpen) {
+                label[i] = ZEUS_LABEL_LEFT;
+                ++left;
+            }
+        }
+        block_count_max(left, unused, sh);
+        for (int k = K + tid; k < mc; k += NT) {
+            if (leader) leader[k] = -1;
+            if (count) count[k] = 0;
+        }
+        if (tid == 0 && res_all) {
+            zeus_cluster_result r;
+            r.n_candidates = nc;
+            r.n_clusters = K;
+            r.n_left = left;
+            r.best_count = K > 0 ? c0 : 0;
+            r.best_leader = K > 0 ? L0 : -1;
+            r.best_f = K > 0 ? f[L0] : CUDART_NAN;
+            r.best_spread = K > 0 ? spread0 : CUDART_NAN;
+            r.error = 0;
+            r.pad = 0;
+            res_all[P] = r;
+        }
+        __syncthreads();  // the next problem reuses the shared scratch
+    }
+}
+
+cudaError_t launch_batch_cluster(const zeus_cluster_params& cp, const BatchDev& bd,
+                                 const double* x, const double* f, const int32_t* status,
+                                 int32_t* label, int32_t* leader_out, int32_t* count_out,
+                                 zeus_cluster_result* res, cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_cluster_kernel,
+                                                          kBatchClusterThreads, 0);
+    if (e != cudaSuccess) return e;
+    long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (blocks > bd.n) blocks = bd.n;
+    if (blocks < 1) return cudaSuccess;
+    batch_cluster_kernel<<<(unsigned)blocks, kBatchClusterThreads, 0, st>>>(
+        cp, bd, x, f, status, label, leader_out, count_out, res);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cluster(const zeus_cluster_params& cp, int n, int d, const double* x,
                            const double* f, const int32_t* status, int32_t* label,
                            int32_t* leader_out, int32_t* count_out, zeus_cluster_result* res,

@@ -188,6 +188,10 @@ cudaError_t launch_cluster(const zeus_cluster_params& cp, int n, int d, const do
                            int32_t* leader_out, int32_t* count_out, zeus_cluster_result* res,
                            void* workspace, cudaStream_t st);
 size_t cluster_work_bytes(int max_clusters);
+cudaError_t launch_batch_cluster(const zeus_cluster_params& cp, const BatchDev& bd,
+                                 const double* x, const double* f, const int32_t* status,
+                                 int32_t* label, int32_t* leader_out, int32_t* count_out,
+                                 zeus_cluster_result* res, cudaStream_t st);
 
 // plug-in metadata of user objective k (zeus_user.cuh): 0 if k is not one
 int user_objective_meta(int k, const char** name, int* min_dim, int* max_dim);

@@ -318,3 +318,26 @@ def test_cluster_argument_errors(z):
     with pytest.raises(z.ZeusError):
         z.zeus_cluster_workspace_size(0)
     assert C.sizeof(z._capi.zeus_cluster_result) == 64 and C.sizeof(P) == 24
+
+
+def test_batch_cluster_argument_errors(z):
+    L = z.lib()
+    EINVAL, EWS = z._capi.ZEUS_EINVAL, z._capi.ZEUS_EWORKSPACE
+    pl = z.zeus_batch_plan_make(_mixed(z, 4))
+    P = z._capi.zeus_cluster_params
+    fake = C.c_void_p(4096)
+
+    def call(cp=P(1, 8, 1, 0, 0.1), plan=pl, ws=fake, wsb=1 << 40, x=fake, f=fake, st=fake,
+             lab=fake):
+        return L.zeus_batch_cluster(C.byref(plan) if plan is not None else None, ws, wsb,
+                                    C.byref(cp) if cp is not None else None, x, f, st, lab,
+                                    None, None, None, None)
+
+    for bad in (dict(cp=None), dict(plan=None), dict(cp=P(2, 8, 1, 0, 0.1)),
+                dict(cp=P(1, 0, 1, 0, 0.1)), dict(cp=P(1, 8, 1, 0, -1.0)), dict(f=None),
+                dict(lab=None), dict(x=None), dict(st=None)):
+        assert call(**bad) == EINVAL, bad
+    bad_plan = z._capi.zeus_batch_plan.from_buffer_copy(bytes(pl))
+    bad_plan.n_classes = 0
+    assert call(plan=bad_plan) == EINVAL
+    assert call(ws=None) == EWS and call(wsb=pl.workspace_bytes - 256) == EWS

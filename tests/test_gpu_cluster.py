@@ -117,3 +117,33 @@ def test_solve_until_confident(z, ora):
         orr = ora.cluster(x[:r * n], f[:r * n], st[:r * n], method="x", tol=1e-4, max_clusters=1,
                           only_converged=True)
         assert orr["summary"]["best_count"] < 3
+
+
+@pytest.mark.parametrize("method,tol,mc,only", [("x", 1e-4, 64, True), ("f", 1e-6, 16, False),
+                                                ("x", 0.5, 3, False)])
+def test_batch_cluster_matches_oracle_per_problem(z, ora, method, tol, mc, only):
+    # every problem of a mixed batch (built-in and user objectives, lane and
+    # block layouts, ragged swarms) clustered in one launch, each against the
+    # oracle on that problem's own outputs
+    probs = [z.Problem(**m, n_starts=40 + 37 * i, pso_iters=i % 3, bfgs_max_iters=80, seed=i)
+             for i, m in enumerate(workloads.mixed_batch(10, seed=3, dmin=2, dmax=48))]
+    probs += [z.Problem(objective="himmelblau", dim=2, lower=-5, upper=5, n_starts=300, seed=1),
+              z.Problem(objective="griewank", dim=6, lower=-20, upper=20, n_starts=1, seed=2)]
+    b = z.Batch(probs)
+    b.solve()
+    c = b.cluster(method=method, tol=tol, max_clusters=mc, only_converged=only)
+    lab = c["labels"].cpu().numpy()
+    for P, p in enumerate(probs):
+        v = b.problem(P)
+        x, f, st = (v[k].cpu().numpy() for k in ("x", "f", "status"))
+        o = ora.cluster(x, f, st, method=method, tol=tol, max_clusters=mc, only_converged=only)
+        so = b.soff[P]
+        assert np.array_equal(lab[so:so + p.n_starts], o["labels"]), P
+        assert np.array_equal(c["leaders"][P].cpu().numpy(), o["leaders"]), P
+        assert np.array_equal(c["counts"][P].cpu().numpy(), o["counts"]), P
+        for k, val in o["summary"].items():
+            a = c["summaries"][P][k]
+            assert a == val or (np.isnan(a) and np.isnan(val)), (P, k, a, val)
+    # the Himmelblau problem: its four minima are four regions
+    if method == "x" and tol == 1e-4:
+        assert c["summaries"][10]["n_clusters"] == 4
