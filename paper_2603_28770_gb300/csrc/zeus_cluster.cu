@@ -1,6 +1,6 @@
 // zeus_cluster.cu -- clustering of the final points of a multistart run
 // (Section VI proposes it: group the candidate solutions by function value
-// or by coordinates, and judge the region of the lowest f by how many
+// or by coordinates, and weigh the region of the lowest f by how many
 // starts reached it).
 //
 // Leader clustering in the order of increasing (f, start index), done in
