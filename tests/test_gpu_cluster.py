@@ -147,3 +147,35 @@ def test_batch_cluster_matches_oracle_per_problem(z, ora, method, tol, mc, only)
     # the Himmelblau problem: its four minima are four regions
     if method == "x" and tol == 1e-4:
         assert c["summaries"][10]["n_clusters"] == 4
+
+
+def test_cluster_replays_from_a_cuda_graph(z):
+    # zeus_cluster is one memset and one cooperative launch: a captured call
+    # replays to the same labels and summary
+    import ctypes as C
+    x, f, st = _points(20000, 5, seed=21)
+    xt, ft, stt = (torch.from_numpy(a).cuda() for a in (x, f, st))
+    cp = z._capi.zeus_cluster_params(1, 128, 1, 0, 0.3)
+    lab = torch.empty(20000, dtype=torch.int32, device="cuda")
+    lead = torch.empty(128, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(128, dtype=torch.int32, device="cuda")
+    res = torch.empty(C.sizeof(z._capi.zeus_cluster_result), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(z.zeus_cluster_workspace_size(128), dtype=torch.uint8, device="cuda")
+    z.zeus_cluster(cp, 20000, 5, xt, ft, stt, lab, lead, cnt, res, ws)
+    torch.cuda.synchronize()
+    ref = (lab.clone(), lead.clone(), cnt.clone(), res.clone())
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        g.capture_begin()
+        z.zeus_cluster(cp, 20000, 5, xt, ft, stt, lab, lead, cnt, res, ws, side)
+        g.capture_end()
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(2):
+        lab.fill_(7)
+        cnt.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for a, b in zip((lab, lead, cnt, res), ref):
+            assert torch.equal(a, b)
