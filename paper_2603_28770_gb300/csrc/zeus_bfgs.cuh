@@ -91,6 +91,26 @@ __device__ __forceinline__ double lane_split_dot(const T* a, const T* b, int n) 
     return v;
 }
 
+// ||g|| < tol from g'g: away from the boundary without the square root
+// (sqrt is monotone and correctly rounded, and the margins of 1e-12 exceed
+// the rounding of tol^2 by far), at it by the square root itself; the same
+// decision as sqrt(gg) < tol in every case.  With tol^2 outside the normal
+// range every decision takes the square root (lo = -1, hi = inf).
+struct GradTest {
+    double lo, hi;
+    __device__ explicit GradTest(double tol) {
+        const double t2 = tol * tol;
+        const bool fast = t2 > 1e-280 && t2 < 1e280;
+        lo = fast ? t2 * (1.0 - 1e-12) : -1.0;
+        hi = fast ? t2 * (1.0 + 1e-12) : CUDART_INF;
+    }
+    __device__ __forceinline__ bool below(double gg, double tol) const {
+        if (gg < lo) return true;
+        if (gg >= hi) return false;
+        return sqrt(gg) < tol;
+    }
+};
+
 // one thread's BFGS dot product in the order above
 template <class T>
 __device__ __forceinline__ double lane_dot(const T* a, const T* b, int n) {
@@ -535,6 +555,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
     const bool use_target = !isnan(p.target_f);
     const bool use_stop = use_target || p.required_converged > 0;
     const double tol = p.grad_tol, cA = p.armijo_c, beta = p.backtrack;
+    const GradTest gtest(tol);
     const int K = p.bfgs_max_iters, L = p.ls_max_iters;
     const int nt = val_nterms<OBJ>(d);
 
@@ -588,8 +609,6 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             if (tid == 1) sh.red[0] = dot01;
         }
         if (tid == 0) {
-            gnorm = sqrt(dot01);
-            sh.red[1] = gnorm;
             int st = -1;
             if (k >= K) {
                 st = ZEUS_RUN_MAX_ITER;
@@ -597,7 +616,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 st = ZEUS_RUN_STOPPED;
             } else if (!isfinite(f0) || bad) {
                 st = ZEUS_RUN_NONFINITE;
-            } else if (gnorm < tol) {
+            } else if (gtest.below(dot01, tol)) {
                 st = ZEUS_RUN_CONVERGED;
                 if (use_stop) {
                     const unsigned long long c = atomicAdd(&ctrl->n_conv, 1ull) + 1ull;
@@ -610,11 +629,12 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 atomicAdd(&ctrl->n_conv, 1ull);
                 atomicExch(&ctrl->stop, 1);
             }
+            if (st >= 0) sh.red[1] = sqrt(dot01);  // ||g|| of the final point
             sh.status = st;
         }
         __syncthreads();
-        gnorm = sh.red[1];
         if (sh.status >= 0) {
+            gnorm = sh.red[1];
             status = sh.status;
             break;
         }
@@ -663,13 +683,20 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 sh.ok[tid] = (m0 + tid < L && ft <= f0 + cA * al[m0 + tid] * ddir) ? 1 : 0;
             }
             __syncthreads();
-            // every thread finds the first accepted trial itself (no further
-            // barrier: the next chunk writes ok and fb only after its terms)
-            for (int mm = 0; mm < nw; ++mm)
-                if (sh.ok[mm]) {
-                    acc_m = m0 + mm;
-                    break;
+            // every warp finds the first accepted trial itself with one
+            // ballot over the flags (no further barrier: the next chunk
+            // writes ok and fb only after its terms)
+            {
+                const int lane = tid & 31;
+                const unsigned b0 = __ballot_sync(0xffffffffu, lane < nw && sh.ok[lane]);
+                if (b0) {
+                    acc_m = m0 + __ffs(b0) - 1;
+                } else if (nw > 32) {  // trials 32-63 of a chunk
+                    const unsigned b1 =
+                        __ballot_sync(0xffffffffu, lane + 32 < nw && sh.ok[lane + 32]);
+                    if (b1) acc_m = m0 + 32 + __ffs(b1) - 1;
                 }
+            }
             if (acc_m >= 0) fn = fb[acc_m - m0];
             else if (m0 + nw == L + 1) fn = fb[L - m0];  // every trial failed
             feval += (acc_m >= 0) ? (acc_m - m0 + 1) : min(nw, L - m0);
