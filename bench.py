@@ -12,10 +12,13 @@ divided by device time).  Prints one JSON line.
                   [--workload rastrigin10d_n16384|mixed4096_n256|...]
 
 The default line also carries the forms' time-to-target comparison
-("forms") and the batched form on the first 1024 problems of the mixed
-4096-problem batch ("batched").  --workload mixed4096_n256 makes the whole
-batch (4096 problems x 256 starts, d in [2, 128]) the timed step, one CUDA
-graph replay of zeus_batch_solve per step.
+("forms"), the batched form on the first 1024 problems of the mixed
+4096-problem batch ("batched") and the clustering of the step's final
+points ("cluster").  --workload mixed4096_n256 makes the whole batch (4096
+problems x 256 starts, d in [2, 128]) the timed step, one CUDA graph
+replay of zeus_batch_solve per step (its line times the clustering of
+every problem); --workload griewank10d_n16384 times a user objective of
+the default plug-in.  --study runs the early-stop study instead.
 
 --impl reference times the FP64 CPU oracle (the only reference: the paper
 ships no code) on the host cores for the same workload, a bounded sample of
