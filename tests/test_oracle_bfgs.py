@@ -76,7 +76,7 @@ def test_update_skipped_without_curvature(oracle_mod):
         assert not ok and np.array_equal(Hn, H)
 
 
-@pytest.mark.parametrize("d", [2, 3, 6, 12, 20])
+@pytest.mark.parametrize("d", [2, 3, 6, 12, 20, 40, 64])  # 40, 64: the split dot order
 def test_quadratic_termination_exact_steps(oracle_mod, d):
     # with exact line searches BFGS minimises 0.5 x^T A x in at most d steps
     # and ends with H = A^{-1} (quadratic termination of the Broyden class)
