@@ -270,30 +270,66 @@ void zo_dual_op(int op, double a1, double b1, double a2, double b2,
 
 static const double ZO_E = 2.71828182845904523536;
 
+/* The sums over the coordinates of the built-in objectives (Rosenbrock's
+ * d-1 chain terms, the terms of Rastrigin and of the quadratic, Ackley's
+ * two sums).  Reading: for d <= 32 left to right from the sum's constant
+ * (Rastrigin's 10 d, else 0); for d > 32, 32 chains, chain l over the terms
+ * j = l (mod 32) left to right with chain 0 starting from the constant,
+ * added pairwise in the tree of zo_bdot (l with l + 16, then l + 8, ...).
+ * The paper writes these sums in exact terms.  A sum is accumulated into
+ * the chains term by term (zo_sum_add) and closed by zo_sum_end. */
+typedef struct {
+    double p[32];
+    int split;
+} zo_sum;
+
+static void zo_sum_start(zo_sum *a, int d, double c0)
+{
+    a->split = d > 32;
+    for (int l = 0; l < 32; ++l) a->p[l] = 0.0;
+    a->p[0] = c0;
+}
+static void zo_sum_add(zo_sum *a, int j, double t)
+{
+    const int l = a->split ? (j & 31) : 0;
+    a->p[l] = a->p[l] + t;
+}
+static double zo_sum_end(zo_sum *a)
+{
+    if (a->split)
+        for (int w = 16; w >= 1; w >>= 1)
+            for (int l = 0; l < w; ++l) a->p[l] = a->p[l] + a->p[l + w];
+    return a->p[0];
+}
+
 double zo_f(int obj, int d, const double *x)
 {
     double s = 0.0;
+    zo_sum a0, a1;
     switch (obj) {
     case ZO_ROSENBROCK:
         /* Reading: the chain sum runs over i = 1..d-1 (the printed upper
          * limit n would need x_{n+1}). */
+        zo_sum_start(&a0, d, 0.0);
         for (int i = 0; i + 1 < d; ++i) {
             double a = 1.0 - x[i];
             double b = x[i + 1] - x[i] * x[i];
-            s = s + (a * a + 100.0 * (b * b));
+            zo_sum_add(&a0, i, a * a + 100.0 * (b * b));
         }
-        return s;
+        return zo_sum_end(&a0);
     case ZO_RASTRIGIN:
-        s = 10.0 * (double)d;
+        zo_sum_start(&a0, d, 10.0 * (double)d);
         for (int i = 0; i < d; ++i)
-            s = s + (x[i] * x[i] - 10.0 * zo_cos2pi(x[i]));
-        return s;
+            zo_sum_add(&a0, i, x[i] * x[i] - 10.0 * zo_cos2pi(x[i]));
+        return zo_sum_end(&a0);
     case ZO_ACKLEY: {
-        double s1 = 0.0, s2 = 0.0;
+        zo_sum_start(&a0, d, 0.0);
+        zo_sum_start(&a1, d, 0.0);
         for (int i = 0; i < d; ++i) {
-            s1 = s1 + x[i] * x[i];
-            s2 = s2 + zo_cos2pi(x[i]);
+            zo_sum_add(&a0, i, x[i] * x[i]);
+            zo_sum_add(&a1, i, zo_cos2pi(x[i]));
         }
+        double s1 = zo_sum_end(&a0), s2 = zo_sum_end(&a1);
         double t1 = -20.0 * zo_exp(-0.2 * sqrt(s1 / (double)d));
         double t2 = zo_exp(s2 / (double)d);
         return (t1 - t2) + (20.0 + ZO_E);
@@ -311,9 +347,10 @@ double zo_f(int obj, int d, const double *x)
         return a * b;
     }
     case ZO_QUADRATIC:
+        zo_sum_start(&a0, d, 0.0);
         for (int i = 0; i < d; ++i)
-            s = s + 0.5 * (double)(i + 1) * (x[i] * x[i]);
-        return s;
+            zo_sum_add(&a0, i, 0.5 * (double)(i + 1) * (x[i] * x[i]));
+        return zo_sum_end(&a0);
     case ZO_GRIEWANK: {
         double prod = 1.0;
         for (int i = 0; i < d; ++i) {
@@ -334,28 +371,57 @@ double zo_f(int obj, int d, const double *x)
 
 /* The same objectives written over dual numbers (Alg. 5 evaluates f on
  * xDual).  Operation order mirrors zo_f, so the value part equals zo_f. */
+/* zo_sum on duals (the value part sums exactly as zo_f) */
+typedef struct {
+    zo_dual p[32];
+    int split;
+} zo_dsum;
+
+static void zo_dsum_start(zo_dsum *a, int d, zo_dual c0)
+{
+    a->split = d > 32;
+    for (int l = 0; l < 32; ++l) a->p[l] = dconst(0.0);
+    a->p[0] = c0;
+}
+static void zo_dsum_add(zo_dsum *a, int j, zo_dual t)
+{
+    const int l = a->split ? (j & 31) : 0;
+    a->p[l] = dadd(a->p[l], t);
+}
+static zo_dual zo_dsum_end(zo_dsum *a)
+{
+    if (a->split)
+        for (int w = 16; w >= 1; w >>= 1)
+            for (int l = 0; l < w; ++l) a->p[l] = dadd(a->p[l], a->p[l + w]);
+    return a->p[0];
+}
+
 static zo_dual zo_f_dual(int obj, int d, const zo_dual *x)
 {
     zo_dual s = dconst(0.0);
+    zo_dsum a0, a1;
     switch (obj) {
     case ZO_ROSENBROCK:
+        zo_dsum_start(&a0, d, dconst(0.0));
         for (int i = 0; i + 1 < d; ++i) {
             zo_dual a = dsub(dconst(1.0), x[i]);
             zo_dual b = dsub(x[i + 1], dmul(x[i], x[i]));
-            s = dadd(s, dadd(dmul(a, a), dscale(100.0, dmul(b, b))));
+            zo_dsum_add(&a0, i, dadd(dmul(a, a), dscale(100.0, dmul(b, b))));
         }
-        return s;
+        return zo_dsum_end(&a0);
     case ZO_RASTRIGIN:
-        s = dconst(10.0 * (double)d);
+        zo_dsum_start(&a0, d, dconst(10.0 * (double)d));
         for (int i = 0; i < d; ++i)
-            s = dadd(s, dsub(dmul(x[i], x[i]), dscale(10.0, dcos2pi(x[i]))));
-        return s;
+            zo_dsum_add(&a0, i, dsub(dmul(x[i], x[i]), dscale(10.0, dcos2pi(x[i]))));
+        return zo_dsum_end(&a0);
     case ZO_ACKLEY: {
-        zo_dual s1 = dconst(0.0), s2 = dconst(0.0);
+        zo_dsum_start(&a0, d, dconst(0.0));
+        zo_dsum_start(&a1, d, dconst(0.0));
         for (int i = 0; i < d; ++i) {
-            s1 = dadd(s1, dmul(x[i], x[i]));
-            s2 = dadd(s2, dcos2pi(x[i]));
+            zo_dsum_add(&a0, i, dmul(x[i], x[i]));
+            zo_dsum_add(&a1, i, dcos2pi(x[i]));
         }
+        zo_dual s1 = zo_dsum_end(&a0), s2 = zo_dsum_end(&a1);
         zo_dual t1 = dscale(-20.0, dexp(dscale(-0.2, dsqrt(ddiv(s1, dconst((double)d))))));
         zo_dual t2 = dexp(ddiv(s2, dconst((double)d)));
         return dadd(dsub(t1, t2), dconst(20.0 + ZO_E));
@@ -382,9 +448,10 @@ static zo_dual zo_f_dual(int obj, int d, const zo_dual *x)
         return dmul(a, b);
     }
     case ZO_QUADRATIC:
+        zo_dsum_start(&a0, d, dconst(0.0));
         for (int i = 0; i < d; ++i)
-            s = dadd(s, dscale(0.5 * (double)(i + 1), dmul(x[i], x[i])));
-        return s;
+            zo_dsum_add(&a0, i, dscale(0.5 * (double)(i + 1), dmul(x[i], x[i])));
+        return zo_dsum_end(&a0);
     case ZO_GRIEWANK: {
         zo_dual prod = dconst(1.0);
         for (int i = 0; i < d; ++i) {

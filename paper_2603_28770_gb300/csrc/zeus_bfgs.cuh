@@ -217,18 +217,30 @@ __device__ __forceinline__ void val_add(Part<double>& acc, double t0, double t1)
     }
 }
 
-// f at a point on one thread, index order (equals the oracle's sweep)
+// f at a point on one thread, in the order of the oracle's sweep (the
+// objective sums of obj_sum; one term for Goldstein-Price and the user
+// objectives)
 template <int OBJ, class X>
 __device__ __forceinline__ double seq_value(const X& xa, int d) {
     using V = decltype(xa(0));
-    Part<double> acc = val_init<OBJ, V>(d);
     const int nt = val_nterms<OBJ>(d);
-    for (int j = 0; j < nt; ++j) {
-        double t0, t1;
-        val_term<OBJ>(xa, j, d, t0, t1);
-        val_add<OBJ>(acc, t0, t1);
+    if constexpr (OBJ == ZEUS_OBJ_GOLDSTEIN_PRICE || OBJ >= ZEUS_OBJ_USER) {
+        Part<double> acc = val_init<OBJ, V>(d);
+        for (int j = 0; j < nt; ++j) {
+            double t0, t1;
+            val_term<OBJ>(xa, j, d, t0, t1);
+            val_add<OBJ>(acc, t0, t1);
+        }
+        return val_finish<OBJ, V>(acc, d);
+    } else {
+        const Part<double> acc =
+            obj_sum<double>(d, nt, val_init<OBJ, V>(d), OBJ == ZEUS_OBJ_ACKLEY, [&](int j) {
+                Part<double> t;
+                val_term<OBJ>(xa, j, d, t.s0, t.s1);
+                return t;
+            });
+        return val_finish<OBJ, V>(acc, d);
     }
-    return val_finish<OBJ, V>(acc, d);
 }
 
 // Gradient: forward pass i (Alg. 5) or adjoint component i.  The adjoint
@@ -674,7 +686,29 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 tb1[mm * d + j] = t1;
             }
             __syncthreads();
-            if (tid < nw) {  // one thread per trial: its terms in order, then the test
+            if (d > kSumSplit && nt > 1) {
+                // a warp per trial: lane l forms chain l of the sums, the
+                // warp adds the chains in the fixed tree (obj_sum's order)
+                const int lane = tid & 31;
+                for (int mm = tid >> 5; mm < nw; mm += NT >> 5) {
+                    Part<double> acc;
+                    acc.s0 = acc.s1 = 0.0;
+                    if (lane == 0) acc = val_init<OBJ, T>(d);
+                    for (int j = lane; j < nt; j += 32)
+                        val_add<OBJ>(acc, tb0[mm * d + j], tb1[mm * d + j]);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        acc.s0 = acc.s0 + __shfl_down_sync(0xffffffffu, acc.s0, o);
+                        if (OBJ == ZEUS_OBJ_ACKLEY)
+                            acc.s1 = acc.s1 + __shfl_down_sync(0xffffffffu, acc.s1, o);
+                    }
+                    if (lane == 0) {
+                        const double ft = val_finish<OBJ, T>(acc, d);
+                        fb[mm] = ft;
+                        sh.ok[mm] = (m0 + mm < L && ft <= f0 + cA * al[m0 + mm] * ddir) ? 1 : 0;
+                    }
+                }
+            } else if (tid < nw) {  // one thread per trial: its terms in order, then the test
                 Part<double> acc = val_init<OBJ, T>(d);
                 for (int j = 0; j < nt; ++j)
                     val_add<OBJ>(acc, tb0[tid * d + j], tb1[tid * d + j]);

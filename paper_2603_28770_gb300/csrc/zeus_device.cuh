@@ -288,6 +288,67 @@ struct Part {
     A s0, s1;
 };
 
+// The sums of an objective over its coordinates: left to right for
+// d <= kSumSplit; past that 32 chains, chain l over the terms j = l (mod
+// 32) left to right with chain 0 starting from the sum's constant, added
+// pairwise in a fixed tree (l with l + 16, then l + 8, l + 4, l + 2, l + 1).
+// One thread forms them here: the chains in bit-reversed order (0, 16, 8,
+// 24, ...), merged as a binary counter does, hold at most five partial sums.
+// term(j) returns the two components of term j (s1 is summed if `two`).
+constexpr int kSumSplit = 32;
+
+// the split order, out of line so that its partial sums do not weigh on
+// the registers of the kernels that mostly take the short path
+template <class A, class F>
+__device__ __noinline__ Part<A> obj_sum_split(int nt, Part<A> init, bool two, F term) {
+    Part<A> q0, q1, q2, q3, q4, v;
+    q0.s0 = q0.s1 = q1.s0 = q1.s1 = q2.s0 = q2.s1 = q3.s0 = q3.s1 = q4.s0 = q4.s1 = A(0);
+    auto add = [two](Part<A> a, Part<A> b) {
+        a.s0 = a.s0 + b.s0;
+        if (two) a.s1 = a.s1 + b.s1;
+        return a;
+    };
+#pragma unroll 1
+    for (int k = 0; k < 32; ++k) {
+        const int l = (int)(__brev((unsigned)k) >> 27);
+        if (l == 0) {
+            v = init;
+        } else {
+            v.s0 = A(0);
+            v.s1 = A(0);
+        }
+#pragma unroll 1
+        for (int j = l; j < nt; j += 32) {
+            const Part<A> t = term(j);
+            v.s0 = v.s0 + t.s0;
+            if (two) v.s1 = v.s1 + t.s1;
+        }
+        if (!(k & 1)) { q0 = v; continue; }
+        v = add(q0, v);
+        if (!(k & 2)) { q1 = v; continue; }
+        v = add(q1, v);
+        if (!(k & 4)) { q2 = v; continue; }
+        v = add(q2, v);
+        if (!(k & 8)) { q3 = v; continue; }
+        v = add(q3, v);
+        if (!(k & 16)) { q4 = v; continue; }
+        v = add(q4, v);
+    }
+    return v;
+}
+
+template <class A, class F>
+__device__ __forceinline__ Part<A> obj_sum(int d, int nt, Part<A> init, bool two, F term) {
+    if (d > kSumSplit) return obj_sum_split<A>(nt, init, two, term);
+    Part<A> acc = init;
+    for (int j = 0; j < nt; ++j) {
+        const Part<A> t = term(j);
+        acc.s0 = acc.s0 + t.s0;
+        if (two) acc.s1 = acc.s1 + t.s1;
+    }
+    return acc;
+}
+
 // A user objective is one term: f at the whole point, evaluated by one
 // thread in the plug-in's own order.  Coordinates reach it through an
 // accessor, x(j); duals carry the tangent seeded on coordinate i.
@@ -411,42 +472,54 @@ __device__ __forceinline__ A value_finish(Part<A> p, int d) {
 // Alg. 5, one pass: f on duals with seed e_i.  Returns (value, df/dx_i).
 template <int OBJ, class T>
 __device__ __forceinline__ Dual<T> builtin_forward_pass(const T* x, int d, int i) {
+    // value sums in the order of obj_sum; the tangent sums have at most
+    // two non-zero terms, so their order does not change them
+    Part<T> zero;
+    zero.s0 = zero.s1 = T(0);
     if (OBJ == ZEUS_OBJ_ROSENBROCK) {
-        T val = T(0), tan = T(0);
-        for (int j = 0; j < d - 1; ++j) {
+        T tan = T(0);
+        const Part<T> acc = obj_sum<T>(d, d - 1, zero, false, [&](int j) {
             const T xj = x[j], xk = x[j + 1];
+            Part<T> r;
+            r.s1 = T(0);
             if (j == i || j + 1 == i) {
                 const Dual<T> u = dmk(xj, T(j == i ? 1 : 0));
                 const Dual<T> v = dmk(xk, T(j + 1 == i ? 1 : 0));
                 const Dual<T> a = dmk(T(1), T(0)) - u;
                 const Dual<T> b = v - u * u;
                 const Dual<T> t = a * a + T(100) * (b * b);
-                val += t.a;
+                r.s0 = t.a;
                 tan += t.b;
             } else {
                 const T a = T(1) - xj;
                 const T b = xk - xj * xj;
-                val += a * a + T(100) * (b * b);
+                r.s0 = a * a + T(100) * (b * b);
             }
-        }
-        return dmk(val, tan);
+            return r;
+        });
+        return dmk(acc.s0, tan);
     } else if (OBJ == ZEUS_OBJ_RASTRIGIN) {
-        T val = T(10) * T(d), tan = T(0);
-        for (int j = 0; j < d; ++j) {
+        T tan = T(0);
+        Part<T> init = zero;
+        init.s0 = T(10) * T(d);
+        const Part<T> acc = obj_sum<T>(d, d, init, false, [&](int j) {
             const T xj = x[j];
+            Part<T> r;
+            r.s1 = T(0);
             if (j == i) {
                 T s, c;
                 sc_2pi(xj, &s, &c);
                 // x^2 - 10 cos(2 pi x) on duals with tangent 1
                 const T tx2 = xj + xj;
                 const T tcos = -s * Consts<T>::two_pi();
-                val += xj * xj - T(10) * c;
+                r.s0 = xj * xj - T(10) * c;
                 tan += tx2 - T(10) * tcos;
             } else {
-                val += xj * xj - T(10) * c_2pi(xj);
+                r.s0 = xj * xj - T(10) * c_2pi(xj);
             }
-        }
-        return dmk(val, tan);
+            return r;
+        });
+        return dmk(acc.s0, tan);
     } else if (OBJ == ZEUS_OBJ_ACKLEY) {
         // the sine of x_i (tangent of the cosine) is taken before the sweep
         // so that the sweep itself is the same for every i (no divergence
@@ -454,12 +527,14 @@ __device__ __forceinline__ Dual<T> builtin_forward_pass(const T* x, int d, int i
         // the cosine of sc_2pi
         T sn, cn;
         sc_2pi(x[i], &sn, &cn);
-        T s1 = T(0), s2 = T(0);
-        for (int j = 0; j < d; ++j) {
+        const Part<T> sums = obj_sum<T>(d, d, zero, true, [&](int j) {
             const T xj = x[j];
-            s1 += xj * xj;
-            s2 += c_2pi(xj);
-        }
+            Part<T> r;
+            r.s0 = xj * xj;
+            r.s1 = c_2pi(xj);
+            return r;
+        });
+        const T s1 = sums.s0, s2 = sums.s1;
         // the only non-zero tangents of the two sums are those of term i
         T t1 = T(0), t2 = T(0);
         t1 += x[i] + x[i];
@@ -491,14 +566,17 @@ __device__ __forceinline__ Dual<T> builtin_forward_pass(const T* x, int d, int i
         const Dual<T> b = dmk(T(30), T(0)) + (u * u) * pb;
         return a * b;
     } else {  // quadratic
-        T val = T(0), tan = T(0);
-        for (int j = 0; j < d; ++j) {
+        T tan = T(0);
+        const Part<T> acc = obj_sum<T>(d, d, zero, false, [&](int j) {
             const T xj = x[j];
             const T c = T(0.5) * T(j + 1);
-            val += c * (xj * xj);
+            Part<T> r;
+            r.s0 = c * (xj * xj);
+            r.s1 = T(0);
             if (j == i) tan += c * (xj + xj);
-        }
-        return dmk(val, tan);
+            return r;
+        });
+        return dmk(acc.s0, tan);
     }
 }
 
@@ -568,12 +646,16 @@ __device__ __forceinline__ AdjShared adjoint_prep(const T* x, int d) {
     a.c1 = 0.0;
     a.c2 = 0.0;
     if (OBJ == ZEUS_OBJ_ACKLEY) {
-        T s1 = T(0), s2 = T(0);
-        for (int j = 0; j < d; ++j) {
+        Part<T> zero;
+        zero.s0 = zero.s1 = T(0);
+        const Part<T> sums = obj_sum<T>(d, d, zero, true, [&](int j) {
             const T xj = x[j];
-            s1 = s1 + xj * xj;
-            s2 = s2 + c_2pi(xj);
-        }
+            Part<T> r;
+            r.s0 = xj * xj;
+            r.s1 = c_2pi(xj);
+            return r;
+        });
+        const T s1 = sums.s0, s2 = sums.s1;
         const T dd = T(d);
         const T r = xsqrt(s1 / dd);
         const T e1 = xexp(T(-0.2) * r);

@@ -132,8 +132,9 @@ struct BatchDev {
 
 // ---- launchers (defined in the kernel translation units) ----
 // lanes per particle of the PSO and objective kernels: one lane (sums in
-// index order) up to d = 64, a warp above
-inline int lanes_for_dim(int d) { return d <= 64 ? 1 : 32; }
+// index order) up to d = 32, a warp above (lane l forms chain l of the
+// objective's sums, the warp adds the chains in the fixed tree)
+inline int lanes_for_dim(int d) { return d <= 32 ? 1 : 32; }
 
 cudaError_t launch_pso(const zeus_problem& p, int G, double* x, double* v, double* px, double* pf,
                        double* gx, Ctrl* ctrl, ArgPair* partials, zeus_result* res,

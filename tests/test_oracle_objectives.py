@@ -141,3 +141,49 @@ def test_forward_pass_seeds_unit_vectors(oracle_mod):
     _, g = oracle_mod.grad_forward("quadratic", x)
     assert np.array_equal(g, np.arange(1, 5) * x)
     assert math.isnan(oracle_mod.f(999, x))
+
+
+@pytest.mark.parametrize("d", [33, 64, 1000])
+def test_split_sums_exact_on_integer_points(oracle_mod, d):
+    # past 32 coordinates the sums run as 32 chains and a tree; at integer
+    # points every Rastrigin term is the integer x^2 - 10 (cos 2 pi x = 1
+    # exactly), so any order gives the exact value sum x^2
+    rng = np.random.default_rng(d)
+    x = rng.integers(-5, 6, d).astype(float)
+    assert oracle_mod.f("rastrigin", x) == float(np.sum(x.astype(np.int64) ** 2))
+    fv, g = oracle_mod.grad_forward("rastrigin", x)
+    assert fv == oracle_mod.f("rastrigin", x) and np.array_equal(g, 2 * x)
+
+
+@pytest.mark.parametrize("obj,d", [("quadratic", 100), ("rosenbrock", 64), ("ackley", 200)])
+def test_split_sums_within_the_error_bound(oracle_mod, obj, d):
+    # the value stays within the rounding bound of its longest chain
+    # (d / 32 + 1 additions, then 5 tree levels) of the exact sum of the
+    # exactly evaluated terms (fractions)
+    from fractions import Fraction
+    rng = np.random.default_rng(7 + d)
+    x = rng.uniform(-2, 2, d)
+    u = 2.0 ** -53
+    k = d // 32 + 1 + 5
+    if obj == "quadratic":
+        terms = [Fraction(0.5 * (i + 1)) * Fraction(float(x[i])) ** 2 for i in range(d)]
+        exact = sum(terms)
+        mag = float(sum(abs(t) for t in terms))
+        # each term itself is rounded at most twice
+        bound = (k + 2) * u * mag / (1 - (k + 2) * u)
+        assert abs(oracle_mod.f(obj, x) - float(exact)) <= bound
+    elif obj == "rosenbrock":
+        terms = [(1 - Fraction(float(x[i]))) ** 2
+                 + 100 * (Fraction(float(x[i + 1])) - Fraction(float(x[i])) ** 2) ** 2
+                 for i in range(d - 1)]
+        exact = sum(terms)
+        mag = float(sum(abs(t) for t in terms))
+        bound = (k + 6) * u * mag / (1 - (k + 6) * u)
+        assert abs(oracle_mod.f(obj, x) - float(exact)) <= bound
+    else:
+        # Ackley: the sums enter exp and sqrt; compare with an mpmath-free
+        # double evaluation in fractions of the sums
+        s1 = float(sum(Fraction(float(v)) ** 2 for v in x))
+        s2 = float(np.sum(np.cos(2 * np.pi * x)))
+        ref = -20 * np.exp(-0.2 * np.sqrt(s1 / d)) - np.exp(s2 / d) + 20 + np.e
+        assert abs(oracle_mod.f(obj, x) - ref) <= 1e-12 * max(1.0, abs(ref))
