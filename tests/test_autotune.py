@@ -57,3 +57,18 @@ def test_tuner_ties_go_to_the_smaller_layout(z, tmp_path):
     from paper_2603_28770_gb300.autotune import Autotuner
     t = Autotuner(str(tmp_path / "t.json"), measure=lambda probe: 1.0, device_name="dev")
     assert t.apply([z.Problem(objective="rosenbrock", dim=4)])[0].threads_per_start == 0
+
+
+def test_candidates_of_user_objectives(z):
+    # a user objective takes the lane and block layouts the plan accepts,
+    # never the streamed-H one (no user objective streams H)
+    from paper_2603_28770_gb300.autotune import Autotuner
+    small = z.Problem(objective="griewank", dim=8, n_starts=64).to_c()
+    large = z.Problem(objective="griewank", dim=100, n_starts=64).to_c()
+    assert Autotuner._valid(small, 0) and Autotuner._valid(small, 1) and Autotuner._valid(small, 128)
+    assert not Autotuner._valid(small, 256)
+    assert Autotuner._valid(large, 128) and not Autotuner._valid(large, 1)
+    assert not Autotuner._valid(large, 256)
+    # forward mode only: the adjoint form of the same problem has no layout
+    adj = z.Problem(objective="griewank", dim=8, n_starts=64, grad_mode="adjoint").to_c()
+    assert not any(Autotuner._valid(adj, t) for t in (0, 1, 128, 256))
