@@ -14,4 +14,5 @@ from .oracle import (  # noqa: F401
     OBJECTIVES, Problem, build, lib, philox4x64_10, uniform, f, grad_forward,
     dual_op, sincos2pi, exp, argmin, pso, line_search, bfgs_update, bfgs, bfgs_many, solve,
     bfgs_quadratic_exact, max_threads, lbfgs_direction, cluster, CLUSTER_METHODS, dot_split,
+    dot_plain, direction, ORDER_LIB, ORDER_PLAIN,
 )

@@ -20,6 +20,10 @@ _SRC = os.path.join(_HERE, "zeus_oracle.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD_DIR, "libzeus_oracle.so")
 
+# rounding orders of zeus_oracle.c (see its ZO_ORDER_* note)
+ORDER_LIB = 0
+ORDER_PLAIN = 1
+
 # Section V-B test functions; QUADRATIC is a test objective 0.5*sum (i+1) x_i^2.
 OBJECTIVES = {"rosenbrock": 0, "rastrigin": 1, "ackley": 2,
               "goldstein_price": 3, "quadratic": 100,
@@ -55,7 +59,7 @@ class _Problem(C.Structure):
         ("target_f", C.c_double),
         ("seed", C.c_uint64),
         ("start_from_pbest", C.c_int32), ("n_threads", C.c_int32),
-        ("lbfgs_m", C.c_int32), ("pad", C.c_int32),
+        ("lbfgs_m", C.c_int32), ("order", C.c_int32),
     ]
 
 
@@ -91,6 +95,10 @@ class Problem:
     start_from_pbest: int = 0
     n_threads: int = 0
     lbfgs_m: int = 0  # 0: dense inverse Hessian (Alg. 4); m > 0: L-BFGS with m pairs
+    # rounding order of sums and the update: ORDER_LIB (fma per product term,
+    # 32-chain sums past 32 terms, mirrored triangle) or ORDER_PLAIN (every
+    # operation rounded on its own, sums left to right, whole-matrix update)
+    order: int = 0
 
     def obj_id(self) -> int:
         o = self.objective
@@ -103,7 +111,7 @@ class Problem:
                         self.grad_tol, self.w, self.c1, self.c2,
                         self.armijo_c, self.backtrack, self.target_f,
                         self.seed & (2**64 - 1), self.start_from_pbest,
-                        self.n_threads, self.lbfgs_m, 0)
+                        self.n_threads, self.lbfgs_m, int(self.order))
 
 
 class _ClusterResult(C.Structure):
@@ -134,7 +142,21 @@ def lib():
     L.zo_exp.restype = C.c_double
     L.zo_f.argtypes = [C.c_int, C.c_int, _D]
     L.zo_f.restype = C.c_double
+    L.zo_f_ord.argtypes = [C.c_int, C.c_int, _D, C.c_int]
+    L.zo_f_ord.restype = C.c_double
     L.zo_grad_forward.argtypes = [C.c_int, C.c_int, _D, _D, _D]
+    L.zo_grad_forward_ord.argtypes = [C.c_int, C.c_int, _D, _D, _D, C.c_int]
+    L.zo_dot_plain.argtypes = [C.c_int, _D, _D]
+    L.zo_dot_plain.restype = C.c_double
+    L.zo_direction.argtypes = [C.c_int, _D, _D, _D, _D, C.c_int]
+    L.zo_direction.restype = C.c_int
+    L.zo_bfgs_update_ord.argtypes = [C.c_int, _D, _D, _D, C.c_int]
+    L.zo_bfgs_update_ord.restype = C.c_int
+    L.zo_lbfgs_direction_ord.argtypes = [C.c_int, C.c_int, _D, _D, _D, _D, _D, C.c_int]
+    L.zo_line_search_ord.argtypes = [C.c_int, C.c_int, _D, _D, C.c_double, C.c_double,
+                                     C.c_double, C.c_double, C.c_int, _D, _I32, _I32, _D,
+                                     C.c_int]
+    L.zo_line_search_ord.restype = C.c_double
     L.zo_cluster.argtypes = [C.c_int, C.c_double, C.c_int32, C.c_int, C.c_int64, C.c_int, _D,
                              _D, _I32, _I32, _I32, _I32, C.POINTER(_ClusterResult)]
     L.zo_dot_split.argtypes = [C.c_int, _D, _D]
@@ -157,7 +179,7 @@ def lib():
                            C.POINTER(_Result)]
     L.zo_solve.restype = C.c_int64
     L.zo_bfgs_quadratic_exact.argtypes = [C.c_int, _D, _D, C.c_int,
-                                          C.c_double, _D, _D]
+                                          C.c_double, _D, _D, C.c_int]
     L.zo_bfgs_quadratic_exact.restype = C.c_int
     L.zo_max_threads.restype = C.c_int
     assert L.zo_sizeof_problem() == C.sizeof(_Problem)
@@ -218,18 +240,18 @@ def _obj(o) -> int:
     return OBJECTIVES[o] if isinstance(o, str) else int(o)
 
 
-def f(objective, x) -> float:
-    """Objective value (Section V-B)."""
+def f(objective, x, order: int = ORDER_LIB) -> float:
+    """Objective value (Section V-B), its sums in the given rounding order."""
     x = _f64(x)
-    return float(lib().zo_f(_obj(objective), x.size, _dp(x)))
+    return float(lib().zo_f_ord(_obj(objective), x.size, _dp(x), int(order)))
 
 
-def grad_forward(objective, x):
+def grad_forward(objective, x, order: int = ORDER_LIB):
     """Forward-mode gradient by d dual passes (Alg. 5); returns (f, g)."""
     x = _f64(x)
     g = np.zeros_like(x)
     fv = C.c_double()
-    lib().zo_grad_forward(_obj(objective), x.size, _dp(x), C.byref(fv), _dp(g))
+    lib().zo_grad_forward_ord(_obj(objective), x.size, _dp(x), C.byref(fv), _dp(g), int(order))
     return fv.value, g
 
 
@@ -250,22 +272,32 @@ def pso(p: Problem) -> dict:
     return dict(x=x, v=v, px=px, pf=pf, gx=gx, gf=gf.value, gidx=gi.value)
 
 
-def line_search(objective, x, p, f0, ddir, c=1e-4, beta=0.5, L=20):
+def line_search(objective, x, p, f0, ddir, c=1e-4, beta=0.5, L=20, order: int = ORDER_LIB):
     """Backtracking Armijo line search (Alg. 6): returns (alpha, accepted, n_feval)."""
     x = _f64(x); p = _f64(p)
     xt = np.zeros_like(x)
     acc = C.c_int(); nf = C.c_int(0); mg = C.c_double(math.inf)
-    a = lib().zo_line_search(_obj(objective), x.size, _dp(x), _dp(p), f0, ddir,
-                             c, beta, L, _dp(xt), C.byref(acc), C.byref(nf),
-                             C.byref(mg))
+    a = lib().zo_line_search_ord(_obj(objective), x.size, _dp(x), _dp(p), f0, ddir,
+                                 c, beta, L, _dp(xt), C.byref(acc), C.byref(nf),
+                                 C.byref(mg), int(order))
     return float(a), bool(acc.value), int(nf.value)
 
 
-def bfgs_update(H, s, y):
+def bfgs_update(H, s, y, order: int = ORDER_LIB):
     """Inverse-Hessian rank-two update of Alg. 4; returns (H_new, applied)."""
     H = _f64(H).copy(); s = _f64(s); y = _f64(y)
-    ok = lib().zo_bfgs_update(s.size, _dp(H), _dp(s), _dp(y))
+    ok = lib().zo_bfgs_update_ord(s.size, _dp(H), _dp(s), _dp(y), int(order))
     return H, bool(ok)
+
+
+def direction(H, g, order: int = ORDER_LIB):
+    """Search direction of Alg. 4 with the non-descent reset: returns
+    (p, H after the call, g'p, reset taken)."""
+    H = _f64(H).copy(); g = _f64(g)
+    p = np.zeros_like(g)
+    dd = C.c_double()
+    r = lib().zo_direction(g.size, _dp(H), _dp(g), _dp(p), C.byref(dd), int(order))
+    return p, H, dd.value, bool(r)
 
 
 def _results(res, n):
@@ -318,17 +350,17 @@ def solve(p: Problem) -> dict:
     return out
 
 
-def bfgs_quadratic_exact(A, x0, max_iters=100, tol=1e-10):
+def bfgs_quadratic_exact(A, x0, max_iters=100, tol=1e-10, order: int = ORDER_LIB):
     """Test-only BFGS with exact steps on 0.5 x^T A x; returns (iters, x, H)."""
     A = _f64(A); x0 = _f64(x0)
     d = x0.size
     xo = np.zeros(d); H = np.zeros((d, d))
     k = lib().zo_bfgs_quadratic_exact(d, _dp(A), _dp(x0), max_iters, tol,
-                                      _dp(xo), _dp(H))
+                                      _dp(xo), _dp(H), int(order))
     return int(k), xo, H
 
 
-def lbfgs_direction(S, Y, g):
+def lbfgs_direction(S, Y, g, order: int = ORDER_LIB):
     """Two-loop L-BFGS direction p = -H g over the pairs (rows of S and Y,
     oldest first) with the initial matrix gamma I."""
     S = np.ascontiguousarray(S, dtype=np.float64)
@@ -337,8 +369,9 @@ def lbfgs_direction(S, Y, g):
     n, d = (S.shape[0], g.shape[0]) if S.size else (0, g.shape[0])
     rho = np.array([1.0 / float(np.dot(Y[i], S[i])) for i in range(n)], dtype=np.float64)
     p = np.zeros(d)
-    lib().zo_lbfgs_direction(d, n, _dp(S if n else np.zeros(1)), _dp(Y if n else np.zeros(1)),
-                             _dp(rho if n else np.zeros(1)), _dp(g), _dp(p))
+    lib().zo_lbfgs_direction_ord(d, n, _dp(S if n else np.zeros(1)),
+                                 _dp(Y if n else np.zeros(1)), _dp(rho if n else np.zeros(1)),
+                                 _dp(g), _dp(p), int(order))
     return p
 
 
@@ -366,6 +399,13 @@ def cluster(x, f, status=None, method="x", tol=1e-3, max_clusters=256, only_conv
                      cnt.ctypes.data_as(p32), C.byref(r))
     summary = {k: getattr(r, k) for k, _ in _ClusterResult._fields_}
     return dict(labels=lab[:n], leaders=lead, counts=cnt, summary=summary)
+
+
+def dot_plain(a, b) -> float:
+    """The BFGS dot product in the plain order: left to right, each
+    product and each sum rounded on its own."""
+    a, b = _f64(a), _f64(b)
+    return float(lib().zo_dot_plain(a.size, _dp(a), _dp(b)))
 
 
 def dot_split(a, b) -> float:

@@ -14,6 +14,13 @@
  * (no FMA contraction, so every product and sum below is rounded exactly
  * once in the order written).
  *
+ * Two rounding orders (zo_problem.order): the plain order rounds every
+ * operation on its own and sums left to right; the library order is a
+ * second fixed order that 32 lanes can form (fma per product term, 32
+ * strided chains past 32 terms, the update over one triangle).  The paper
+ * states the arithmetic exactly, so both are readings of it; the pins in
+ * tests/test_oracle_*.py hold for both.
+ *
  * Each function names the part of the paper it follows (Zeus, arXiv
  * 2603.28770).  Readings of points the paper leaves open are marked
  * "Reading:".
@@ -60,8 +67,25 @@ typedef struct {
     int32_t start_from_pbest;   /* 0 = current swarm positions (Alg. 10) */
     int32_t n_threads;          /* OpenMP threads for the per-start loops */
     int32_t lbfgs_m;            /* 0 = dense inverse Hessian (Alg. 4); m > 0 = L-BFGS, m pairs */
-    int32_t pad;
+    int32_t order;              /* rounding order of the sums and the update: ZO_ORDER_LIB or
+                                   ZO_ORDER_PLAIN (below) */
 } zo_problem;
+
+/* Rounding order.  The paper states every sum and product of the method in
+ * exact arithmetic; the oracle offers two readings of the order in which
+ * they are rounded.
+ *  ZO_ORDER_PLAIN  the textbook order: every sum left to right, every product
+ *                  and every sum rounded on its own (no fused multiply-add
+ *                  outside the elementary functions), the rank-two update
+ *                  formed element by element over the whole matrix from its
+ *                  expanded form.  Independent of how any GPU forms a sum.
+ *  ZO_ORDER_LIB    a second, fixed order that a warp can form: products
+ *                  accumulated with one rounding (fma), sums past 32 terms in
+ *                  32 strided chains added by a fixed pairwise tree, the
+ *                  update over the upper triangle, mirrored.
+ * The two agree to rounding; the GPU path is compared with the plain order
+ * within a tolerance and with the library order bit for bit. */
+enum { ZO_ORDER_LIB = 0, ZO_ORDER_PLAIN = 1 };
 
 /* per-start result of one BFGS run (Alg. 4) */
 typedef struct {
@@ -277,15 +301,16 @@ static const double ZO_E = 2.71828182845904523536;
  * j = l (mod 32) left to right with chain 0 starting from the constant,
  * added pairwise in the tree of zo_bdot (l with l + 16, then l + 8, ...).
  * The paper writes these sums in exact terms.  A sum is accumulated into
- * the chains term by term (zo_sum_add) and closed by zo_sum_end. */
+ * the chains term by term (zo_sum_add) and closed by zo_sum_end.  In the
+ * plain order (ZO_ORDER_PLAIN) every sum is one chain, left to right. */
 typedef struct {
     double p[32];
     int split;
 } zo_sum;
 
-static void zo_sum_start(zo_sum *a, int d, double c0)
+static void zo_sum_start(zo_sum *a, int d, double c0, int ord)
 {
-    a->split = d > 32;
+    a->split = ord == ZO_ORDER_LIB && d > 32;
     for (int l = 0; l < 32; ++l) a->p[l] = 0.0;
     a->p[0] = c0;
 }
@@ -302,7 +327,7 @@ static double zo_sum_end(zo_sum *a)
     return a->p[0];
 }
 
-double zo_f(int obj, int d, const double *x)
+double zo_f_ord(int obj, int d, const double *x, int ord)
 {
     double s = 0.0;
     zo_sum a0, a1;
@@ -310,7 +335,7 @@ double zo_f(int obj, int d, const double *x)
     case ZO_ROSENBROCK:
         /* Reading: the chain sum runs over i = 1..d-1 (the printed upper
          * limit n would need x_{n+1}). */
-        zo_sum_start(&a0, d, 0.0);
+        zo_sum_start(&a0, d, 0.0, ord);
         for (int i = 0; i + 1 < d; ++i) {
             double a = 1.0 - x[i];
             double b = x[i + 1] - x[i] * x[i];
@@ -318,13 +343,13 @@ double zo_f(int obj, int d, const double *x)
         }
         return zo_sum_end(&a0);
     case ZO_RASTRIGIN:
-        zo_sum_start(&a0, d, 10.0 * (double)d);
+        zo_sum_start(&a0, d, 10.0 * (double)d, ord);
         for (int i = 0; i < d; ++i)
             zo_sum_add(&a0, i, x[i] * x[i] - 10.0 * zo_cos2pi(x[i]));
         return zo_sum_end(&a0);
     case ZO_ACKLEY: {
-        zo_sum_start(&a0, d, 0.0);
-        zo_sum_start(&a1, d, 0.0);
+        zo_sum_start(&a0, d, 0.0, ord);
+        zo_sum_start(&a1, d, 0.0, ord);
         for (int i = 0; i < d; ++i) {
             zo_sum_add(&a0, i, x[i] * x[i]);
             zo_sum_add(&a1, i, zo_cos2pi(x[i]));
@@ -347,7 +372,7 @@ double zo_f(int obj, int d, const double *x)
         return a * b;
     }
     case ZO_QUADRATIC:
-        zo_sum_start(&a0, d, 0.0);
+        zo_sum_start(&a0, d, 0.0, ord);
         for (int i = 0; i < d; ++i)
             zo_sum_add(&a0, i, 0.5 * (double)(i + 1) * (x[i] * x[i]));
         return zo_sum_end(&a0);
@@ -369,6 +394,8 @@ double zo_f(int obj, int d, const double *x)
     }
 }
 
+double zo_f(int obj, int d, const double *x) { return zo_f_ord(obj, d, x, ZO_ORDER_LIB); }
+
 /* The same objectives written over dual numbers (Alg. 5 evaluates f on
  * xDual).  Operation order mirrors zo_f, so the value part equals zo_f. */
 /* zo_sum on duals (the value part sums exactly as zo_f) */
@@ -377,9 +404,9 @@ typedef struct {
     int split;
 } zo_dsum;
 
-static void zo_dsum_start(zo_dsum *a, int d, zo_dual c0)
+static void zo_dsum_start(zo_dsum *a, int d, zo_dual c0, int ord)
 {
-    a->split = d > 32;
+    a->split = ord == ZO_ORDER_LIB && d > 32;
     for (int l = 0; l < 32; ++l) a->p[l] = dconst(0.0);
     a->p[0] = c0;
 }
@@ -396,13 +423,13 @@ static zo_dual zo_dsum_end(zo_dsum *a)
     return a->p[0];
 }
 
-static zo_dual zo_f_dual(int obj, int d, const zo_dual *x)
+static zo_dual zo_f_dual(int obj, int d, const zo_dual *x, int ord)
 {
     zo_dual s = dconst(0.0);
     zo_dsum a0, a1;
     switch (obj) {
     case ZO_ROSENBROCK:
-        zo_dsum_start(&a0, d, dconst(0.0));
+        zo_dsum_start(&a0, d, dconst(0.0), ord);
         for (int i = 0; i + 1 < d; ++i) {
             zo_dual a = dsub(dconst(1.0), x[i]);
             zo_dual b = dsub(x[i + 1], dmul(x[i], x[i]));
@@ -410,13 +437,13 @@ static zo_dual zo_f_dual(int obj, int d, const zo_dual *x)
         }
         return zo_dsum_end(&a0);
     case ZO_RASTRIGIN:
-        zo_dsum_start(&a0, d, dconst(10.0 * (double)d));
+        zo_dsum_start(&a0, d, dconst(10.0 * (double)d), ord);
         for (int i = 0; i < d; ++i)
             zo_dsum_add(&a0, i, dsub(dmul(x[i], x[i]), dscale(10.0, dcos2pi(x[i]))));
         return zo_dsum_end(&a0);
     case ZO_ACKLEY: {
-        zo_dsum_start(&a0, d, dconst(0.0));
-        zo_dsum_start(&a1, d, dconst(0.0));
+        zo_dsum_start(&a0, d, dconst(0.0), ord);
+        zo_dsum_start(&a1, d, dconst(0.0), ord);
         for (int i = 0; i < d; ++i) {
             zo_dsum_add(&a0, i, dmul(x[i], x[i]));
             zo_dsum_add(&a1, i, dcos2pi(x[i]));
@@ -448,7 +475,7 @@ static zo_dual zo_f_dual(int obj, int d, const zo_dual *x)
         return dmul(a, b);
     }
     case ZO_QUADRATIC:
-        zo_dsum_start(&a0, d, dconst(0.0));
+        zo_dsum_start(&a0, d, dconst(0.0), ord);
         for (int i = 0; i < d; ++i)
             zo_dsum_add(&a0, i, dscale(0.5 * (double)(i + 1), dmul(x[i], x[i])));
         return zo_dsum_end(&a0);
@@ -474,21 +501,26 @@ static zo_dual zo_f_dual(int obj, int d, const zo_dual *x)
  * evaluates f on duals and reads the tangent as df/dx_i.  The value part
  * of the first pass is returned as f(x) (reading: the line search's f0 is
  * this value). */
-void zo_grad_forward(int obj, int d, const double *x, double *f, double *g)
+void zo_grad_forward_ord(int obj, int d, const double *x, double *f, double *g, int ord)
 {
     zo_dual *xd = (zo_dual *)malloc(sizeof(zo_dual) * (size_t)(d > 0 ? d : 1));
     for (int i = 0; i < d; ++i) { xd[i].a = x[i]; xd[i].b = 0.0; }
     double fval = NAN;
     for (int i = 0; i < d; ++i) {
         xd[i].b = 1.0;
-        zo_dual r = zo_f_dual(obj, d, xd);
+        zo_dual r = zo_f_dual(obj, d, xd, ord);
         g[i] = r.b;
         if (i == 0) fval = r.a;
         xd[i].b = 0.0;
     }
-    if (d == 0) fval = zo_f(obj, d, x);
+    if (d == 0) fval = zo_f_ord(obj, d, x, ord);
     *f = fval;
     free(xd);
+}
+
+void zo_grad_forward(int obj, int d, const double *x, double *f, double *g)
+{
+    zo_grad_forward_ord(obj, d, x, f, g, ZO_ORDER_LIB);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -537,7 +569,7 @@ void zo_pso(const zo_problem *pr, double *x, double *v, double *px,
             v[i * d + j] = vlo + (vhi - vlo) * uv;
             px[i * d + j] = x[i * d + j];
         }
-        pf[i] = zo_f(pr->objective, d, x + i * d);
+        pf[i] = zo_f_ord(pr->objective, d, x + i * d, pr->order);
     }
     int64_t b = zo_argmin(pf, n);
     *gidx = b;
@@ -557,7 +589,7 @@ void zo_pso(const zo_problem *pr, double *x, double *v, double *px,
                 vi[j] = vn;
                 xi[j] = xi[j] + vn;
             }
-            double fv = zo_f(pr->objective, d, xi);
+            double fv = zo_f_ord(pr->objective, d, xi, pr->order);
             if (fv < pf[i]) {
                 pf[i] = fv;
                 for (int j = 0; j < d; ++j) pi[j] = xi[j];
@@ -587,15 +619,15 @@ static double track_margin(double margin, double lhs, double rhs)
     return m < margin ? m : margin;
 }
 
-double zo_line_search(int obj, int d, const double *x, const double *p,
-                      double f0, double ddir, double c, double beta, int L,
-                      double *xt, int *accepted, int *n_feval, double *margin)
+double zo_line_search_ord(int obj, int d, const double *x, const double *p,
+                          double f0, double ddir, double c, double beta, int L,
+                          double *xt, int *accepted, int *n_feval, double *margin, int ord)
 {
     double alpha = 1.0;
     *accepted = 0;
     for (int m = 0; m < L; ++m) {
         for (int j = 0; j < d; ++j) xt[j] = x[j] + alpha * p[j];
-        double ft = zo_f(obj, d, xt);
+        double ft = zo_f_ord(obj, d, xt, ord);
         (*n_feval)++;
         double rhs = f0 + c * alpha * ddir;
         if (margin) *margin = track_margin(*margin, ft, rhs);
@@ -605,11 +637,20 @@ double zo_line_search(int obj, int d, const double *x, const double *p,
     return alpha;
 }
 
+double zo_line_search(int obj, int d, const double *x, const double *p,
+                      double f0, double ddir, double c, double beta, int L,
+                      double *xt, int *accepted, int *n_feval, double *margin)
+{
+    return zo_line_search_ord(obj, d, x, p, f0, ddir, c, beta, L, xt, accepted, n_feval,
+                              margin, ZO_ORDER_LIB);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dot products and matrix-vector products (Alg. 4: H g, g^T p, y^T s,      */
-/* H y, y^T H y).  Reading: every product term is accumulated with one      */
-/* rounding, acc = fma(a_i, b_i, acc), in index order; the paper fixes the  */
-/* arithmetic only in exact terms.                                           */
+/* H y, y^T H y).  The paper fixes them only in exact terms.                */
+/* Plain order: acc = acc + a_i b_i in index order, the product and the sum */
+/* each rounded.  Library order: every product term accumulated with one    */
+/* rounding, acc = fma(a_i, b_i, acc), in index order.                      */
 /* ------------------------------------------------------------------------ */
 
 static double zo_dot(int n, const double *a, const double *b)
@@ -619,13 +660,19 @@ static double zo_dot(int n, const double *a, const double *b)
     return acc;
 }
 
+static double zo_pdot(int n, const double *a, const double *b)
+{
+    double acc = 0.0;
+    for (int i = 0; i < n; ++i) acc = acc + a[i] * b[i];
+    return acc;
+}
+
 /* The dot products of the BFGS step (||g||^2, g^T p, y^T s, s^T s, y^T y,
- * y^T H y).  Reading: for n <= 32 as zo_dot; for n > 32, 32 partial sums,
- * partial l over the indices j = l (mod 32) in increasing order, each term
- * with one rounding (fma), then added pairwise in a fixed tree: partial l
- * with partial l + 16 (l < 16), then l with l + 8 (l < 8), l + 4, l + 2,
- * l + 1.  The paper fixes these sums only in exact terms; this order lets
- * 32 lanes form one sum. */
+ * y^T H y) in the library order: for n <= 32 as zo_dot; for n > 32, 32
+ * partial sums, partial l over the indices j = l (mod 32) in increasing
+ * order, each term with one rounding (fma), then added pairwise in a fixed
+ * tree: partial l with partial l + 16 (l < 16), then l with l + 8 (l < 8),
+ * l + 4, l + 2, l + 1.  This order lets 32 lanes form one sum. */
 static double zo_bdot(int n, const double *a, const double *b)
 {
     if (n <= 32) return zo_dot(n, a, b);
@@ -640,44 +687,64 @@ static double zo_bdot(int n, const double *a, const double *b)
     return p[0];
 }
 
-/* zo_bdot for the tests */
-double zo_dot_split(int n, const double *a, const double *b) { return zo_bdot(n, a, b); }
-
-/* out = M v for row-major M [d][d] (rows as zo_dot) */
-static void zo_matvec(int d, const double *M, const double *v, double *out)
+/* a step dot product in the given order */
+static double zo_sdot(int n, const double *a, const double *b, int ord)
 {
-    for (int r = 0; r < d; ++r) out[r] = zo_dot(d, M + (size_t)r * d, v);
+    return ord == ZO_ORDER_PLAIN ? zo_pdot(n, a, b) : zo_bdot(n, a, b);
+}
+
+/* zo_bdot and zo_pdot for the tests */
+double zo_dot_split(int n, const double *a, const double *b) { return zo_bdot(n, a, b); }
+double zo_dot_plain(int n, const double *a, const double *b) { return zo_pdot(n, a, b); }
+
+/* out = M v for row-major M [d][d], each row one chain in index order
+ * (fma per term in the library order, plain otherwise) */
+static void zo_matvec(int d, const double *M, const double *v, double *out, int ord)
+{
+    for (int r = 0; r < d; ++r)
+        out[r] = ord == ZO_ORDER_PLAIN ? zo_pdot(d, M + (size_t)r * d, v)
+                                       : zo_dot(d, M + (size_t)r * d, v);
 }
 
 /* ------------------------------------------------------------------------ */
 /* Inverse-Hessian rank-two update (the update formula of Alg. 4).           */
 /* The printed product form (I - rho s y^T) H (I - rho y s^T) + rho s s^T    */
 /* expands, for symmetric H, to                                              */
-/*   H - rho (Hy s^T + s (Hy)^T) + (rho^2 y^T H y + rho) s s^T,              */
-/* whose element (r, c) regroups as H_rc + s_c A_r + (Hy)_c B_r with         */
-/*   A_r = beta s_r - rho (Hy)_r,  B_r = -rho s_r,  beta = rho^2 y^T H y + rho.*/
-/* Reading: each element takes two fused multiply-adds,                      */
-/*   H_rc <- fma(s_c, A_r, fma((Hy)_c, B_r, H_rc)),                          */
-/* and A_r = fma(beta, s_r, -(rho (Hy)_r)).  Returns 1 if applied.  Reading: */
-/* skipped when y^T s <= 1e-12 |s| |y|.                                      */
+/*   H - rho (Hy s^T + s (Hy)^T) + (rho^2 y^T H y + rho) s s^T.              */
+/* Plain order: every element (r, c) of the whole matrix from that           */
+/* expression as written, each operation rounded on its own:                 */
+/*   H_rc <- (H_rc - rho ((Hy)_r s_c + s_r (Hy)_c)) + beta (s_r s_c),        */
+/* beta = rho^2 y^T H y + rho (H stays symmetric: the expression is).        */
+/* Library order: the element regrouped as H_rc + s_c A_r + (Hy)_c B_r with  */
+/*   A_r = beta s_r - rho (Hy)_r,  B_r = -rho s_r,                           */
+/* two fused multiply-adds, H_rc <- fma(s_c, A_r, fma((Hy)_c, B_r, H_rc)),   */
+/* A_r = fma(beta, s_r, -(rho (Hy)_r)), over the elements r <= c, mirrored.  */
+/* Reading: skipped when y^T s <= 1e-12 |s| |y|.  Returns 1 if applied.      */
 /* ------------------------------------------------------------------------ */
 
-int zo_bfgs_update(int d, double *H, const double *s, const double *y)
+int zo_bfgs_update_ord(int d, double *H, const double *s, const double *y, int ord)
 {
-    const double sy = zo_bdot(d, y, s), ss = zo_bdot(d, s, s), yy = zo_bdot(d, y, y);
+    const double sy = zo_sdot(d, y, s, ord), ss = zo_sdot(d, s, s, ord),
+                 yy = zo_sdot(d, y, y, ord);
     if (!(sy > 1e-12 * sqrt(ss) * sqrt(yy))) return 0;
     double rho = 1.0 / sy;
     double *Hy = (double *)malloc(sizeof(double) * (size_t)d * 3);
     double *A = Hy + d, *B = Hy + 2 * d;
-    zo_matvec(d, H, y, Hy);
-    const double yHy = zo_bdot(d, y, Hy);
+    zo_matvec(d, H, y, Hy, ord);
+    const double yHy = zo_sdot(d, y, Hy, ord);
     const double beta = rho * rho * yHy + rho;
+    if (ord == ZO_ORDER_PLAIN) {
+        for (int r = 0; r < d; ++r)
+            for (int c = 0; c < d; ++c)
+                H[r * d + c] = H[r * d + c] - rho * (Hy[r] * s[c] + s[r] * Hy[c])
+                               + beta * (s[r] * s[c]);
+        free(Hy);
+        return 1;
+    }
     for (int r = 0; r < d; ++r) {
         A[r] = fma(beta, s[r], -(rho * Hy[r]));
         B[r] = -(rho * s[r]);
     }
-    /* Reading: H is symmetric in exact arithmetic; the elements r <= c are
-     * formed and mirrored, so H stays exactly symmetric */
     for (int r = 0; r < d; ++r)
         for (int c = r; c < d; ++c) {
             const double v = fma(s[c], A[r], fma(Hy[c], B[r], H[r * d + c]));
@@ -688,47 +755,68 @@ int zo_bfgs_update(int d, double *H, const double *s, const double *y)
     return 1;
 }
 
+int zo_bfgs_update(int d, double *H, const double *s, const double *y)
+{
+    return zo_bfgs_update_ord(d, H, s, y, ZO_ORDER_LIB);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Limited-memory direction (L-BFGS, the paper's future work, Section VI):   */
 /* the two-loop recursion of Nocedal & Wright, Numerical Optimization,       */
 /* Alg. 7.4, over the n stored pairs (s_i, y_i), oldest first, with         */
 /* rho_i = 1 / y_i's_i and the initial matrix gamma I, gamma = s'y / y'y of  */
 /* the newest pair (their eq. 7.20; 1 when no pair is stored).  Returns      */
-/* p = -H g in p.  Dot products as zo_dot; each update of q and r is one     */
-/* fused multiply-add per element.                                           */
+/* p = -H g in p.  Library order: dot products as zo_dot, each update of q   */
+/* and r one fused multiply-add per element; plain order: plain dot          */
+/* products, each product and sum of an update rounded on its own.           */
 /* ------------------------------------------------------------------------ */
 
-void zo_lbfgs_direction(int d, int n, const double *S, const double *Y, const double *rho,
-                        const double *g, double *p)
+void zo_lbfgs_direction_ord(int d, int n, const double *S, const double *Y, const double *rho,
+                            const double *g, double *p, int ord)
 {
+    const int plain = ord == ZO_ORDER_PLAIN;
     double *q = (double *)malloc(sizeof(double) * (size_t)(d > 0 ? d : 1));
     double *al = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     for (int j = 0; j < d; ++j) q[j] = g[j];
     for (int i = n - 1; i >= 0; --i) {
-        al[i] = rho[i] * zo_dot(d, S + (size_t)i * d, q);
-        for (int j = 0; j < d; ++j) q[j] = fma(-al[i], Y[(size_t)i * d + j], q[j]);
+        const double *si = S + (size_t)i * d, *yi = Y + (size_t)i * d;
+        al[i] = rho[i] * (plain ? zo_pdot(d, si, q) : zo_dot(d, si, q));
+        for (int j = 0; j < d; ++j)
+            q[j] = plain ? q[j] - al[i] * yi[j] : fma(-al[i], yi[j], q[j]);
     }
     double gamma = 1.0;
     if (n > 0) {
         const double *sn = S + (size_t)(n - 1) * d, *yn = Y + (size_t)(n - 1) * d;
-        gamma = zo_dot(d, sn, yn) / zo_dot(d, yn, yn);
+        gamma = plain ? zo_pdot(d, sn, yn) / zo_pdot(d, yn, yn)
+                      : zo_dot(d, sn, yn) / zo_dot(d, yn, yn);
     }
     for (int j = 0; j < d; ++j) q[j] = gamma * q[j];  /* r = gamma q, in place */
     for (int i = 0; i < n; ++i) {
-        const double b = rho[i] * zo_dot(d, Y + (size_t)i * d, q);
-        for (int j = 0; j < d; ++j) q[j] = fma(al[i] - b, S[(size_t)i * d + j], q[j]);
+        const double *si = S + (size_t)i * d, *yi = Y + (size_t)i * d;
+        const double b = rho[i] * (plain ? zo_pdot(d, yi, q) : zo_dot(d, yi, q));
+        for (int j = 0; j < d; ++j)
+            q[j] = plain ? q[j] + (al[i] - b) * si[j] : fma(al[i] - b, si[j], q[j]);
     }
     for (int j = 0; j < d; ++j) p[j] = -q[j];
     free(q);
     free(al);
 }
 
+void zo_lbfgs_direction(int d, int n, const double *S, const double *Y, const double *rho,
+                        const double *g, double *p)
+{
+    zo_lbfgs_direction_ord(d, n, S, Y, rho, g, p, ZO_ORDER_LIB);
+}
+
 /* Stores the pair (s, y) as the newest of at most m (the oldest is dropped)
  * if it passes the curvature test of zo_bfgs_update; returns 1 if stored. */
 static int zo_lbfgs_push(int d, int m, int *n, double *S, double *Y, double *rho,
-                         const double *s, const double *y)
+                         const double *s, const double *y, int ord)
 {
-    const double sy = zo_dot(d, y, s), ss = zo_dot(d, s, s), yy = zo_dot(d, y, y);
+    const int plain = ord == ZO_ORDER_PLAIN;
+    const double sy = plain ? zo_pdot(d, y, s) : zo_dot(d, y, s);
+    const double ss = plain ? zo_pdot(d, s, s) : zo_dot(d, s, s);
+    const double yy = plain ? zo_pdot(d, y, y) : zo_dot(d, y, y);
     if (!(sy > 1e-12 * sqrt(ss) * sqrt(yy))) return 0;
     if (*n == m) {  /* drop the oldest */
         memmove(S, S + d, sizeof(double) * (size_t)(m - 1) * d);
@@ -741,6 +829,30 @@ static int zo_lbfgs_push(int d, int m, int *n, double *S, double *Y, double *rho
     rho[*n] = 1.0 / sy;
     *n += 1;
     return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Search direction of Alg. 4: p = -H g and ddir = g^T p.  Reading: when p   */
+/* is not a descent direction (ddir < 0 fails, which also catches NaN), H is  */
+/* reset to the identity and p = -g, ddir = g^T p recomputed.  Returns 1 if   */
+/* the reset was taken.                                                      */
+/* ------------------------------------------------------------------------ */
+
+int zo_direction(int d, double *H, const double *g, double *p, double *ddir, int ord)
+{
+    zo_matvec(d, H, g, p, ord);
+    for (int r = 0; r < d; ++r) p[r] = -p[r];
+    double dd = zo_sdot(d, g, p, ord);
+    int reset = 0;
+    if (!(dd < 0.0)) {
+        for (int i = 0; i < d * d; ++i) H[i] = 0.0;
+        for (int i = 0; i < d; ++i) H[i * d + i] = 1.0;
+        for (int r = 0; r < d; ++r) p[r] = -g[r];
+        dd = zo_sdot(d, g, p, ord);
+        reset = 1;
+    }
+    *ddir = dd;
+    return reset;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -781,14 +893,15 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
     double *p = (double *)malloc(nb), *xn = (double *)malloc(nb);
     double *gn = (double *)malloc(nb), *s = (double *)malloc(nb);
     double *y = (double *)malloc(nb);
+    const int ord = pr->order;
     for (int i = 0; i < d; ++i) x[i] = x0[i];
     double f0;
-    zo_grad_forward(obj, d, x, &f0, g);
+    zo_grad_forward_ord(obj, d, x, &f0, g, ord);
     double margin = INFINITY;
     int k = 0, status = 0, n_feval = 0;
     double gnorm = NAN;
     for (;;) {
-        gnorm = sqrt(zo_bdot(d, g, g));
+        gnorm = sqrt(zo_sdot(d, g, g, ord));
         if (k >= pr->bfgs_max_iters) { status = 0; break; }
         if (stop && *stop) { status = 2; break; }
         if (!isfinite(f0) || !finite_vec(d, g)) { status = 3; break; }
@@ -809,40 +922,35 @@ void zo_bfgs(const zo_problem *pr, const double *x0, double *x_out,
             if (stop) *stop = 1;
             break;
         }
-        /* p = -H g, ddir = g^T p */
+        /* p = -H g, ddir = g^T p (reading: a non-descent direction restarts
+         * from H = I, p = -g; L-BFGS forgets its stored pairs) */
+        double ddir;
         if (m > 0) {
-            zo_lbfgs_direction(d, n_pairs, S, Y, rho, g, p);
-        } else {
-            zo_matvec(d, H, g, p);
-            for (int r = 0; r < d; ++r) p[r] = -p[r];
-        }
-        double ddir = zo_bdot(d, g, p);
-        if (!(ddir < 0.0)) {
-            /* Reading: non-descent direction -> restart from H = I (L-BFGS:
-             * forget the stored pairs) */
-            if (H) {
-                for (int i = 0; i < d * d; ++i) H[i] = 0.0;
-                for (int i = 0; i < d; ++i) H[i * d + i] = 1.0;
+            zo_lbfgs_direction_ord(d, n_pairs, S, Y, rho, g, p, ord);
+            ddir = zo_sdot(d, g, p, ord);
+            if (!(ddir < 0.0)) {
+                n_pairs = 0;
+                for (int r = 0; r < d; ++r) p[r] = -g[r];
+                ddir = zo_sdot(d, g, p, ord);
             }
-            n_pairs = 0;
-            for (int r = 0; r < d; ++r) p[r] = -g[r];
-            ddir = zo_bdot(d, g, p);
+        } else {
+            zo_direction(d, H, g, p, &ddir, ord);
         }
         int accepted = 0;
-        double alpha = zo_line_search(obj, d, x, p, f0, ddir, pr->armijo_c,
-                                      pr->backtrack, pr->ls_max_iters, xn,
-                                      &accepted, &n_feval, &margin);
+        double alpha = zo_line_search_ord(obj, d, x, p, f0, ddir, pr->armijo_c,
+                                          pr->backtrack, pr->ls_max_iters, xn,
+                                          &accepted, &n_feval, &margin, ord);
         for (int j = 0; j < d; ++j) xn[j] = x[j] + alpha * p[j];
         double fn;
-        zo_grad_forward(obj, d, xn, &fn, gn);
+        zo_grad_forward_ord(obj, d, xn, &fn, gn, ord);
         for (int j = 0; j < d; ++j) {
             s[j] = xn[j] - x[j];
             y[j] = gn[j] - g[j];
         }
         if (m > 0)
-            zo_lbfgs_push(d, m, &n_pairs, S, Y, rho, s, y);
+            zo_lbfgs_push(d, m, &n_pairs, S, Y, rho, s, y, ord);
         else
-            zo_bfgs_update(d, H, s, y);
+            zo_bfgs_update_ord(d, H, s, y, ord);
         for (int j = 0; j < d; ++j) { x[j] = xn[j]; g[j] = gn[j]; }
         f0 = fn;
         ++k;
@@ -898,13 +1006,14 @@ int64_t zo_solve(const zo_problem *pr, double *x, double *v, double *px,
 /* with exact steps BFGS terminates on a quadratic in at most d iterations   */
 /* and H_d = A^{-1} (Nocedal & Wright, Numerical Optimization, Thm. 6.4 /    */
 /* the quadratic-termination property of the Broyden class).  Uses the same  */
-/* zo_bfgs_update as the main path.  Returns the iterations taken; H is      */
+/* zo_bfgs_update_ord as the main path, in the order asked for.  Returns the  */
+/* iterations taken; H is                                                    */
 /* left in H_out.                                                            */
 /* ------------------------------------------------------------------------ */
 
 int zo_bfgs_quadratic_exact(int d, const double *A, const double *x0,
                             int max_iters, double tol, double *x_out,
-                            double *H_out)
+                            double *H_out, int ord)
 {
     size_t nb = sizeof(double) * (size_t)d;
     double *x = (double *)malloc(nb), *g = (double *)malloc(nb);
@@ -943,7 +1052,7 @@ int zo_bfgs_quadratic_exact(int d, const double *A, const double *x0,
             x[r] = x[r] + s[r];
             y[r] = alpha * Ap[r];     /* y = A s */
         }
-        zo_bfgs_update(d, H, s, y);
+        zo_bfgs_update_ord(d, H, s, y, ord);
         ++k;
     }
     for (int i = 0; i < d; ++i) x_out[i] = x[i];

@@ -1,5 +1,8 @@
 """Pins of the oracle's line search (Alg. 6), inverse-Hessian update and
 BFGS loop (Alg. 4), and of the whole method (Alg. 7) on small cases.
+Tests that take `order` run in both rounding orders of the oracle (the
+library order and the plain order: every operation rounded on its own,
+sums left to right, the update over the whole matrix).
 """
 import math
 
@@ -48,18 +51,20 @@ def _spd(rng, d):
     return m @ m.T + d * np.eye(d)
 
 
-def test_update_secant_symmetry_and_product_form(oracle_mod):
+@pytest.mark.parametrize("order", [0, 1])
+def test_update_secant_symmetry_and_product_form(oracle_mod, order):
     rng = np.random.default_rng(3)
     for d in (1, 2, 5, 8, 40):
         for _ in range(10):
             H = np.linalg.inv(_spd(rng, d))
+            H = (H + H.T) / 2  # exactly symmetric, as every H of a run is
             s = rng.normal(size=d)
             y = _spd(rng, d) @ s  # y^T s > 0
-            Hn, ok = oracle_mod.bfgs_update(H, s, y)
+            Hn, ok = oracle_mod.bfgs_update(H, s, y, order=order)
             assert ok
             # secant condition H+ y = s
             assert np.abs(Hn @ y - s).max() <= 1e-10 * max(1.0, np.abs(s).max())
-            assert np.array_equal(Hn, Hn.T)  # the upper triangle, mirrored
+            assert np.array_equal(Hn, Hn.T)  # mirrored, or symmetric by its expression
             assert np.linalg.eigvalsh((Hn + Hn.T) / 2).min() > 0
             # the product form printed in Alg. 4
             rho = 1.0 / (y @ s)
@@ -68,22 +73,24 @@ def test_update_secant_symmetry_and_product_form(oracle_mod):
             assert np.abs(Hn - P).max() <= 1e-11 * max(1.0, np.abs(P).max())
 
 
-def test_update_skipped_without_curvature(oracle_mod):
+@pytest.mark.parametrize("order", [0, 1])
+def test_update_skipped_without_curvature(oracle_mod, order):
     H = np.eye(3)
     s = np.array([1.0, 0.0, 0.0])
     for y in (np.array([-1.0, 0.5, 0.0]), np.zeros(3), np.array([0.0, 1.0, 0.0])):
-        Hn, ok = oracle_mod.bfgs_update(H, s, y)
+        Hn, ok = oracle_mod.bfgs_update(H, s, y, order=order)
         assert not ok and np.array_equal(Hn, H)
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("d", [2, 3, 6, 12, 20, 40, 64])  # 40, 64: the split dot order
-def test_quadratic_termination_exact_steps(oracle_mod, d):
+def test_quadratic_termination_exact_steps(oracle_mod, d, order):
     # with exact line searches BFGS minimises 0.5 x^T A x in at most d steps
     # and ends with H = A^{-1} (quadratic termination of the Broyden class)
     rng = np.random.default_rng(d)
     A = _spd(rng, d)
     x0 = rng.normal(size=d)
-    k, x, H = oracle_mod.bfgs_quadratic_exact(A, x0, max_iters=5 * d, tol=1e-9)
+    k, x, H = oracle_mod.bfgs_quadratic_exact(A, x0, max_iters=5 * d, tol=1e-9, order=order)
     assert k <= d
     assert np.abs(A @ x).max() < 1e-9
     if k == d:
@@ -93,15 +100,17 @@ def test_quadratic_termination_exact_steps(oracle_mod, d):
 
 # --------------------------------------------------------------- BFGS loop
 
-def test_identity_quadratic_one_step(oracle_mod):
+@pytest.mark.parametrize("order", [0, 1])
+def test_identity_quadratic_one_step(oracle_mod, order):
     # f = 0.5 x^2 (d = 1): p = -g = -x, alpha = 1 lands on 0 exactly
-    p = oracle_mod.Problem("quadratic", dim=1, bfgs_max_iters=50)
+    p = oracle_mod.Problem("quadratic", dim=1, bfgs_max_iters=50, order=order)
     r = oracle_mod.bfgs(p, [3.5])
     assert r["status"] == 1 and r["iters"] == 1 and r["x"][0] == 0.0 and r["f"] == 0.0
 
 
-def test_rosenbrock_classic_start(oracle_mod):
-    p = oracle_mod.Problem("rosenbrock", dim=2, bfgs_max_iters=100)
+@pytest.mark.parametrize("order", [0, 1])
+def test_rosenbrock_classic_start(oracle_mod, order):
+    p = oracle_mod.Problem("rosenbrock", dim=2, bfgs_max_iters=100, order=order)
     r = oracle_mod.bfgs(p, [-1.2, 1.0])
     assert r["status"] == 1 and r["gnorm"] < 1e-8
     assert np.linalg.norm(r["x"] - 1.0) < 1e-6  # Euclidean criterion, Section V-A
@@ -134,13 +143,14 @@ def test_ackley_never_meets_gradient_test_near_zero(oracle_mod):
     assert r["status"] == 0 and r["f"] < 1e-3
 
 
-def test_iterates_decrease_f(oracle_mod):
+@pytest.mark.parametrize("order,d", [(0, 10), (1, 10), (0, 40), (1, 40)])
+def test_iterates_decrease_f(oracle_mod, order, d):
     rng = np.random.default_rng(9)
-    x0 = rng.uniform(-5.12, 5.12, size=(32, 10))
+    x0 = rng.uniform(-5.12, 5.12, size=(32, d))
     for K in (1, 2, 5, 10):
-        p = oracle_mod.Problem("rastrigin", dim=10, bfgs_max_iters=K, n_threads=2)
+        p = oracle_mod.Problem("rastrigin", dim=d, bfgs_max_iters=K, n_threads=2, order=order)
         r = oracle_mod.bfgs_many(p, x0)
-        f0 = np.array([oracle_mod.f("rastrigin", xi) for xi in x0])
+        f0 = np.array([oracle_mod.f("rastrigin", xi, order=order) for xi in x0])
         assert np.all(r["f"] <= f0)
 
 
@@ -166,10 +176,12 @@ def _grid_min(fn, lo, hi, n):
     ("goldstein_price", -2.0, 2.0, lambda X, Y: (1 + (X + Y + 1) ** 2 * (19 - 14 * X + 3 * X**2 - 14 * Y + 6 * X * Y + 3 * Y**2))
      * (30 + (2 * X - 3 * Y) ** 2 * (18 - 32 * X + 12 * X**2 + 48 * Y - 36 * X * Y + 27 * Y**2))),
 ])
-def test_two_dimensional_brute_force(oracle_mod, obj, lo, hi, fn):
+@pytest.mark.parametrize("order", [0, 1])
+def test_two_dimensional_brute_force(oracle_mod, obj, lo, hi, fn, order):
     # a 2001 x 2001 grid over the box (containing the minimiser) bounds the
     # global minimum from above; the method must do at least as well
     gmin = _grid_min(fn, lo, hi, 2001)
-    p = oracle_mod.Problem(obj, dim=2, lower=lo, upper=hi, n_starts=256, pso_iters=5, bfgs_max_iters=200, seed=1)
+    p = oracle_mod.Problem(obj, dim=2, lower=lo, upper=hi, n_starts=256, pso_iters=5, bfgs_max_iters=200,
+                           seed=1, order=order)
     r = oracle_mod.solve(p)
     assert r["f"][r["best"]] <= gmin + 1e-9

@@ -33,12 +33,13 @@ def _explicit(S, Y, g):
     return -H @ g
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("d,n", [(1, 1), (3, 2), (6, 6), (10, 4), (17, 8)])
-def test_two_loop_equals_the_explicit_bfgs_matrix(oracle_mod, d, n):
+def test_two_loop_equals_the_explicit_bfgs_matrix(oracle_mod, d, n, order):
     rng = np.random.default_rng(100 * d + n)
     S, Y = _pairs(rng, d, n)
     g = rng.normal(size=d)
-    p = oracle_mod.lbfgs_direction(S, Y, g)
+    p = oracle_mod.lbfgs_direction(S, Y, g, order=order)
     q = _explicit(S, Y, g)
     assert np.abs(p - q).max() <= 1e-10 * max(1.0, np.abs(q).max())
 
@@ -48,20 +49,22 @@ def test_no_pairs_gives_steepest_descent(oracle_mod):
     assert np.array_equal(oracle_mod.lbfgs_direction(np.zeros((0, 3)), np.zeros((0, 3)), g), -g)
 
 
-def test_secant_condition_of_the_newest_pair(oracle_mod):
+@pytest.mark.parametrize("order", [0, 1])
+def test_secant_condition_of_the_newest_pair(oracle_mod, order):
     # H maps the newest y to its s: the direction for g = -y is s
     rng = np.random.default_rng(7)
     S, Y = _pairs(rng, 8, 5)
-    p = oracle_mod.lbfgs_direction(S, Y, -Y[-1])
+    p = oracle_mod.lbfgs_direction(S, Y, -Y[-1], order=order)
     assert np.abs(p - S[-1]).max() <= 1e-10 * np.abs(S[-1]).max()
 
 
 @pytest.mark.parametrize("obj,d,lo,hi", [("rosenbrock", 20, -2.0, 2.0), ("quadratic", 30, -3.0, 3.0),
                                          ("rastrigin", 6, -0.4, 0.4), ("ackley", 12, -0.3, 0.3)])
-def test_lbfgs_reaches_the_known_minimum(oracle_mod, obj, d, lo, hi):
+@pytest.mark.parametrize("order", [0, 1])
+def test_lbfgs_reaches_the_known_minimum(oracle_mod, obj, d, lo, hi, order):
     # the closed-form minima (Rosenbrock chain 0 at 1; the others 0 at 0)
     p = oracle_mod.Problem(objective=obj, dim=d, lower=lo, upper=hi, n_starts=8, pso_iters=2,
-                           bfgs_max_iters=2000, lbfgs_m=6, seed=3)
+                           bfgs_max_iters=2000, lbfgs_m=6, seed=3, order=order)
     r = oracle_mod.solve(p)
     b = r["best"]
     assert r["f"][b] < 1e-10
