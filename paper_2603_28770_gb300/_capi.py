@@ -24,7 +24,7 @@ OBJECTIVES = {"rosenbrock": 0, "rastrigin": 1, "ackley": 2, "goldstein_price": 3
 OBJ_USER = 200  # objective id of user objective k: OBJ_USER + k (include/zeus_user.cuh)
 PRECISIONS = {"fp64": 0, "fp32_guarded": 1}
 GRAD_MODES = {"forward": 0, "adjoint": 1}
-RUN_STATUS = {0: "max_iter", 1: "converged", 2: "stopped", 3: "nonfinite"}
+RUN_STATUS = {0: "max_iter", 1: "converged", 2: "stopped", 3: "nonfinite", 4: "stalled"}
 
 
 class zeus_problem(C.Structure):
@@ -106,6 +106,7 @@ _lock = threading.Lock()
 SIGNATURES = {
     "zeus_strerror": (C.c_char_p, [C.c_int]),
     "zeus_abi_version": (C.c_int, []),
+    "zeus_set_wait_limit": (C.c_int, [C.c_uint32]),
     "zeus_default_problem": (C.c_int, [C.POINTER(zeus_problem)]),
     "zeus_validate": (C.c_int, [C.POINTER(zeus_problem)]),
     "zeus_workspace_size": (C.c_int, [C.POINTER(zeus_problem), C.POINTER(C.c_size_t)]),

@@ -62,9 +62,9 @@ __global__ void __launch_bounds__(kWideThreads)
 // early run on blocks that have no tile while the tiles are still in
 // progress.  Servers poll for entries while a tile may still produce one;
 // the launch is cooperative, so every block is resident and the polls
-// end.  Each poll loop is bounded (then the error word is set and the
-// block stops serving).
-constexpr unsigned kFusedSpinLimit = 1u << 23;  // polls of 256 ns: about 2 s
+// end.  Each poll loop is bounded by `spin_limit` polls of about 256 ns
+// (zeus_set_wait_limit; then the error word is set and the block stops
+// serving).
 
 __device__ __forceinline__ int smid_of() {
     unsigned r;
@@ -73,10 +73,11 @@ __device__ __forceinline__ int smid_of() {
 }
 
 // waits (bounded) until entry `slot` is marked written
-__device__ __forceinline__ bool wait_ready(const Queue& q, int slot, Ctrl* ctrl) {
+__device__ __forceinline__ bool wait_ready(const Queue& q, int slot, Ctrl* ctrl,
+                                           unsigned spin_limit) {
     volatile int* rd = q.ready + slot;
     for (unsigned spin = 0; !*rd; ++spin) {
-        if (spin >= kFusedSpinLimit) {
+        if (spin >= spin_limit) {
             atomicExch(&ctrl->error, 1);
             return false;
         }
@@ -89,12 +90,13 @@ __device__ __forceinline__ bool wait_ready(const Queue& q, int slot, Ctrl* ctrl)
 // *count if a producer has claimed it (it is then written shortly: waits
 // for its flag); -1 if there is none now.  Never waits for production.
 __device__ __forceinline__ int claim_now(unsigned* head, unsigned* count, int base, int cap_r,
-                                         const Queue& q, Ctrl* ctrl) {
+                                         const Queue& q, Ctrl* ctrl, unsigned spin_limit) {
     for (;;) {
         const unsigned h = *((volatile unsigned*)head);
         const unsigned c = min(*((volatile unsigned*)count), (unsigned)cap_r);
         if (h >= c) return -1;
-        if (atomicCAS(head, h, h + 1) == h) return wait_ready(q, base + (int)h, ctrl) ? base + (int)h : -1;
+        if (atomicCAS(head, h, h + 1) == h)
+            return wait_ready(q, base + (int)h, ctrl, spin_limit) ? base + (int)h : -1;
     }
 }
 
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(kWideThreads)
                       const int n_tiles, const int W, const double* x0, double* x_out,
                       double* __restrict__ f_out, double* __restrict__ gnorm_out,
                       int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
-                      Ctrl* __restrict__ ctrl, const Queue q) {
+                      Ctrl* __restrict__ ctrl, const Queue q, const unsigned spin_limit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ WideShared sh;
     const int tid = wide_role(blockDim.x);
@@ -144,20 +146,20 @@ __global__ void __launch_bounds__(kWideThreads)
             for (unsigned spin = 0;; ++spin) {
                 if (q.long_cap > 0 && sm < kMaxSMs && atomicCAS(q.sm_long + sm, 0, 1) == 0) {
                     item = claim_now(&ctrl->q_head_long, &ctrl->q_count_long, lbase, q.long_cap, q,
-                                     ctrl);
+                                     ctrl, spin_limit);
                     if (item >= 0) {
                         held = 1;
                         break;
                     }
                     atomicExch(q.sm_long + sm, 0);
                 }
-                item = claim_now(&ctrl->q_head, &ctrl->q_count, 0, ncap, q, ctrl);
+                item = claim_now(&ctrl->q_head, &ctrl->q_count, 0, ncap, q, ctrl, spin_limit);
                 if (item >= 0) break;
                 if (*((volatile unsigned*)&ctrl->tiles_done) >= (unsigned)n_tiles) {
                     __threadfence();  // the counts are final now
                     if (q.long_cap > 0) {
                         item = claim_now(&ctrl->q_head_long, &ctrl->q_count_long, lbase, q.long_cap,
-                                         q, ctrl);
+                                         q, ctrl, spin_limit);
                         if (item >= 0) break;
                     }
                     if (drained(&ctrl->q_head, &ctrl->q_count, ncap) &&
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(kWideThreads)
                          drained(&ctrl->q_head_long, &ctrl->q_count_long, q.long_cap)))
                         break;
                 }
-                if (spin >= kFusedSpinLimit) {
+                if (spin >= spin_limit) {
                     atomicExch(&ctrl->error, 1);
                     break;
                 }
@@ -222,7 +224,9 @@ static cudaError_t fused_go(const zeus_problem& p, const BfgsLaunch& L, const do
     Queue qq = q;
     // long entries: half of the queue (and the per-SM table)
     qq.long_cap = (q.sm_long && sms <= kMaxSMs) ? q.cap / 2 : 0;
-    void* args[] = {&pp, &stride, &budget, &tile, &n_tiles, &W, &xin, &xo, &fo, &go, &so, &io, &c, &qq};
+    unsigned spin_limit = wait_limit();
+    void* args[] = {&pp,  &stride, &budget, &tile, &n_tiles, &W, &xin, &xo,
+                    &fo,  &go,     &so,     &io,   &c,       &qq, &spin_limit};
     return cudaLaunchCooperativeKernel((const void*)kf, dim3(sms * per_sm), dim3(kWideThreads), args,
                                        smem, st);
 }

@@ -7,10 +7,19 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "zeus.h"
 #include "zeus_internal.h"
 
 using namespace zeus;
+
+namespace zeus {
+namespace {
+std::atomic<unsigned> g_wait_polls{kDefaultWaitPolls};
+}
+unsigned wait_limit() { return g_wait_polls.load(std::memory_order_relaxed); }
+}  // namespace zeus
 
 namespace {
 
@@ -165,6 +174,11 @@ const char* zeus_strerror(int code) {
 }
 
 int zeus_abi_version(void) { return ZEUS_ABI_VERSION; }
+
+int zeus_set_wait_limit(uint32_t polls) {
+    g_wait_polls.store(polls ? (unsigned)polls : kDefaultWaitPolls, std::memory_order_relaxed);
+    return ZEUS_OK;
+}
 
 int zeus_default_problem(zeus_problem* p) {
     if (!p) return ZEUS_EINVAL;
@@ -497,10 +511,14 @@ int zeus_solve_host(zeus_context* ctx, const zeus_problem* p, double* x_out, dou
         e = cudaMemcpyAsync(status_out, ctx->st, n * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && iters_out)
         e = cudaMemcpyAsync(iters_out, ctx->it, n * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && result)
-        e = cudaMemcpyAsync(result, ctx->res, sizeof(zeus_result), cudaMemcpyDeviceToHost, st);
+    // the summary always comes back: its error word says whether a bounded
+    // device wait gave up (the outputs are then incomplete)
+    zeus_result local;
+    zeus_result* r = result ? result : &local;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r, ctx->res, sizeof(zeus_result), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e);
+    return r->error ? ZEUS_ETIMEOUT : ZEUS_OK;
 }
 
 }  // extern "C"

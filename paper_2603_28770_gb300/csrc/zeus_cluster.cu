@@ -32,7 +32,7 @@ namespace zeus {
 constexpr int kClusterThreads = 256;
 constexpr int kClusterMaxBlocks = 1024;
 constexpr int kOpen = -3;                      // a candidate not yet in a cluster
-constexpr unsigned kBarSpinLimit = 1u << 23;   // polls of 256 ns: about 2 s
+
 
 struct ClusterPart {
     double f;
@@ -140,7 +140,7 @@ __device__ __forceinline__ void block_count_max(long long& c, double& m, Cluster
 // block to arrive resets the count and advances the generation; the others
 // poll the generation (bounded: on timeout the error word is set).  Returns
 // false once the error word is set.
-__device__ __forceinline__ bool grid_barrier(ClusterWork* w, unsigned nblocks) {
+__device__ __forceinline__ bool grid_barrier(ClusterWork* w, unsigned nblocks, unsigned spin_limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned* gen = &w->bar_gen;
@@ -152,7 +152,7 @@ __device__ __forceinline__ bool grid_barrier(ClusterWork* w, unsigned nblocks) {
             atomicAdd(&w->bar_gen, 1u);
         } else {
             for (unsigned spin = 0; *gen == g; ++spin) {
-                if (spin >= kBarSpinLimit || *((volatile int*)&w->error)) {
+                if (spin >= spin_limit || *((volatile int*)&w->error)) {
                     atomicExch(&w->error, 1);
                     break;
                 }
@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(kClusterThreads)
                    const double* __restrict__ x, const double* __restrict__ f,
                    const int32_t* __restrict__ status, int32_t* __restrict__ label,
                    int32_t* __restrict__ leader_out, int32_t* __restrict__ count_out,
-                   zeus_cluster_result* __restrict__ res, ClusterWork* __restrict__ w) {
+                   zeus_cluster_result* __restrict__ res, ClusterWork* __restrict__ w,
+                   const unsigned spin_limit) {
     __shared__ ClusterShared sh;
     int* leader = reinterpret_cast<int*>(w + 1);
     int* count = leader + cp.max_clusters;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(kClusterThreads)
             part[blockIdx.x].f = bf;
             part[blockIdx.x].i = bi;
         }
-        ok = grid_barrier(w, G);
+        ok = grid_barrier(w, G, spin_limit);
         if (!ok) break;
         bf = INFINITY;
         bi = -1;
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kClusterThreads)
     }
     block_count_max(left, unused, sh);
     if (threadIdx.x == 0 && left) atomicAdd(&w->n_left, (unsigned long long)left);
-    if (ok) ok = grid_barrier(w, G);
+    if (ok) ok = grid_barrier(w, G, spin_limit);
     if (blockIdx.x != 0) return;
     // block 0 formed every leader entry; the counts are complete after the
     // barrier (read past L1)
@@ -463,7 +464,9 @@ cudaError_t launch_cluster(const zeus_cluster_params& cp, int n, int d, const do
     if (e != cudaSuccess) return e;
     zeus_cluster_params pp = cp;
     int nn = n, dd = d;
-    void* args[] = {&pp, &nn, &dd, &x, &f, &status, &label, &leader_out, &count_out, &res, &w};
+    unsigned spin_limit = wait_limit();
+    void* args[] = {&pp, &nn, &dd, &x, &f, &status, &label, &leader_out, &count_out, &res, &w,
+                    &spin_limit};
     return cudaLaunchCooperativeKernel((const void*)cluster_kernel, dim3((unsigned)blocks),
                                        dim3(kClusterThreads), args, 0, st);
 }

@@ -43,6 +43,11 @@ struct ArgPair {
 
 constexpr int kMaxReduceBlocks = 4096;  // argmin partials kept in the workspace
 
+// polls (of about 256 ns each) a bounded device wait makes before it gives
+// up; zeus_set_wait_limit sets it, 2^23 (about 2 s) by default
+constexpr unsigned kDefaultWaitPolls = 1u << 23;
+unsigned wait_limit();
+
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Workspace carve-up (offsets in bytes from the workspace base).
