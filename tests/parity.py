@@ -79,3 +79,66 @@ def clopper_pearson(k: int, n: int, level: float = 0.95):
     lo = 0.0 if k == 0 else float(beta.ppf(a, k, n - k + 1))
     hi = 1.0 if k == n else float(beta.ppf(1.0 - a, k + 1, n - k))
     return lo, hi
+
+
+# ---------------------------------------------------------------------------
+# Comparison with the oracle's plain rounding order.  The paper states the
+# arithmetic exactly; the plain order rounds every operation on its own and
+# shares no choice of order with the kernels.  Bar: after K iterations every
+# start agrees within 1e-9 relative (status and iteration count equal; x, f
+# and ||g|| within 1e-9), widened per start to ENVELOPE times the oracle's
+# own spread where the exact arithmetic does not pin the result to 1e-9: the
+# spread is how far the plain-order run moves when its start moves by one
+# ulp (either way).  Starts whose plain-order run passed a branch decision
+# (Armijo test, gradient test) within MARGIN_TOL relative may take the other
+# branch under any other rounding and are excused, counted and bounded.
+# Calibration on the oracle alone: its library-order runs fall inside this
+# bar on every start of every case of tests/test_gpu_plain_order.py.
+# ---------------------------------------------------------------------------
+MARGIN_TOL = 1e-12
+ENVELOPE = 20.0
+
+
+def rel_diff(a: dict, b: dict) -> np.ndarray:
+    """Per-start largest relative difference of x, f, ||g|| (inf if the
+    status or the iteration count differs)."""
+    xa, xb = np.asarray(a["x"]), np.asarray(b["x"])
+    r = np.abs(xa - xb).max(axis=1) / np.maximum(1.0, np.abs(xb).max(axis=1))
+    for k in ("f", "gnorm"):
+        va, vb = np.asarray(a[k], dtype=np.float64), np.asarray(b[k], dtype=np.float64)
+        dk = np.abs(va - vb) / np.maximum(1.0, np.abs(vb))
+        dk[np.isnan(va) & np.isnan(vb)] = 0.0
+        dk[np.isinf(va) & np.isinf(vb) & (np.sign(va) == np.sign(vb))] = 0.0
+        r = np.maximum(r, dk)
+    bad = (np.asarray(a["status"]) != np.asarray(b["status"])) | (np.asarray(a["iters"]) != np.asarray(b["iters"]))
+    r[bad] = np.inf
+    return r
+
+
+def plain_reference(ora, fields: dict, x0, **kw):
+    """Oracle runs in the plain order from x0, each start's spread (how far
+    the run moves under one-ulp moves of its start) and the starts excused
+    for a near-tie branch.  Returns (plain, spread, excused)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    pp = oracle_problem(ora, fields, order=ora.ORDER_PLAIN, **kw)
+    plain = ora.bfgs_many(pp, x0)
+    up = ora.bfgs_many(pp, np.nextafter(x0, np.inf))
+    dn = ora.bfgs_many(pp, np.nextafter(x0, -np.inf))
+    spread = np.maximum(rel_diff(up, plain), rel_diff(dn, plain))
+    excused = np.asarray(plain["margin"]) < MARGIN_TOL
+    return plain, spread, excused
+
+
+def compare_plain(gpu: dict, plain: dict, spread, excused, rtol=RTOL, max_excused=None):
+    """GPU against the plain order (bar above).  Returns (excused fraction,
+    fraction held to rtol itself)."""
+    r = rel_diff(gpu, plain)
+    bound = np.maximum(rtol, ENVELOPE * np.asarray(spread))
+    held = ~np.asarray(excused)
+    bad = np.flatnonzero(held & ~(r <= bound))
+    assert bad.size == 0, (f"{bad.size} of {int(held.sum())} starts differ from the plain order "
+                           f"beyond the bar, first {bad[:5]}: rel {r[bad[:5]]}, bound {bound[bad[:5]]}")
+    frac = float(np.mean(excused))
+    if max_excused is not None:
+        assert frac <= max_excused, f"{frac:.3f} of the starts excused (> {max_excused})"
+    return frac, float(np.mean(held & (bound <= rtol)))

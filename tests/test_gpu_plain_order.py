@@ -1,0 +1,173 @@
+"""Every BFGS kernel path against the oracle's plain rounding order (every
+operation rounded on its own, sums left to right, the whole-matrix update):
+an order that shares no design choice with the kernels.  Bar: the first 20
+iterations (bfgs_max_iters = 20) agree per start within 1e-9 relative
+(status and iteration count equal; x, f and ||g|| within 1e-9), widened to
+20 times the oracle's own spread (how far its run moves when the start
+moves by one ulp) where the exact arithmetic does not pin the result to
+1e-9; starts whose oracle run passed a branch decision within 1e-12
+relative are excused and counted (tests/parity.py).  Where no such ties
+occur (Rosenbrock chain, d = 256, the benchmark's large-d shapes) at most
+2 % of the starts may be excused."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2603_28770_gb300 import workloads
+from parity import compare_plain, oracle_problem, plain_reference, to_np, zeus_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def z():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2603_28770_gb300 as z
+    z.lib()
+    return z
+
+
+@pytest.fixture(scope="module")
+def ora():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+_REF = {}
+
+
+def _reference(ora, key, fields, x0, **kw):
+    if key not in _REF:
+        _REF[key] = plain_reference(ora, fields, x0, **kw)
+    return _REF[key]
+
+
+# (objective, d, starts, box, kernel layouts, max excused fraction)
+# layouts: 1 one lane per start, 128 one block per start (H in shared
+# memory), 0 automatic (lane tiles and the hand-over in one cooperative
+# launch at d <= 16), 256 one block per start with H streamed from HBM
+CASES = [
+    ("rastrigin", 10, 512, -5.12, 5.12, (1, 128, 0, 256), None),
+    ("ackley", 10, 512, -5.0, 5.0, (1, 128, 0, 256), None),
+    ("rosenbrock", 10, 512, -5.0, 5.0, (1, 128, 0, 256), None),
+    ("rastrigin", 40, 256, -5.12, 5.12, (128, 256), None),
+    ("ackley", 40, 256, -5.0, 5.0, (128, 256), None),
+    ("rosenbrock", 40, 256, -5.0, 5.0, (128, 256), 0.02),
+    ("rastrigin", 100, 128, -5.12, 5.12, (128, 256), None),
+    ("ackley", 100, 128, -5.0, 5.0, (128, 256), None),
+    ("rosenbrock", 100, 128, -5.0, 5.0, (128, 256), 0.02),
+    ("rastrigin", 256, 64, -5.12, 5.12, (256,), 0.02),
+    ("ackley", 256, 64, -5.0, 5.0, (256,), 0.02),
+    ("rosenbrock", 256, 64, -2.0, 2.0, (256,), 0.02),
+]
+PARAMS = [(o, d, n, lo, hi, lay, mx) for (o, d, n, lo, hi, lays, mx) in CASES for lay in lays]
+
+
+@pytest.mark.parametrize("obj,d,n,lo,hi,layout,max_excused", PARAMS)
+@pytest.mark.parametrize("grad", ["forward", "adjoint"])
+def test_kernels_against_plain_order(z, ora, obj, d, n, lo, hi, layout, max_excused, grad):
+    x0 = workloads.start_points(n, d, lo, hi, seed=1000 + d)
+    fields = dict(objective=obj, dim=d, lower=lo, upper=hi, n_starts=n, bfgs_max_iters=20)
+    plain, spread, excused = _reference(ora, (obj, d, n), fields, x0)
+    pz = zeus_problem(z, fields, threads_per_start=layout, grad_mode=grad)
+    plan = z.zeus_plan_info(pz)
+    assert plan["stream"] == (1 if layout == 256 else 0)
+    g = to_np(z.solve_from(pz, torch.from_numpy(x0).cuda()))
+    compare_plain(g, plain, spread, excused, max_excused=max_excused)
+    assert g["summary"]["total_iters"] == int(g["iters"].sum())
+
+
+def test_batch_against_plain_order(z, ora):
+    # one batch of mixed problems (d = 10, 40, 100; three objectives): the
+    # batch's PSO phase equals the oracle's (library order, bit for bit,
+    # tested elsewhere); BFGS from its final positions against the plain order
+    specs = [("rastrigin", 10), ("ackley", 40), ("rosenbrock", 100), ("rosenbrock", 10),
+             ("rastrigin", 100), ("ackley", 10)]
+    fields = []
+    for P, (obj, d) in enumerate(specs):
+        lo, hi = workloads.BOXES[obj]
+        fields.append(dict(objective=obj, dim=d, lower=lo, upper=hi, n_starts=96, pso_iters=3,
+                           bfgs_max_iters=20, seed=40 + P))
+    b = z.Batch([z.Problem(**f) for f in fields])
+    b.solve()
+    torch.cuda.synchronize()
+    for P, f in enumerate(fields):
+        sw = ora.pso(oracle_problem(ora, f))
+        plain, spread, excused = plain_reference(ora, f, sw["x"])
+        g = to_np(b.problem(P))
+        compare_plain(g, plain, spread, excused,
+                      max_excused=0.02 if f["objective"] == "rosenbrock" else None)
+
+
+@pytest.mark.parametrize("name,grad,n_sample", [("rosenbrock256d_n8192", "forward", 64),
+                                                ("rosenbrock1024d_n2048", "forward", 64),
+                                                ("rosenbrock1024d_n2048", "adjoint", 64),
+                                                ("ackley1024d_n2048", "forward", 32),
+                                                ("ackley1024d_n2048", "adjoint", 32)])
+def test_streamed_full_size_against_plain_order(z, ora, name, grad, n_sample):
+    # the whole workload as the benchmark launches it (all particles, the
+    # PSO phase, then BFGS from every particle with H streamed from HBM),
+    # FP64, first 20 iterations; the oracle runs BFGS in the plain order
+    # from a sample of the same PSO positions
+    fields = workloads.workload(name, grad_mode=grad, bfgs_max_iters=20)
+    p = zeus_problem(z, fields)
+    assert z.zeus_plan_info(p)["stream"] == 1
+    op = ora.pso(oracle_problem(ora, fields))
+    sample = np.random.default_rng(5).choice(fields["n_starts"], n_sample, replace=False)
+    plain, spread, excused = _reference(ora, (name, n_sample), fields, op["x"][sample])
+    g = z.solve(p)
+    assert g["summary"]["gbest_index"] == op["gidx"]
+    gs = {k: g[k].cpu().numpy()[sample] for k in ("x", "f", "gnorm", "status", "iters")}
+    compare_plain(gs, plain, spread, excused, max_excused=0.02)
+
+
+# L-BFGS on 10-D Rastrigin and 40-D Ackley: the line searches of nearly every
+# start meet an Armijo tie within 20 iterations (the oracle's margin), so
+# those cases are excused almost wholly and bound little
+LB_CASES = [("rosenbrock", 12, 64, -2.0, 2.0, 0.05), ("rastrigin", 10, 64, -5.12, 5.12, None),
+            ("ackley", 40, 32, -5.0, 5.0, None), ("quadratic", 33, 16, -1.0, 1.0, 0.05),
+            ("rosenbrock", 300, 16, -2.0, 2.0, 0.05)]
+
+
+@pytest.mark.parametrize("obj,d,n,lo,hi,max_excused", LB_CASES)
+@pytest.mark.parametrize("m", [1, 5, 17])
+def test_lbfgs_against_plain_order(z, ora, obj, d, n, lo, hi, max_excused, m):
+    x0 = workloads.start_points(n, d, lo, hi, seed=11 * n + d + m)
+    fields = dict(objective=obj, dim=d, lower=lo, upper=hi, n_starts=n, bfgs_max_iters=20,
+                  lbfgs_m=m)
+    plain, spread, excused = plain_reference(ora, fields, x0)
+    g = to_np(z.solve_from(zeus_problem(z, fields), torch.from_numpy(x0).cuda()))
+    compare_plain(g, plain, spread, excused, max_excused=max_excused)
+
+
+@pytest.mark.parametrize("obj", ["ackley", "rosenbrock"])
+def test_adjoint_gradient_at_full_dimension(z, ora, obj):
+    # d = 1024 (the large-d workloads' dimension), 16 starts on the
+    # workloads' box: the reverse-mode adjoint against the forward-mode
+    # (Alg. 5) gradient on the GPU, and against FP64 central differences
+    # of the oracle's f (h = 1e-6), whose own error is bounded by the
+    # rounding of f over 2h plus the truncation h^2/6 |f'''|
+    d, n, h = 1024, 16, 1e-6
+    x = workloads.start_points(n, d, -5.0, 5.0, seed=31)
+    xt = torch.from_numpy(x).cuda()
+    fa, ga = z.objective(obj, xt, grad=True, grad_mode="adjoint")
+    ff, gf = z.objective(obj, xt, grad=True, grad_mode="forward")
+    ga, gf, fa = ga.cpu().numpy(), gf.cpu().numpy(), fa.cpu().numpy()
+    for i in range(n):
+        scale = max(1.0, np.abs(gf[i]).max())
+        assert np.abs(ga[i] - gf[i]).max() <= 1e-11 * scale
+    for i in range(4):  # central differences, coordinate by coordinate
+        fi = abs(float(fa[i]))
+        cd = np.empty(d)
+        for j in range(d):
+            xp, xm = x[i].copy(), x[i].copy()
+            xp[j] += h
+            xm[j] -= h
+            cd[j] = (ora.f(obj, xp, order=ora.ORDER_PLAIN) - ora.f(obj, xm, order=ora.ORDER_PLAIN)) / (
+                (xp[j] - x[i][j]) + (x[i][j] - xm[j]))
+        # rounding of f: d terms of size |f| at most, each within 2^-52
+        # relative, over 2h; truncation: |f'''| <= 2400 max|x| (Rosenbrock),
+        # 20 (2 pi)^3 / d + ... (Ackley, below 1)
+        tol = 4 * d * 2.0 ** -52 * max(1.0, fi) / (2 * h) + h * h * 2400 * 5
+        assert np.abs(ga[i] - cd).max() <= tol, (np.abs(ga[i] - cd).max(), tol)
