@@ -82,7 +82,11 @@ typedef enum {
     ZEUS_RUN_MAX_ITER = 0,   /* iteration cap reached (the paper's status 0) */
     ZEUS_RUN_CONVERGED = 1,  /* ||g|| < grad_tol, or f <= target_f */
     ZEUS_RUN_STOPPED = 2,    /* the shared stop flag was raised (Alg. 10) */
-    ZEUS_RUN_NONFINITE = 3   /* f or g became NaN or infinite */
+    ZEUS_RUN_NONFINITE = 3,  /* f or g became NaN or infinite */
+    ZEUS_RUN_STALLED = 4     /* ZEUS_FP32_GUARDED only: the last iteration lowered f by no
+                                more than FP32 can resolve, f_k - f_{k+1} <=
+                                2^-23 max(|f_k|, |f_{k+1}|) (the gradient tolerance is
+                                out of reach at FP32 resolution) */
 } zeus_run_status;
 
 /*
@@ -145,6 +149,20 @@ const char *zeus_strerror(int code);
 
 /* ZEUS_ABI_VERSION of the built library. */
 int zeus_abi_version(void);
+
+/* Limit of the bounded device-side waits: the servers of the fused BFGS
+ * launch poll the hand-over queue and the clustering kernel's blocks poll a
+ * grid barrier (both the library's own; the paper's design has no such
+ * waits).  Each poll sleeps about 256 ns; a wait that has not ended after
+ * `polls` polls gives up: the kernel sets its error word
+ * (zeus_result.error or zeus_cluster_result.error = 1), the outputs of the
+ * starts it had not finished are undefined, and it returns, so the context
+ * stays usable and the next call runs normally.  polls = 0 restores the
+ * default, 2^23 polls (about two seconds).  The setting is process-wide
+ * and is read when a call enqueues its kernels; thread-safe.  Meant for
+ * tests of the error paths: a small limit makes correct runs report an
+ * error.  Always ZEUS_OK. */
+int zeus_set_wait_limit(uint32_t polls);
 
 /* Fill *p with the defaults: 2-D Rosenbrock on [-5,5]^2, N = 128, T = 5,
  * w = 0.7, c1 = c2 = 1.5, K = 100, L = 20, c = 1e-4, beta = 0.5,
@@ -337,17 +355,22 @@ int zeus_batch_solve(const zeus_batch_plan *plan, void *workspace, size_t worksp
  * the process exits.
  *   - Limit: when the automatic mode runs one lane per start and hands
  *     long runs to the block-per-start kernel (dim <= 16 with
- *     threads_per_start 0), every start must fit the queue:
- *     n_starts * (12 + 8 * dim * dim) bytes within the array (about 20000
- *     starts at dim 10); larger problems get ZEUS_EWORKSPACE.  Otherwise
- *     zeus_validate's limits apply.
- *   - Problems whose H must stream from HBM (zeus_plan_info().stream) need
- *     more than the array and get ZEUS_EWORKSPACE.
+ *     threads_per_start 0), the hand-over queue holds as many entries as
+ *     zeus_solve_from's would, at most as many as fit the array at
+ *     16 + 8 * dim * dim bytes each (about 20000 at dim 10); a start that
+ *     finds the queue full finishes in its lane, with the same result.
+ *     The lane tiles and the queue's service run in one cooperative launch,
+ *     as in zeus_solve_from.
+ *   - Problems whose H must stream from HBM (zeus_plan_info().stream with
+ *     lbfgs_m = 0) need more than the array and get ZEUS_EWORKSPACE;
+ *     L-BFGS problems (no H) run.  Otherwise zeus_validate's limits apply.
  *   - f_out is required (device double [N]); the other arguments are those
  *     of zeus_solve_from.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *     before any stream capture begins.  The address is kept for the life
+ *     of the process: do not call this entry point on a device again after
+ *     cudaDeviceReset (or anything else that destroys its primary context).
  *   - All calls share the one array and it keeps the previous call's
  *     contents (the call clears what must start at zero): calls that
  *     overlap on the GPU, on any streams, race and give undefined results.
@@ -369,7 +392,8 @@ int zeus_context_destroy(zeus_context *ctx);
 
 /* zeus_solve with HOST outputs: runs on `stream`, copies the outputs to
  * the host buffers (any of which may be NULL except x_out) and synchronizes
- * `stream` before returning.  Grows the context's device buffers on demand
+ * `stream` before returning.  Returns ZEUS_ETIMEOUT (outputs incomplete)
+ * when the run's device error word is set (a bounded wait gave up).  Grows the context's device buffers on demand
  * (ZEUS_ENOMEM if that fails).  x_out: host double [N][dim]; f_out,
  * gnorm_out: host double [N]; status_out, iters_out: host int32 [N];
  * result: host zeus_result. */

@@ -25,9 +25,10 @@ __all__ = [
     "Problem", "ZeusError", "zeus_solve", "zeus_solve_from", "zeus_solve_from_noalloc", "zeus_pso", "zeus_objective_eval",
     "zeus_objective_eval_f32", "zeus_argmin", "zeus_argmin_workspace_size", "zeus_uniform",
     "zeus_workspace_size", "zeus_plan_info", "zeus_validate", "zeus_default_problem", "zeus_strerror",
-    "zeus_abi_version", "zeus_math_eval", "Context", "solve", "solve_from", "pso", "objective", "ObjectiveFn",
+    "zeus_abi_version", "zeus_set_wait_limit", "zeus_math_eval", "Context", "solve", "solve_from", "pso", "objective", "ObjectiveFn",
     "decode_result", "library_path", "lib", "zeus_batch_plan_make", "zeus_batch_prepare",
     "zeus_batch_solve", "Batch", "user_objectives", "zeus_cluster", "zeus_cluster_workspace_size", "cluster", "solve_until_confident",
+    "precision_error",
 ]
 
 
@@ -125,6 +126,13 @@ def zeus_strerror(code: int) -> str:
 
 def zeus_abi_version() -> int:
     return lib().zeus_abi_version()
+
+
+def zeus_set_wait_limit(polls: int) -> None:
+    """Polls (about 256 ns each) a bounded device wait makes before it
+    gives up and sets the call's error word; 0 restores the default
+    (about two seconds).  Process-wide."""
+    check(lib().zeus_set_wait_limit(int(polls)), "zeus_set_wait_limit")
 
 
 def zeus_default_problem() -> zeus_problem:
@@ -588,3 +596,32 @@ def solve_until_confident(problem: Problem, required: int, tol: float = 1e-3, me
 def status_names(status: torch.Tensor):
     return [RUN_STATUS.get(int(s), str(int(s))) for s in status.cpu().tolist()]
 
+
+
+def precision_error(problem: Problem, x0: torch.Tensor, device="cuda", stream=None) -> dict:
+    """The FP32 form's error, start by start: BFGS from the same starts x0
+    in the FP32 form with FP64 guards and in the FP64 method (the paper's
+    precision), then per start |f32 - f64| (both final values are FP64
+    evaluations) and max_j |x32_j - x64_j| / max(1, max_j |x64_j|).  Returns
+    the per-start arrays (numpy), both runs' statuses and a summary of the
+    error distribution (synchronizes)."""
+    p = problem if isinstance(problem, Problem) else None
+    if p is None:
+        raise TypeError("precision_error takes a Problem")
+    r64 = solve_from(p.replace(precision="fp64"), x0, device, stream)
+    r32 = solve_from(p.replace(precision="fp32_guarded"), x0, device, stream)
+    f64, f32 = r64["f"].double(), r32["f"].double()
+    x64, x32 = r64["x"], r32["x"]
+    abs_f = (f32 - f64).abs()
+    both_inf = torch.isinf(f32) & torch.isinf(f64) & (torch.sign(f32) == torch.sign(f64))
+    abs_f = torch.where(both_inf, torch.zeros_like(abs_f), abs_f)
+    rel_x = (x32 - x64).abs().amax(dim=1) / torch.clamp(x64.abs().amax(dim=1), min=1.0)
+    a = abs_f.cpu().numpy()
+    q = torch.quantile(abs_f[torch.isfinite(abs_f)].cpu(), torch.tensor([0.5, 0.9, 1.0],
+                                                                       dtype=torch.float64))
+    return {"abs_f": a, "rel_x": rel_x.cpu().numpy(),
+            "status_fp32": r32["status"].cpu().numpy(), "status_fp64": r64["status"].cpu().numpy(),
+            "summary": {"starts": int(a.size), "median": float(q[0]), "p90": float(q[1]),
+                        "max": float(q[2]), "within_1e-6": float((a <= 1e-6).mean()),
+                        "iters_fp32": int(r32["iters"].sum().item()),
+                        "iters_fp64": int(r64["iters"].sum().item())}}

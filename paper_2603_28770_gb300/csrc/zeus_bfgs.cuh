@@ -320,6 +320,7 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
 
     int k = 0, status = ZEUS_RUN_MAX_ITER, feval = 0;
     bool ls_failed = false;  // the previous iteration's search accepted no trial
+    bool stalled = false;    // FP32 form: the previous iteration's decrease was unresolved
     double gnorm;
     for (;;) {
         double gg = 0.0;
@@ -355,6 +356,10 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
             status = ZEUS_RUN_CONVERGED;
             atomicAdd(&ctrl->n_conv, 1ull);
             atomicExch(&ctrl->stop, 1);
+            break;
+        }
+        if (stalled) {
+            status = ZEUS_RUN_STALLED;
             break;
         }
         if (budget > 0 && (k + feval >= budget || ls_failed)) {
@@ -480,6 +485,7 @@ __device__ __forceinline__ void narrow_run(const zeus_problem& p, const long lon
                 }
             }
         }
+        stalled = stalled_step<T>(f0, fn);
         f0 = fn;
         ++k;
     }
@@ -597,6 +603,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
     int status = ZEUS_RUN_MAX_ITER;
     double gnorm = 0.0;
     int hint = W;  // trials the previous search needed
+    bool stalled = false;  // FP32 form: the previous iteration's decrease was unresolved
     for (;;) {
         // ---- tests at the top of iteration k, with the direction p = -H g
         // formed alongside (one row per thread, columns in order; used only
@@ -640,6 +647,8 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 st = ZEUS_RUN_CONVERGED;
                 atomicAdd(&ctrl->n_conv, 1ull);
                 atomicExch(&ctrl->stop, 1);
+            } else if (stalled) {
+                st = ZEUS_RUN_STALLED;
             }
             if (st >= 0) sh.red[1] = sqrt(dot01);  // ||g|| of the final point
             sh.status = st;
@@ -811,6 +820,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             x[j] = xn[j];
             g[j] = gn[j];
         }
+        stalled = stalled_step<T>(f0, fn);
         f0 = fn;
         ++k;
         __syncthreads();

@@ -81,6 +81,20 @@ __device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_
     return o;
 }
 
+// FP32 form: an iteration whose decrease of f is below what FP32 resolves
+// relative to f ends the start (status ZEUS_RUN_STALLED): f_k - f_{k+1} <=
+// eps32 max(|f_k|, |f_{k+1}|), eps32 = 2^-23 (a relative-decrease test at
+// the working precision; no absolute floor, so runs that still creep
+// towards a minimum at f = 0 go on).  Decided at the end of an iteration,
+// acted on at the top of the next (after the gradient and target tests), so
+// the hand-over point does not change it.
+constexpr double kEps32 = 1.1920928955078125e-07;
+template <class T>
+__device__ __forceinline__ bool stalled_step(double f0, double fn) {
+    if (sizeof(T) != 4) return false;
+    return !(f0 - fn > kEps32 * fmax(fabs(f0), fabs(fn)));
+}
+
 // top 53 bits -> [0, 1)
 __device__ __forceinline__ double u01(uint64_t w) { return (double)(w >> 11) * 0x1.0p-53; }
 

@@ -406,6 +406,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
         bool ident = true, corr = false;
         int npair = 0, head = 0;  // L-BFGS pairs stored, oldest slot
         int k = 0, feval = 0, status = ZEUS_RUN_MAX_ITER;
+        bool stalled = false;  // FP32 form: the previous decrease was below FP32 resolution
         unsigned long long n_read = 0, n_write = 0;  // H passes through HBM
         double gnorm = 0.0;
         __syncthreads();
@@ -425,6 +426,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
             else if (!isfinite(f0) || v3[1] != 0.0) st = ZEUS_RUN_NONFINITE;
             else if (gnorm < tol) st = ZEUS_RUN_CONVERGED;
             else if (use_target && f0 <= p.target_f) st = ZEUS_RUN_CONVERGED;
+            else if (stalled) st = ZEUS_RUN_STALLED;
             if (tid == 0) sh.status = st;
             __syncthreads();
             st = sh.status;
@@ -498,6 +500,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
                     x[j] = xn[j];
                     g[j] = gn[j];
                 }
+                stalled = stalled_step<T>(f0, fn);
                 f0 = fn;
                 ++k;
                 __syncthreads();
@@ -551,6 +554,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
                 x[j] = xn[j];
                 g[j] = gn[j];
             }
+            stalled = stalled_step<T>(f0, fn);
             f0 = fn;
             ++k;
             __syncthreads();
