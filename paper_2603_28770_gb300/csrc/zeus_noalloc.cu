@@ -23,7 +23,9 @@ std::mutex g_mu;
 void* g_ptr[kMaxDevices];
 
 // Device address of g_scratch on the current device, looked up once per
-// device (the first call on a device does this set-up).
+// device (the first call on a device does this set-up) and kept for the
+// life of the process: after cudaDeviceReset, or anything else that
+// destroys the device's primary context, the kept address is stale.
 int scratch_address(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ZEUS_ECUDA;
@@ -51,38 +53,55 @@ extern "C" int zeus_solve_from_noalloc(const zeus_problem* p, const double* x0, 
     BfgsLaunch L;
     v = plan_bfgs(*p, &L);
     if (v != ZEUS_OK) return v;
-    // carve the static scratch: control block | argmin partials | queue
+    if (L.stream && L.hslot_bytes > 0) return ZEUS_EWORKSPACE;  // H slots do not fit the array
+    // carve the static scratch as the workspace of zeus_solve_from is
+    // carved: control block | ready flags | per-SM table | argmin partials |
+    // hand-over queue (start, k, evaluations, H)
     const size_t d = (size_t)p->dim;
-    const size_t off_parts = align256(sizeof(Ctrl));
-    const size_t off_queue = off_parts + align256((size_t)argmin_blocks(p->n_starts) * sizeof(ArgPair));
+    const size_t parts_bytes = align256((size_t)argmin_blocks(p->n_starts) * sizeof(ArgPair));
+    const size_t smlong_bytes = align256(kMaxSMs * sizeof(int));
+    size_t qc = 0;
     if (L.budget > 0) {
-        // every start must fit the hand-over queue: 3 ints and H per start
-        const size_t per = 3 * sizeof(int) + d * d * sizeof(double);
-        const size_t room = kScratchBytes - off_queue - 4 * 256;
-        if ((size_t)p->n_starts > room / per) return ZEUS_EWORKSPACE;
-        L.q_cap = (int)p->n_starts;
+        // the planner's queue, clamped to what the array holds; a start that
+        // finds the queue full runs on in its lane, so a shorter queue only
+        // changes which kernel finishes a start, not its result
+        const size_t per = 4 * sizeof(int) + d * d * sizeof(double);
+        const size_t fixed = align256(sizeof(Ctrl)) + smlong_bytes + parts_bytes + 5 * 256;
+        const size_t fit = kScratchBytes > fixed ? (kScratchBytes - fixed) / per : 0;
+        if (fit < 1) return ZEUS_EWORKSPACE;
+        qc = (size_t)L.q_cap < fit ? (size_t)L.q_cap : fit;
+        L.q_cap = (int)qc;
     } else {
         L.q_cap = 0;
     }
+    const size_t off_ready = align256(sizeof(Ctrl));
+    const size_t off_smlong = off_ready + align256(qc * sizeof(int));
+    const size_t off_parts = off_smlong + smlong_bytes;
+    const size_t off_queue = off_parts + parts_bytes;
+    const size_t off_k = off_queue + align256(qc * sizeof(int));
+    const size_t off_feval = off_k + align256(qc * sizeof(int));
+    const size_t off_h = off_feval + align256(qc * sizeof(int));
+    if (off_h + qc * d * d * sizeof(double) > kScratchBytes) return ZEUS_EWORKSPACE;
     void* base = nullptr;
     v = scratch_address(&base);
     if (v != ZEUS_OK) return v;
     char* b = static_cast<char*>(base);
-    const size_t qc = (size_t)L.q_cap;
     Queue q;
     q.prob = nullptr;
     q.start = reinterpret_cast<int*>(b + off_queue);
-    q.k = reinterpret_cast<int*>(b + off_queue + align256(qc * sizeof(int)));
-    q.feval = reinterpret_cast<int*>(b + off_queue + 2 * align256(qc * sizeof(int)));
-    q.H = reinterpret_cast<double*>(b + off_queue + 3 * align256(qc * sizeof(int)));
+    q.k = reinterpret_cast<int*>(b + off_k);
+    q.feval = reinterpret_cast<int*>(b + off_feval);
+    q.H = reinterpret_cast<double*>(b + off_h);
     q.cap = L.q_cap;
     q.hslots = nullptr;
-    if (L.stream && L.hslot_bytes > 0) return ZEUS_EWORKSPACE;  // H slots do not fit the array
+    q.ready = reinterpret_cast<int*>(b + off_ready);
+    q.sm_long = reinterpret_cast<int*>(b + off_smlong);
     Ctrl* ctrl = reinterpret_cast<Ctrl*>(b);
     ArgPair* parts = reinterpret_cast<ArgPair*>(b + off_parts);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // the control block must start at zero; the rest is written before it is read
-    if (cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return ZEUS_ECUDA;
+    // the control block, the ready flags and the per-SM table must start at
+    // zero; the rest is written before it is read
+    if (cudaMemsetAsync(ctrl, 0, off_parts, st) != cudaSuccess) return ZEUS_ECUDA;
     if (launch_bfgs(*p, L, x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl, q, st) !=
         cudaSuccess)
         return ZEUS_ECUDA;

@@ -53,7 +53,18 @@ def _same(a, b, ra, rb):
     dict(objective="rastrigin", dim=10, lower=-5.12, upper=5.12, n_starts=3000, bfgs_max_iters=400),
     # block-per-start throughout (d above the one-lane limit)
     dict(objective="ackley", dim=40, lower=-5.0, upper=5.0, n_starts=300, bfgs_max_iters=60),
-], ids=["handover", "block_per_start"])
+    # the FP32 form with more starts than its hand-over queue holds
+    dict(objective="rastrigin", dim=10, lower=-5.12, upper=5.12, n_starts=5000, bfgs_max_iters=400,
+         precision="fp32_guarded"),
+    # the adjoint gradient
+    dict(objective="rosenbrock", dim=12, lower=-2.0, upper=2.0, n_starts=2000, bfgs_max_iters=300,
+         grad_mode="adjoint"),
+    # L-BFGS (block per start, no H)
+    dict(objective="rosenbrock", dim=64, lower=-2.0, upper=2.0, n_starts=256, bfgs_max_iters=200,
+         lbfgs_m=5),
+    # more starts than the array's queue holds: the rest finish in their lanes
+    dict(objective="rastrigin", dim=10, lower=-5.12, upper=5.12, n_starts=100000, bfgs_max_iters=200),
+], ids=["handover", "block_per_start", "fp32_queue", "adjoint", "lbfgs", "queue_clamped"])
 def test_noalloc_equals_workspace_entry_two_calls(z, case):
     p = z.Problem(**case)
     x0 = torch.from_numpy(workloads.start_points(p.n_starts, p.dim, p.lower, p.upper, seed=17)).cuda()
@@ -62,11 +73,15 @@ def test_noalloc_equals_workspace_entry_two_calls(z, case):
     for _ in range(2):  # the second call finds the first call's leftovers in the array
         got, res = _run_noalloc(z, p, x0)
         _same(got, ref_np, res, ref["summary"])
+        assert res["error"] == 0
 
 
 def test_noalloc_rejects_problems_beyond_the_array(z):
-    # 10-D with one lane per start needs 12 + 8*10*10 bytes of queue per start
-    p = z.Problem(objective="rastrigin", dim=10, lower=-5.12, upper=5.12, n_starts=100000)
+    # a dense H streamed from device memory (d = 256) needs H slots of
+    # 512 KiB per block, more than the array holds
+    p = z.Problem(objective="rosenbrock", dim=256, lower=-2.0, upper=2.0, n_starts=64,
+                  bfgs_max_iters=10)
+    assert z.zeus_plan_info(p)["stream"] == 1
     x0 = torch.zeros(p.n_starts, p.dim, dtype=torch.float64, device="cuda")
     with pytest.raises(z.ZeusError) as e:
         _run_noalloc(z, p, x0)
