@@ -22,6 +22,7 @@
 // Armijo sums and the final value); T = double is the FP64 method.
 #include "zeus_device.cuh"
 #include "zeus_internal.h"
+#include "zeus_tma.cuh"
 
 namespace zeus {
 
@@ -272,6 +273,124 @@ __device__ __forceinline__ void h_pass(T* __restrict__ Hs, int d, bool ident, bo
     __syncthreads();
 }
 
+// Staged pass: where a row of H is a multiple of 16 bytes and at most 2 KB
+// (d = 256 in FP32 or FP64, the d of the benchmark's streamed workload),
+// the rows reach shared memory by bulk copies of one chunk of
+// kStreamWarps rows each (one row per warp), `ns` chunks in flight per
+// block, so that a block keeps its share of HBM busy whatever its number of
+// warps.  The arithmetic and its order are those of h_pass (lane l of a
+// row's warp takes the 16-byte vectors l, l + 32, ...); the updated rows go
+// back to device memory with streaming stores.
+struct StagePlan {
+    int ns;                 // chunks in flight (0: the pass reads H directly)
+    unsigned chunk_bytes;   // kStreamWarps rows
+};
+
+__host__ __device__ inline StagePlan stage_plan(int d, int tsize) {
+    StagePlan sp{0, 0};
+    const long long row = (long long)d * tsize;
+    if (row % 16 != 0 || row > 2048) return sp;
+    sp.ns = tsize == 4 ? 3 : 2;
+    sp.chunk_bytes = (unsigned)(row * kStreamWarps);
+    return sp;
+}
+
+__host__ __device__ inline size_t stage_offset(int d, size_t tsize) {
+    return (10 * (size_t)d * tsize + 127) & ~size_t(127);
+}
+
+// Returns false if a chunk did not arrive within `spin_limit` polls: the
+// error word is set, the copies still in flight are waited for (bounded)
+// and the caller ends the kernel.  ctr counts the chunks the block has
+// waited for (it fixes each chunk's stage and mbarrier parity).
+template <class T>
+__device__ bool h_pass_staged(T* __restrict__ Hs, int d, bool corr, const T* s, const T* hy,
+                              const T* A, const T* B, const T* g, T* u, unsigned char* stage,
+                              uint64_t* bar, const StagePlan sp, unsigned& ctr,
+                              const unsigned spin_limit, Ctrl* ctrl) {
+    using VT = Vec16<T>;
+    using V = typename VT::V;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nc = (d + kStreamWarps - 1) / kStreamWarps;
+    const size_t rowb = (size_t)d * sizeof(T);
+    const int nv = d / VT::n;
+    // the previous pass's stores to H come before the copies that read them
+    fence_async_global();
+    __syncthreads();
+    auto issue = [&](int c) {
+        const unsigned k = ctr + (unsigned)c;
+        const int st = (int)(k % (unsigned)sp.ns);
+        const int r0 = c * kStreamWarps;
+        const int nr = min(kStreamWarps, d - r0);
+        const unsigned bytes = (unsigned)(nr * rowb);
+        mbar_arrive_expect_tx(bar + st, bytes);
+        bulk_copy_g2s(stage + (size_t)st * sp.chunk_bytes,
+                      reinterpret_cast<const char*>(Hs) + (size_t)r0 * rowb, bytes, bar + st);
+    };
+    if (threadIdx.x == 0)
+        for (int c = 0; c < min(sp.ns, nc); ++c) issue(c);
+    bool ok = true;
+    int c = 0;
+    for (; c < nc; ++c) {
+        const unsigned k = ctr + (unsigned)c;
+        const int st = (int)(k % (unsigned)sp.ns);
+        const bool arrived = mbar_wait_bounded(bar + st, (k / (unsigned)sp.ns) & 1u, spin_limit);
+        const int r = c * kStreamWarps + w;
+        if (arrived && r < d) {
+            const V* rv = reinterpret_cast<const V*>(stage + (size_t)st * sp.chunk_bytes + (size_t)w * rowb);
+            V* gvout = reinterpret_cast<V*>(Hs + (size_t)r * d);
+            const V* sv4 = reinterpret_cast<const V*>(s);
+            const V* hv4 = reinterpret_cast<const V*>(hy);
+            const V* gv4 = reinterpret_cast<const V*>(g);
+            const T ar = corr ? A[r] : T(0), br = corr ? B[r] : T(0);
+            T acc = T(0);
+#pragma unroll 2
+            for (int c4 = lane; c4 < nv; c4 += 32) {
+                V h = rv[c4];
+                const V gq = gv4[c4];
+                V sq, hq;
+                if (corr) {
+                    sq = sv4[c4];
+                    hq = hv4[c4];
+                }
+#pragma unroll
+                for (int i = 0; i < VT::n; ++i) {
+                    T e = VT::get(h, i);
+                    if (corr) e = fma(VT::get(sq, i), ar, fma(VT::get(hq, i), br, e));
+                    VT::set(h, i, e);
+                    acc = fma(e, VT::get(gq, i), acc);
+                }
+                if (corr) __stcs(gvout + c4, h);
+            }
+            acc = warp_sum_t(acc);
+            if (lane == 0) u[r] = acc;
+        }
+        // every thread is done with the stage; then it is refilled
+        if (__syncthreads_or(arrived ? 0 : 1)) {
+            ok = false;
+            break;
+        }
+        if (threadIdx.x == 0 && c + sp.ns < nc) {
+            fence_async_shared();
+            issue(c + sp.ns);
+        }
+    }
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            atomicExch(&ctrl->error, 1);
+            // the chunks issued and not waited for: c .. min(c + ns, nc) - 1
+            for (int cc = c; cc < min(c + sp.ns, nc); ++cc) {
+                const unsigned k = ctr + (unsigned)cc;
+                mbar_wait_bounded(bar + (k % (unsigned)sp.ns), (k / (unsigned)sp.ns) & 1u, spin_limit);
+            }
+        }
+        __syncthreads();
+        return false;
+    }
+    ctr += (unsigned)nc;
+    return true;
+}
+
 // One L-BFGS step after the gradient at x_new: the pair (s, y) joins the
 // history if it passes the curvature test (as in Alg. 4's update), then
 // p = -H g_new by the two-loop recursion (Nocedal & Wright, Alg. 7.4) with
@@ -360,9 +479,10 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     bfgs_stream_kernel(const zeus_problem p, const double* x0, double* x_out,
                        double* __restrict__ f_out, double* __restrict__ gnorm_out,
                        int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
-                       Ctrl* __restrict__ ctrl, T* __restrict__ hslots) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+                       Ctrl* __restrict__ ctrl, T* __restrict__ hslots, const unsigned spin_limit) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ StreamShared sh;
+    __shared__ __align__(8) uint64_t stage_bar[4];
     const int tid = threadIdx.x, NT = blockDim.x;
     const int d = p.dim;
     T* x = reinterpret_cast<T*>(smem_raw);
@@ -384,6 +504,17 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
         smem_raw + ((((size_t)10 * d + 2 * (size_t)lm * d) * sizeof(T) + 7) & ~size_t(7)));
     double* gam_m = rho_m + lm;  // s'y / y'y of each pair (the initial scaling)
     double* al_m = gam_m + lm;   // alpha of the first loop
+    // staged pass (dense H only): chunks of rows in shared memory
+    const StagePlan sp = LB ? StagePlan{0, 0} : stage_plan(d, (int)sizeof(T));
+    unsigned char* stage = smem_raw + stage_offset(d, sizeof(T));
+    unsigned chunk_ctr = 0;
+    if (sp.ns > 0) {
+        if (tid == 0) {
+            for (int i = 0; i < sp.ns; ++i) mbar_init(stage_bar + i, 1);
+            fence_async_shared();
+        }
+        __syncthreads();
+    }
 
     const bool use_target = !isnan(p.target_f);
     const bool use_stop = use_target || p.required_converged > 0;
@@ -511,7 +642,13 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
                 for (int j = tid; j < d; j += NT) u[j] = gn[j];
                 __syncthreads();
             } else {
-                h_pass<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u);
+                if (sp.ns > 0 && !ident) {
+                    if (!h_pass_staged<T>(Hs, d, corr, sv, hy, Av, Bv, gn, u, stage, stage_bar, sp,
+                                          chunk_ctr, spin_limit, ctrl))
+                        return;  // a chunk never arrived: the error word is set
+                } else {
+                    h_pass<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u);
+                }
                 n_read += ident ? 0 : 1;             // H_{k-1} read unless still I
                 n_write += (corr || ident) ? 1 : 0;  // H_k stored when it changed
                 ident = false;
@@ -602,7 +739,11 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     }
 }
 
-size_t stream_smem(int d, size_t tsize) { return 10 * (size_t)d * tsize; }
+size_t stream_smem(int d, size_t tsize) {
+    const StagePlan sp = stage_plan(d, (int)tsize);
+    if (sp.ns == 0) return 10 * (size_t)d * tsize;
+    return stage_offset(d, tsize) + (size_t)sp.ns * sp.chunk_bytes;
+}
 
 size_t lbfgs_smem(int d, int m, size_t tsize) {
     return ((((size_t)10 * d + 2 * (size_t)m * d) * tsize + 7) & ~size_t(7)) +
@@ -629,7 +770,7 @@ static cudaError_t stream_go(const zeus_problem& p, const double* x0, double* x_
         cudaError_t e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
         if (e != cudaSuccess) return e;
         kl<<<stream_blocks(p), kStreamThreads, sl, st>>>(p, x0, x_out, f_out, gnorm_out, status_out,
-                                                         iters_out, ctrl, nullptr);
+                                                         iters_out, ctrl, nullptr, wait_limit());
         return cudaGetLastError();
     }
     auto kern = bfgs_stream_kernel<OBJ, GRAD, T, false>;
@@ -637,7 +778,8 @@ static cudaError_t stream_go(const zeus_problem& p, const double* x0, double* x_
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     kern<<<stream_blocks(p), kStreamThreads, sm, st>>>(p, x0, x_out, f_out, gnorm_out, status_out,
-                                                       iters_out, ctrl, static_cast<T*>(hslots));
+                                                       iters_out, ctrl, static_cast<T*>(hslots),
+                                                       wait_limit());
     return cudaGetLastError();
 }
 
