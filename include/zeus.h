@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define ZEUS_ABI_VERSION 1
+#define ZEUS_ABI_VERSION 2
 
 typedef enum {
     ZEUS_OK = 0,
@@ -280,10 +280,14 @@ int zeus_math_eval(int32_t fn, int64_t n, const double *x, double *y0, double *y
 /* ---- Batched form (the paper solves one problem per call) ----
  *
  * Many independent problems (any mix of objective, dim, N, T, K, seed)
- * solved by one fixed sequence of kernels: PSO updates of every problem in
- * one launch per update, BFGS of every start from a device work list
- * (persistent blocks; one launch per shared-memory class), the hand-over
- * launch, and one best-of-swarm reduction per problem.  Problem P's results
+ * solved by one fixed set of kernels: PSO updates of every problem in one
+ * launch per update, BFGS of every start from a device work list
+ * (persistent blocks; one launch per class of items that share a layout
+ * and an occupancy), the hand-over launch, and one best-of-swarm reduction
+ * per problem.  The lane-tile classes and the hand-over launch run on a
+ * stream of the library's own, concurrently with the block-per-start
+ * classes on `stream` (forked from and joined back to `stream`, so the
+ * call stays stream-ordered and graph-capturable).  Problem P's results
  * equal those of zeus_solve(&probs[P]) bit for bit.
  *
  * Every problem of a batch shares `precision` and `grad_mode`; problems
@@ -299,7 +303,7 @@ int zeus_math_eval(int32_t fn, int64_t n, const double *x, double *y0, double *y
  *   results    device zeus_result [n_problems]     (may be NULL)
  * Problem P's rows start at the prefix sums of N_Q * dim_Q and N_Q, Q < P.
  */
-#define ZEUS_BATCH_MAX_CLASSES 16
+#define ZEUS_BATCH_MAX_CLASSES 32
 
 typedef struct {
     int32_t n_problems;
@@ -317,6 +321,7 @@ typedef struct {
     int32_t class_first[ZEUS_BATCH_MAX_CLASSES];  /* work-list range and dynamic */
     int32_t class_count[ZEUS_BATCH_MAX_CLASSES];  /* shared memory of each BFGS */
     int32_t class_smem[ZEUS_BATCH_MAX_CLASSES];   /* launch */
+    int32_t class_kind[ZEUS_BATCH_MAX_CLASSES];   /* 0: lane tiles, 1: one block per start */
     int64_t total_starts;     /* sum_P N_P */
     int64_t total_coords;     /* sum_P N_P * dim_P */
     int64_t total_g;          /* sum_P dim_P */
@@ -329,7 +334,9 @@ int zeus_batch_plan_make(const zeus_problem *probs, int32_t n, zeus_batch_plan *
 
 /* Writes the batch's tables (problem parameters, offsets, work list) into
  * the workspace: one host-to-device copy on `stream`, then synchronizes
- * `stream`.  probs and plan must be those given to zeus_batch_plan_make;
+ * `stream`.  On its first call on a device it also creates the library's
+ * second stream and two events for that device (kept until exit), so call
+ * it before any stream capture of zeus_batch_solve.  probs and plan must be those given to zeus_batch_plan_make;
  * workspace: device, plan->workspace_bytes, 256-byte aligned.  The tables
  * stay valid for any number of zeus_batch_solve calls on this workspace. */
 int zeus_batch_prepare(const zeus_problem *probs, int32_t n, const zeus_batch_plan *plan,

@@ -61,7 +61,7 @@ class zeus_plan(C.Structure):
                 ("h_bytes", C.c_int64)]
 
 
-BATCH_MAX_CLASSES = 16
+BATCH_MAX_CLASSES = 32
 
 
 class zeus_batch_plan(C.Structure):
@@ -72,6 +72,7 @@ class zeus_batch_plan(C.Structure):
                 ("class_first", C.c_int32 * BATCH_MAX_CLASSES),
                 ("class_count", C.c_int32 * BATCH_MAX_CLASSES),
                 ("class_smem", C.c_int32 * BATCH_MAX_CLASSES),
+                ("class_kind", C.c_int32 * BATCH_MAX_CLASSES),
                 ("total_starts", C.c_int64), ("total_coords", C.c_int64), ("total_g", C.c_int64),
                 ("workspace_bytes", C.c_uint64), ("table_bytes", C.c_uint64)]
 
@@ -169,7 +170,7 @@ def lib() -> C.CDLL:
                 fn = getattr(L, name)
                 fn.restype = res
                 fn.argtypes = args
-            if L.zeus_abi_version() != 1:
+            if L.zeus_abi_version() != 2:
                 raise RuntimeError("libzeus.so ABI version mismatch")
             _lib = L
     return _lib

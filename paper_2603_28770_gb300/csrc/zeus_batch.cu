@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "zeus.h"
@@ -77,7 +78,7 @@ struct BatchHost {
     Sizes sz;
     int pso_iters_max = 0, handover_smem = 0, n_classes = 0, n_user = 0;
     int class_first[ZEUS_BATCH_MAX_CLASSES], class_count[ZEUS_BATCH_MAX_CLASSES],
-        class_smem[ZEUS_BATCH_MAX_CLASSES];
+        class_smem[ZEUS_BATCH_MAX_CLASSES], class_kind[ZEUS_BATCH_MAX_CLASSES];
 };
 
 // blocks of the batched BFGS kernel that share an SM at this dynamic shared
@@ -148,22 +149,24 @@ int build_host(const zeus_problem* probs, int n, BatchHost& B) {
         }
     }
     if (work.size() >= (size_t)1 << 31) return ZEUS_EINVAL;
-    // classes by occupancy (fewest blocks per SM first); within a class the
-    // block-per-start items first, then larger d first (long work starts early)
+    // classes by kind (block-per-start items, then lane tiles, which feed
+    // the hand-over queue) and occupancy (fewest blocks per SM first); within
+    // a class larger d first (long work starts early)
     std::stable_sort(work.begin(), work.end(), [](const Work& a, const Work& b) {
+        if (a.item.w != b.item.w) return a.item.w > b.item.w;
         const int ca = per_sm(a.smem), cb = per_sm(b.smem);
         if (ca != cb) return ca < cb;
-        if (a.item.w != b.item.w) return a.item.w > b.item.w;
         return a.dim > b.dim;
     });
     B.n_classes = 0;
     for (size_t i = 0; i < work.size(); ++i) {
         const int c = per_sm(work[i].smem);
-        if (i == 0 || c != per_sm(work[i - 1].smem)) {
+        if (i == 0 || c != per_sm(work[i - 1].smem) || work[i].item.w != work[i - 1].item.w) {
             if (B.n_classes == ZEUS_BATCH_MAX_CLASSES) return ZEUS_EUNSUPPORTED;
             B.class_first[B.n_classes] = (int)i;
             B.class_count[B.n_classes] = 0;
             B.class_smem[B.n_classes] = 0;
+            B.class_kind[B.n_classes] = work[i].item.w;
             ++B.n_classes;
         }
         const int k = B.n_classes - 1;
@@ -297,6 +300,7 @@ void fill_plan(const BatchHost& B, const BatchLayout& l, zeus_batch_plan* plan) 
         plan->class_first[c] = B.class_first[c];
         plan->class_count[c] = B.class_count[c];
         plan->class_smem[c] = B.class_smem[c];
+        plan->class_kind[c] = B.class_kind[c];
     }
     plan->total_starts = B.sz.total_starts;
     plan->total_coords = B.sz.total_coords;
@@ -310,6 +314,39 @@ int check_ws(void* ws, size_t have, size_t need) {
     return ZEUS_OK;
 }
 
+// The library's second stream of each device (the lane-tile classes and the
+// hand-over launch run there, concurrently with the block-per-start
+// classes) and the two events that fork it from and join it to the
+// caller's stream.  Created once per device, kept until exit; the mutex
+// also keeps one call's fork and join from interleaving with another's.
+constexpr int kMaxDevices = 64;
+struct Aux {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_aux_mu;
+Aux g_aux[kMaxDevices];
+
+// with g_aux_mu held
+cudaError_t aux_for_device(Aux** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    Aux& a = g_aux[dev];
+    if (!a.stream) {
+        e = cudaStreamCreateWithFlags(&a.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            a = Aux();
+            return e;
+        }
+    }
+    *out = &a;
+    return cudaSuccess;
+}
+
 bool plan_sane(const zeus_batch_plan& p) {
     if (p.n_problems < 1 || p.pso_blocks < 1 || p.items < 1 || p.pso_iters_max < 0) return false;
     if (p.n_classes < 1 || p.n_classes > ZEUS_BATCH_MAX_CLASSES) return false;
@@ -320,6 +357,7 @@ bool plan_sane(const zeus_batch_plan& p) {
     for (int c = 0; c < p.n_classes; ++c) {
         if (p.class_first[c] != next || p.class_count[c] < 1) return false;
         if (p.class_smem[c] < 0 || p.class_smem[c] > (int)kSmemCap) return false;
+        if (p.class_kind[c] != 0 && p.class_kind[c] != 1) return false;
         next += p.class_count[c];
     }
     if (next != p.items) return false;
@@ -377,6 +415,11 @@ int zeus_batch_prepare(const zeus_problem* probs, int32_t n, const zeus_batch_pl
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(workspace, host.data(), host.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(g_aux_mu);
+        Aux* a = nullptr;
+        e = aux_for_device(&a);
+    }
     return e == cudaSuccess ? ZEUS_OK : ZEUS_ECUDA;
 }
 
@@ -395,15 +438,34 @@ int zeus_batch_solve(const zeus_batch_plan* plan, void* workspace, size_t worksp
         cudaMemsetAsync(static_cast<char*>(workspace) + l.pctrl, 0, l.partials - l.pctrl, st);
     for (int t = -1; t < plan->pso_iters_max && e == cudaSuccess; ++t)
         e = launch_batch_pso(bd, t, x_out, st);
-    for (int c = 0; c < plan->n_classes && e == cudaSuccess; ++c)
-        e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, c,
-                              plan->class_first[c],
-                              plan->class_count[c], (size_t)plan->class_smem[c], x_out, f_out,
-                              gnorm_out, status_out, iters_out, st);
-    if (e == cudaSuccess && plan->q_cap > 0)
-        e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, -1, 0, 0,
-                              (size_t)plan->handover_smem, x_out, f_out, gnorm_out, status_out,
-                              iters_out, st);
+    if (e != cudaSuccess) return ZEUS_ECUDA;
+    {
+        // fork: lane-tile classes then the hand-over launch on the second
+        // stream, block-per-start classes on `stream`; join before the
+        // reduction.  The two sets touch disjoint problems (a problem's
+        // starts are all lane tiles or all blocks).
+        std::lock_guard<std::mutex> lock(g_aux_mu);
+        Aux* a = nullptr;
+        e = aux_for_device(&a);
+        if (e == cudaSuccess) e = cudaEventRecord(a->fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(a->stream, a->fork, 0);
+        for (int c = 0; c < plan->n_classes && e == cudaSuccess; ++c)
+            e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, c,
+                                  plan->class_first[c], plan->class_count[c],
+                                  (size_t)plan->class_smem[c], x_out, f_out, gnorm_out, status_out,
+                                  iters_out, plan->class_kind[c] == 0 ? a->stream : st);
+        if (e == cudaSuccess && plan->q_cap > 0)
+            e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, -1, 0, 0,
+                                  (size_t)plan->handover_smem, x_out, f_out, gnorm_out, status_out,
+                                  iters_out, a->stream);
+        // join whatever was enqueued, also after a failed launch, so that a
+        // capture never ends with the second stream still forked
+        if (a) {
+            const cudaError_t e1 = cudaEventRecord(a->join, a->stream);
+            const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(st, a->join, 0) : e1;
+            if (e == cudaSuccess) e = e2;
+        }
+    }
     if (e == cudaSuccess) e = launch_batch_argmin(bd, f_out, results, st);
     return e == cudaSuccess ? ZEUS_OK : ZEUS_ECUDA;
 }

@@ -165,6 +165,10 @@ def test_batch_plan(z):
         assert 0 < pl.class_smem[c] <= 227 * 1024
         nxt += pl.class_count[c]
     assert nxt == pl.items
+    # block-per-start classes first, then the lane-tile classes (which run
+    # on the library's second stream with the hand-over launch)
+    kinds = [pl.class_kind[c] for c in range(pl.n_classes)]
+    assert set(kinds) <= {0, 1} and kinds == sorted(kinds, reverse=True)
     # work items: one per block-per-start start, one per lane tile of <= 128 starts
     lane = [p for p in probs if z.zeus_plan_info(p)["narrow"]]
     block = [p for p in probs if not z.zeus_plan_info(p)["narrow"]]
