@@ -61,6 +61,9 @@ def _args():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--grad-mode", default="forward", choices=["forward", "adjoint"])
     ap.add_argument("--lanes", type=int, default=0, help="threads per start (0 = automatic)")
+    ap.add_argument("--layout", type=int, default=-1,
+                    help="batched workload: threads per start of every problem instead of the "
+                         "autotuner's choice (profiling cases)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_guarded"])
     ap.add_argument("--study", action="store_true",
                     help="the early-stop study instead of the benchmark: PSO updates vs time and "
@@ -526,8 +529,10 @@ def run_batch_main(a, z, dev, world, rank):
     # weak scaling: each rank solves its own batch (seeds shifted by rank);
     # threads per start chosen by the autotuner (measured once, then cached)
     t0 = time.perf_counter()
+    if a.layout >= 0:
+        fields = [dict(f, threads_per_start=a.layout) for f in fields]
     b = z.Batch([z.Problem(**dict(f, seed=rank_seed(f["seed"], rank, 4096))) for f in fields],
-                device=dev, autotuner=_tuner())
+                device=dev, autotuner=None if a.layout >= 0 else _tuner())
     tune_s = time.perf_counter() - t0
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     b.solve()
