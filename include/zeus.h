@@ -117,6 +117,8 @@ typedef struct {
                                    long-running starts handed to one 128-thread block
                                    each; H streamed from HBM when it does not fit on
                                    chip; 1 = one lane per start throughout;
+                                   32 = one warp per start, four starts to a 128-thread
+                                   block, H in shared memory;
                                    128 = one 128-thread block per start throughout;
                                    256 = one 256-thread block per start, H streamed */
     int32_t lbfgs_m;            /* 0 = the dense inverse-Hessian update of Alg. 4; m in 1..64 =
@@ -180,6 +182,7 @@ typedef struct {
     int32_t stream;          /* 1: one 256-thread block per start, H streamed from HBM */
     int32_t blocks;          /* grid of the block-per-start / streaming kernel */
     int32_t lbfgs;           /* 1: L-BFGS (problem.lbfgs_m > 0), block per start, no H */
+    int32_t warp;            /* 1: one warp per start, H in shared memory */
     int64_t h_bytes;         /* bytes of H per start in the chosen precision */
 } zeus_plan;
 int zeus_plan_info(const zeus_problem *p, zeus_plan *plan);
@@ -321,7 +324,8 @@ typedef struct {
     int32_t class_first[ZEUS_BATCH_MAX_CLASSES];  /* work-list range and dynamic */
     int32_t class_count[ZEUS_BATCH_MAX_CLASSES];  /* shared memory of each BFGS */
     int32_t class_smem[ZEUS_BATCH_MAX_CLASSES];   /* launch */
-    int32_t class_kind[ZEUS_BATCH_MAX_CLASSES];   /* 0: lane tiles, 1: one block per start */
+    int32_t class_kind[ZEUS_BATCH_MAX_CLASSES];   /* 0: lane tiles, 1: one block per start,
+                                                     2: one warp per start */
     int64_t total_starts;     /* sum_P N_P */
     int64_t total_coords;     /* sum_P N_P * dim_P */
     int64_t total_g;          /* sum_P dim_P */

@@ -58,7 +58,7 @@ class zeus_result(C.Structure):
 class zeus_plan(C.Structure):
     _fields_ = [("narrow", C.c_int32), ("handover", C.c_int32), ("block", C.c_int32),
                 ("stream", C.c_int32), ("blocks", C.c_int32), ("lbfgs", C.c_int32),
-                ("h_bytes", C.c_int64)]
+                ("warp", C.c_int32), ("h_bytes", C.c_int64)]
 
 
 BATCH_MAX_CLASSES = 32

@@ -1,9 +1,9 @@
 """Autotuner of the per-start kernel layout of the batched form.
 
 Each start of a batch runs either on one lane (H of the start in the
-block's shared memory, 32 starts to a warp), or on one 128-thread block, or
-on lanes first with the long runs handed over to blocks (the automatic
-choice for d <= 16).  Which is fastest depends on the objective, the
+block's shared memory, 32 starts to a warp), or on one warp (four starts to
+a 128-thread block), or on one 128-thread block, or on lanes first with the
+long runs handed over to blocks (the automatic choice for d <= 16).  Which is fastest depends on the objective, the
 dimension, the precision and the gradient mode, and the arithmetic does not:
 every layout produces the same bits (the kernels perform the same operations
 in the same order), so the tuner only changes the time.
@@ -11,7 +11,10 @@ in the same order), so the tuner only changes the time.
 The tuner keys problems by (objective, dimension bucket, precision, gradient
 mode), times every layout the kernels accept on a probe batch built from the
 problems of that key (at most `probe_problems` of them, truncated to
-`probe_starts` starts each), and keeps the fastest.  Choices persist in a
+`probe_starts` starts each, repeated with other seeds until the probe holds
+`probe_total` starts, so that the layouts that keep many starts on an SM at
+once are compared at throughput rather than at the latency of a few
+starts), and keeps the fastest.  Choices persist in a
 JSON file keyed also by the device name, so a key is measured once per GPU
 model.
 """
@@ -25,8 +28,9 @@ import threading
 BUCKETS = (2, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024, 4096)
 
 # threads_per_start values the kernels provide: 0 automatic (lanes with
-# hand-over for d <= 16, else a block), 1 lanes throughout, 128 a block
-CANDIDATES = (0, 1, 128)
+# hand-over for d <= 16, else a block), 1 lanes throughout, 32 a warp (four
+# starts to a block), 128 a block
+CANDIDATES = (0, 1, 32, 128)
 
 
 def bucket(d: int) -> int:
@@ -51,11 +55,13 @@ class Autotuner:
     (used by the host tests); by default a probe batch is solved on the
     current CUDA device and timed with CUDA events."""
 
-    def __init__(self, cache_path: str | None = None, probe_problems: int = 8,
-                 probe_starts: int = 128, reps: int = 2, measure=None, device_name: str | None = None):
+    def __init__(self, cache_path: str | None = None, probe_problems: int = 16,
+                 probe_starts: int = 256, reps: int = 1, measure=None, device_name: str | None = None,
+                 probe_total: int = 8192):
         self.cache_path = cache_path or default_cache_path()
         self.probe_problems = probe_problems
         self.probe_starts = probe_starts
+        self.probe_total = probe_total
         self.reps = reps
         self._measure = measure or self._measure_gpu
         self._device = device_name
@@ -111,13 +117,19 @@ class Autotuner:
 
     def _probe(self, members, tps: int):
         from . import _capi
-        out = []
-        for p in members[: self.probe_problems]:
-            q = _capi.zeus_problem.from_buffer_copy(bytes(p))
-            q.threads_per_start = tps
-            q.n_starts = min(int(q.n_starts), self.probe_starts)
-            out.append(q)
-        return out
+        out, total, r = [], 0, 0
+        base = members[: self.probe_problems]
+        while True:
+            for p in base:
+                q = _capi.zeus_problem.from_buffer_copy(bytes(p))
+                q.threads_per_start = tps
+                q.n_starts = min(int(q.n_starts), self.probe_starts)
+                q.seed = (int(q.seed) + 1000003 * r) & (2**64 - 1)
+                out.append(q)
+                total += int(q.n_starts)
+            r += 1
+            if total >= self.probe_total or r >= 64:
+                return out
 
     def _measure_gpu(self, probe) -> float:
         import torch

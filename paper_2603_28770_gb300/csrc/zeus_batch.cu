@@ -28,13 +28,13 @@
 namespace zeus {
 
 cudaError_t launch_batch_bfgs(const BatchDev& bd, int precision, int grad_mode, bool user, int cls,
-                              int first, int count, size_t smem, double* x_out, double* f_out,
-                              double* gnorm_out, int32_t* status_out, int32_t* iters_out,
-                              cudaStream_t st) {
+                              int first, int count, size_t smem, bool warp_items, double* x_out,
+                              double* f_out, double* gnorm_out, int32_t* status_out,
+                              int32_t* iters_out, cudaStream_t st) {
     const bool f32 = precision == ZEUS_FP32_GUARDED;
     auto go = [&](auto launch) {
-        return launch(bd, cls, first, count, smem, x_out, f_out, gnorm_out, status_out, iters_out,
-                      st);
+        return launch(bd, cls, first, count, smem, warp_items, x_out, f_out, gnorm_out, status_out,
+                      iters_out, st);
     };
     if (grad_mode == ZEUS_GRAD_ADJOINT)
         return f32 ? go(batch_launch_gt<ZEUS_GRAD_ADJOINT, float, false>)
@@ -143,14 +143,18 @@ int build_host(const zeus_problem* probs, int n, BatchHost& B) {
                 B.sz.d_max_handover = std::max<long long>(B.sz.d_max_handover, d);
                 hsmem = std::max(hsmem, L.wide_smem);
             }
+        } else if (L.warp) {  // one warp per start, four starts to a block
+            for (long long s = 0; s < p.n_starts; ++s)
+                work.push_back({make_int4(P, (int)s, L.W, 2), 4 * L.warp_slot, d});
         } else {
             for (long long s = 0; s < p.n_starts; ++s)
                 work.push_back({make_int4(P, (int)s, L.W, 1), L.wide_smem, d});
         }
     }
     if (work.size() >= (size_t)1 << 31) return ZEUS_EINVAL;
-    // classes by kind (block-per-start items, then lane tiles, which feed
-    // the hand-over queue) and occupancy (fewest blocks per SM first); within
+    // classes by kind (warp-per-start and block-per-start items, then lane
+    // tiles, which feed the hand-over queue) and occupancy (fewest blocks
+    // per SM first); within
     // a class larger d first (long work starts early)
     std::stable_sort(work.begin(), work.end(), [](const Work& a, const Work& b) {
         if (a.item.w != b.item.w) return a.item.w > b.item.w;
@@ -357,7 +361,7 @@ bool plan_sane(const zeus_batch_plan& p) {
     for (int c = 0; c < p.n_classes; ++c) {
         if (p.class_first[c] != next || p.class_count[c] < 1) return false;
         if (p.class_smem[c] < 0 || p.class_smem[c] > (int)kSmemCap) return false;
-        if (p.class_kind[c] != 0 && p.class_kind[c] != 1) return false;
+        if (p.class_kind[c] < 0 || p.class_kind[c] > 2) return false;
         next += p.class_count[c];
     }
     if (next != p.items) return false;
@@ -452,12 +456,13 @@ int zeus_batch_solve(const zeus_batch_plan* plan, void* workspace, size_t worksp
         for (int c = 0; c < plan->n_classes && e == cudaSuccess; ++c)
             e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, c,
                                   plan->class_first[c], plan->class_count[c],
-                                  (size_t)plan->class_smem[c], x_out, f_out, gnorm_out, status_out,
-                                  iters_out, plan->class_kind[c] == 0 ? a->stream : st);
+                                  (size_t)plan->class_smem[c], plan->class_kind[c] == 2, x_out,
+                                  f_out, gnorm_out, status_out, iters_out,
+                                  plan->class_kind[c] == 0 ? a->stream : st);
         if (e == cudaSuccess && plan->q_cap > 0)
             e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, -1, 0, 0,
-                                  (size_t)plan->handover_smem, x_out, f_out, gnorm_out, status_out,
-                                  iters_out, a->stream);
+                                  (size_t)plan->handover_smem, false, x_out, f_out, gnorm_out,
+                                  status_out, iters_out, a->stream);
         // join whatever was enqueued, also after a failed launch, so that a
         // capture never ends with the second stream still forked
         if (a) {

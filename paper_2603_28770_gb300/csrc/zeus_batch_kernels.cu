@@ -55,15 +55,15 @@ __device__ __forceinline__ void batch_narrow(const zeus_problem& p, int P, long 
     }
 }
 
-template <int GRAD, class T, bool U>
+template <int GRAD, class T, bool U, int NTW = kWideThreads>
 __device__ __forceinline__ void batch_wide(const zeus_problem& p, int W, long long s, int k,
                                            int fe, const T* Hq, const T* xq, const RunIO& io,
                                            WideShared& sh, unsigned char* smem_raw, int tid) {
     if constexpr (U && GRAD == ZEUS_GRAD_FORWARD) {  // user objectives: forward mode only
         switch (p.objective) {
-#define ZEUS_UCASE(O)                                                            \
-    case O:                                                                      \
-        wide_run<O, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);     \
+#define ZEUS_UCASE(O)                                                                  \
+    case O:                                                                            \
+        wide_run<O, GRAD, T, NTW>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);      \
         return;
             ZEUS_USER_EACH(ZEUS_UCASE)
 #undef ZEUS_UCASE
@@ -73,20 +73,23 @@ __device__ __forceinline__ void batch_wide(const zeus_problem& p, int W, long lo
     }
     switch (p.objective) {
         case ZEUS_OBJ_ROSENBROCK:
-            wide_run<ZEUS_OBJ_ROSENBROCK, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);
-            break;
-        case ZEUS_OBJ_RASTRIGIN:
-            wide_run<ZEUS_OBJ_RASTRIGIN, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);
-            break;
-        case ZEUS_OBJ_ACKLEY:
-            wide_run<ZEUS_OBJ_ACKLEY, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);
-            break;
-        case ZEUS_OBJ_GOLDSTEIN_PRICE:
-            wide_run<ZEUS_OBJ_GOLDSTEIN_PRICE, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw,
+            wide_run<ZEUS_OBJ_ROSENBROCK, GRAD, T, NTW>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw,
                                                         tid);
             break;
+        case ZEUS_OBJ_RASTRIGIN:
+            wide_run<ZEUS_OBJ_RASTRIGIN, GRAD, T, NTW>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw,
+                                                       tid);
+            break;
+        case ZEUS_OBJ_ACKLEY:
+            wide_run<ZEUS_OBJ_ACKLEY, GRAD, T, NTW>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);
+            break;
+        case ZEUS_OBJ_GOLDSTEIN_PRICE:
+            wide_run<ZEUS_OBJ_GOLDSTEIN_PRICE, GRAD, T, NTW>(p, W, s, k, fe, Hq, xq, io, sh,
+                                                             smem_raw, tid);
+            break;
         default:
-            wide_run<ZEUS_OBJ_QUADRATIC, GRAD, T>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw, tid);
+            wide_run<ZEUS_OBJ_QUADRATIC, GRAD, T, NTW>(p, W, s, k, fe, Hq, xq, io, sh, smem_raw,
+                                                       tid);
             break;
     }
 }
@@ -108,15 +111,20 @@ __device__ __forceinline__ RunIO batch_io(const BatchDev& bd, const zeus_problem
 // Persistent blocks over work items [first, first + count) (cls >= 0) or
 // over the hand-over queue (cls < 0).  Item (P, s, c, 0): a tile of c
 // starts s.. of problem P, one lane each; item (P, s, W, 1): start s on the
-// whole block with W line-search trials at once.
+// whole block with W line-search trials at once; item (P, s, W, 2): start s
+// on one warp (a class holds one kind of item; in a class of warp items
+// each warp of a block pulls items for itself, its start's shared memory
+// the warp's quarter of the block's).
 // at least six blocks per SM: the lane-tile classes keep their residency
 template <int GRAD, class T, bool U>
 __global__ void __launch_bounds__(kWideThreads, 6)
     batch_bfgs_kernel(const BatchDev bd, const int cls, const int first, const int count,
-                      double* x_out, double* __restrict__ f_out, double* __restrict__ gnorm_out,
-                      int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out) {
+                      const int smem_bytes, double* x_out, double* __restrict__ f_out,
+                      double* __restrict__ gnorm_out, int32_t* __restrict__ status_out,
+                      int32_t* __restrict__ iters_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ WideShared sh;
+    (void)smem_bytes;
     const int tid = wide_role(blockDim.x);
     unsigned* head = cls >= 0 ? bd.heads + cls : &bd.gctrl->q_head;
     const int n_items =
@@ -154,11 +162,38 @@ __global__ void __launch_bounds__(kWideThreads, 6)
     }
 }
 
+// A class of warp items (P, s, W, 2): each warp of a block pulls items for
+// itself; its start's shared memory is the warp's quarter of the block's.
+template <int GRAD, class T, bool U>
+__global__ void __launch_bounds__(kWideThreads, 5)
+    batch_warp_kernel(const BatchDev bd, const int cls, const int first, const int count,
+                      const int smem_bytes, double* x_out, double* __restrict__ f_out,
+                      double* __restrict__ gnorm_out, int32_t* __restrict__ status_out,
+                      int32_t* __restrict__ iters_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ WideShared shw[kWideThreads / 32];
+    unsigned* head = bd.heads + cls;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t slot = ((size_t)smem_bytes / 4) & ~size_t(15);
+    unsigned char* mine = smem_raw + (size_t)w * slot;
+    for (;;) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(head, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if ((int)it >= count) break;
+        const int4 wi = bd.items[first + (int)it];
+        const int P = wi.x;
+        const zeus_problem p = bd.probs[P];
+        const RunIO io = batch_io(bd, p, P, x_out, f_out, gnorm_out, status_out, iters_out);
+        batch_wide<GRAD, T, U, 32>(p, wi.z, wi.y, 0, 0, nullptr, nullptr, io, shw[w], mine, lane);
+    }
+}
+
 template <int GRAD, class T, bool U>
 cudaError_t batch_launch_gt(const BatchDev& bd, int cls, int first, int count, size_t smem,
-                            double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
-                            int32_t* iters_out, cudaStream_t st) {
-    auto k = batch_bfgs_kernel<GRAD, T, U>;
+                            bool warp_items, double* x_out, double* f_out, double* gnorm_out,
+                            int32_t* status_out, int32_t* iters_out, cudaStream_t st) {
+    auto k = warp_items ? batch_warp_kernel<GRAD, T, U> : batch_bfgs_kernel<GRAD, T, U>;
     // The launches of one solve use different shared memory sizes, and a
     // captured graph launches its kernel nodes later: allow the largest
     // size the device offers once, rather than the size of the launch at
@@ -178,21 +213,22 @@ cudaError_t batch_launch_gt(const BatchDev& bd, int cls, int first, int count, s
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long blocks = (long long)sms * per_sm;
-    if (cls >= 0 && blocks > count) blocks = count;  // no block without an item
+    const long long holders = (cls >= 0 && warp_items) ? (count + 3) / 4 : count;
+    if (cls >= 0 && blocks > holders) blocks = holders;  // no block without an item
     if (cls < 0 && blocks > bd.q.cap) blocks = bd.q.cap;
     if (blocks < 1) return cudaSuccess;
-    k<<<(int)blocks, kWideThreads, smem, st>>>(bd, cls, first, count, x_out, f_out, gnorm_out,
-                                                status_out, iters_out);
+    k<<<(int)blocks, kWideThreads, smem, st>>>(bd, cls, first, count, (int)smem, x_out, f_out,
+                                                gnorm_out, status_out, iters_out);
     return cudaGetLastError();
 }
 
 #if ZEUS_KF32
 template cudaError_t batch_launch_gt<ZEUS_KGRAD, float, ZEUS_KUSER != 0>(
-    const BatchDev&, int, int, int, size_t, double*, double*, double*, int32_t*, int32_t*,
+    const BatchDev&, int, int, int, size_t, bool, double*, double*, double*, int32_t*, int32_t*,
     cudaStream_t);
 #else
 template cudaError_t batch_launch_gt<ZEUS_KGRAD, double, ZEUS_KUSER != 0>(
-    const BatchDev&, int, int, int, size_t, double*, double*, double*, int32_t*, int32_t*,
+    const BatchDev&, int, int, int, size_t, bool, double*, double*, double*, int32_t*, int32_t*,
     cudaStream_t);
 #endif
 

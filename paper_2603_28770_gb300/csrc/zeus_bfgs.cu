@@ -69,6 +69,27 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
         L->hslot_bytes = 0;
         return L->stream_smem <= cap ? ZEUS_OK : ZEUS_EUNSUPPORTED;
     }
+    L->warp = false;
+    L->warp_slot = 0;
+    if (req == 32) {  // one warp per start, four starts to a block, H in shared memory
+        L->narrow = false;
+        L->stride = 0;
+        L->narrow_threads = 0;
+        L->narrow_smem = 0;
+        L->narrow_blocks = 0;
+        L->W = wide_trials(d, p.ls_max_iters, 32);
+        L->wide_smem = wide_smem(d, L->W, p.ls_max_iters, ts);
+        L->warp_slot = (L->wide_smem + 15) & ~size_t(15);
+        L->wide_blocks = 152 * 4;
+        L->budget = 0;
+        L->q_cap = 0;
+        L->stream = false;
+        L->stream_blocks = 0;
+        L->stream_smem = 0;
+        L->hslot_bytes = 0;
+        L->warp = true;
+        return 4 * L->warp_slot <= cap ? ZEUS_OK : ZEUS_EUNSUPPORTED;
+    }
     const size_t row = narrow_stride(d) * ts;
     const bool narrow_fits = row * 32 <= cap;
     L->narrow = (req == 1) || (req == 0 && narrow_fits && d <= 16);

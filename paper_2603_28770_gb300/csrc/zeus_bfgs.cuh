@@ -525,12 +525,29 @@ __device__ __forceinline__ double ordered_dot(const T* a, const T* b, int n) {
     return s;
 }
 
-template <int OBJ, int GRAD, class T>
+// Synchronisation of the threads that carry one start: the whole block
+// (NTW = kWideThreads) or one warp (NTW = 32, several starts per block).
+template <int NTW>
+__device__ __forceinline__ void group_sync() {
+    if constexpr (NTW == 32) __syncwarp();
+    else __syncthreads();
+}
+template <int NTW>
+__device__ __forceinline__ int group_sync_or(int b) {
+    if constexpr (NTW == 32) {
+        __syncwarp();
+        return __any_sync(0xffffffffu, b);
+    } else {
+        return __syncthreads_or(b);
+    }
+}
+
+template <int OBJ, int GRAD, class T, int NTW = kWideThreads>
 __device__ __forceinline__ void wide_gradient(const T* x, T* g, int d, int tid, WideShared& sh) {
-    const int NT = blockDim.x;
+    const int NT = NTW == 32 ? 32 : (int)blockDim.x;
     if (GRAD == ZEUS_GRAD_ADJOINT) {
         if (tid == 0) sh.adj = adjoint_prep<OBJ>(x, d);
-        __syncthreads();
+        group_sync<NTW>();
     }
     const AdjShared a = sh.adj;
     for (int i = tid; i < d; i += NT) g[i] = grad_component<OBJ, GRAD>(x, d, i, a);
@@ -545,15 +562,19 @@ __host__ __device__ __forceinline__ size_t wide_t_bytes(int d, size_t tsize) {
 // threads of roles 0 and 32 that form the ordered sums of the same phase.
 __device__ __forceinline__ int row_of(int tid, int NT) { return (tid + 32) % NT; }
 
-// One start on one block, from iteration k with `feval` evaluations done:
-// H from Hq (nullptr: identity), x from xq (nullptr: row s of io.x0).
-template <int OBJ, int GRAD, class T>
+// One start on one block (NTW = kWideThreads) or on one warp (NTW = 32),
+// from iteration k with `feval` evaluations done: H from Hq (nullptr:
+// identity), x from xq (nullptr: row s of io.x0).  The warp form performs
+// the same operations in the same order; sums that the block forms on
+// different warps at once, it forms one after the other.
+template <int OBJ, int GRAD, class T, int NTW = kWideThreads>
 __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, const long long s,
                                          int k, int feval, const T* Hq, const T* xq,
                                          const RunIO& io, WideShared& sh,
                                          unsigned char* smem_raw, const int tid,
                                          const bool peer = false) {
-    const int NT = blockDim.x;
+    static_assert(NTW == 32 || NTW >= 96, "a warp, or a block of at least three warps");
+    const int NT = NTW == 32 ? 32 : (int)blockDim.x;
     const int d = p.dim;
     T* H = reinterpret_cast<T*>(smem_raw);
     T* x = H + (size_t)d * d;
@@ -595,10 +616,10 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
     } else {
         for (int e = tid; e < d * d; e += NT) H[e] = (e / d == e % d) ? T(1) : T(0);
     }
-    __syncthreads();
-    wide_gradient<OBJ, GRAD>(x, g, d, tid, sh);
+    group_sync<NTW>();
+    wide_gradient<OBJ, GRAD, T, NTW>(x, g, d, tid, sh);
     if (tid == 0) sh.red[0] = seq_value<OBJ>(AtPoint<T>{x}, d);
-    __syncthreads();
+    group_sync<NTW>();
     double f0 = sh.red[0];
     int status = ZEUS_RUN_MAX_ITER;
     double gnorm = 0.0;
@@ -616,13 +637,19 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             for (int c = 0; c < d; ++c) a = mv_fma(Hr[c], g[c], a);
             pv[r] = -a;
         }
-        const int bad = __syncthreads_or(b);
+        const int bad = group_sync_or<NTW>(b);
         // g'g and g'p on roles 0 and 1 (one warp, one instruction stream:
         // an FP64 warp instruction costs the same for one lane or two)
         double dot01 = 0.0;
         if (d > kDotSplit) {  // g'g on the warp of roles 0-31, g'p on the next
-            if (tid < 64) dot01 = warp_split_dot(g, tid < 32 ? g : pv, d, tid & 31);
-            if (tid == 32) sh.red[0] = dot01;
+            if constexpr (NTW == 32) {
+                const double gp = warp_split_dot(g, pv, d, tid);
+                dot01 = warp_split_dot(g, g, d, tid);
+                if (tid == 0) sh.red[0] = gp;
+            } else {
+                if (tid < 64) dot01 = warp_split_dot(g, tid < 32 ? g : pv, d, tid & 31);
+                if (tid == 32) sh.red[0] = dot01;
+            }
         } else {
             if (tid < 2) dot01 = ordered_dot(g, tid == 0 ? g : pv, d);
             if (tid == 1) sh.red[0] = dot01;
@@ -653,7 +680,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             if (st >= 0) sh.red[1] = sqrt(dot01);  // ||g|| of the final point
             sh.status = st;
         }
-        __syncthreads();
+        group_sync<NTW>();
         if (sh.status >= 0) {
             gnorm = sh.red[1];
             status = sh.status;
@@ -661,10 +688,10 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         }
         double ddir = sh.red[0];
         if (!(ddir < 0.0)) {  // not a descent direction: restart from H = I
-            __syncthreads();
+            group_sync<NTW>();
             for (int e = tid; e < d * d; e += NT) H[e] = (e / d == e % d) ? T(1) : T(0);
             for (int r = tid; r < d; r += NT) pv[r] = -g[r];
-            __syncthreads();
+            group_sync<NTW>();
             if (d > kDotSplit) {
                 if (tid < 32) {
                     const double v = warp_split_dot(g, pv, d, tid);
@@ -673,7 +700,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             } else if (tid == 0) {
                 sh.red[0] = ordered_dot(g, pv, d);
             }
-            __syncthreads();
+            group_sync<NTW>();
             ddir = sh.red[0];
         }
         // ---- line search: trials in chunks, the first accepted wins.
@@ -694,7 +721,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 tb0[mm * d + j] = t0;
                 tb1[mm * d + j] = t1;
             }
-            __syncthreads();
+            group_sync<NTW>();
             if (d > kSumSplit && nt > 1) {
                 // a warp per trial: lane l forms chain l of the sums, the
                 // warp adds the chains in the fixed tree (obj_sum's order)
@@ -725,7 +752,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 fb[tid] = ft;
                 sh.ok[tid] = (m0 + tid < L && ft <= f0 + cA * al[m0 + tid] * ddir) ? 1 : 0;
             }
-            __syncthreads();
+            group_sync<NTW>();
             // every warp finds the first accepted trial itself with one
             // ballot over the flags (no further barrier: the next chunk
             // writes ok and fb only after its terms)
@@ -748,19 +775,24 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         hint = (acc_m >= 0) ? acc_m + 1 : L + 1;
         const T alpha = T((acc_m >= 0) ? al[acc_m] : al[L]);
         for (int j = tid; j < d; j += NT) xn[j] = x[j] + alpha * pv[j];
-        __syncthreads();
+        group_sync<NTW>();
         // ---- gradient at x_new
-        wide_gradient<OBJ, GRAD>(xn, gn, d, tid, sh);
-        __syncthreads();
+        wide_gradient<OBJ, GRAD, T, NTW>(xn, gn, d, tid, sh);
+        group_sync<NTW>();
         // ---- curvature pair; H y formed alongside its sums (used only if
         // the pair passes the curvature test)
         for (int j = tid; j < d; j += NT) {  // s into sv, y over g
             sv[j] = xn[j] - x[j];
             g[j] = gn[j] - g[j];
         }
-        __syncthreads();
+        group_sync<NTW>();
         if (d > kDotSplit) {  // y's, s's, y'y on the warps of roles 0-95
-            if (tid < 96) {
+            if constexpr (NTW == 32) {
+                for (int w = 0; w < 3; ++w) {
+                    const double v = warp_split_dot(w == 1 ? sv : g, w == 2 ? g : sv, d, tid);
+                    if (tid == 0) sh.red[w] = v;
+                }
+            } else if (tid < 96) {
                 const int w = tid >> 5;
                 const double v = warp_split_dot(w == 1 ? sv : g, w == 2 ? g : sv, d, tid & 31);
                 if ((tid & 31) == 0) sh.red[w] = v;
@@ -774,7 +806,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             for (int c = 0; c < d; ++c) a = mv_fma(Hr[c], g[c], a);
             pv[r] = a;
         }
-        __syncthreads();
+        group_sync<NTW>();
         const double sy = sh.red[0], ss = sh.red[1], yy = sh.red[2];
         if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
             const double rho = 1.0 / sy;
@@ -786,7 +818,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             } else if (tid == 0) {
                 sh.red[3] = ordered_dot(g, pv, d);
             }
-            __syncthreads();
+            group_sync<NTW>();
             const double b2 = rho * rho * sh.red[3] + rho;
             const T rt = T(rho), bt = T(b2);
             // A = b2 s - rho Hy and B = -rho s (in the spent scratch rows)
@@ -794,7 +826,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 sc0[r] = (double)mv_fma(bt, sv[r], -(rt * pv[r]));
                 sc1[r] = (double)(-(rt * sv[r]));
             }
-            __syncthreads();
+            group_sync<NTW>();
             // the elements r <= c, mirrored (H stays symmetric): rows r and
             // d - 1 - r together hold d + 1 of them, so t = p (d + 1) + q
             // numbers them without gaps
@@ -823,10 +855,10 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         stalled = stalled_step<T>(f0, fn);
         f0 = fn;
         ++k;
-        __syncthreads();
+        group_sync<NTW>();
     }
     if (tid == 0) sh.red[0] = final_value<OBJ>(x, d, f0);
-    __syncthreads();
+    group_sync<NTW>();
     for (int j = tid; j < d; j += NT) io.x_out[s * d + j] = (double)x[j];
     if (tid == 0) {
         if (io.f_out) io.f_out[s] = sh.red[0];
@@ -837,7 +869,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         atomicAdd(&ctrl->total_feval, (unsigned long long)feval);
         if (!use_stop && status == ZEUS_RUN_CONVERGED) atomicAdd(&ctrl->n_conv, 1ull);
     }
-    __syncthreads();
+    group_sync<NTW>();
 }
 
 // Roles rotate with the block index so that the thread doing the serial
@@ -856,9 +888,10 @@ inline size_t narrow_stride(int d) {
 }
 
 // trials a chunk of the block-per-start line search evaluates at once (up
-// to L + 1: the trials and the point after the last halving)
-__host__ __device__ inline int wide_trials(int d, int L) {
-    int W = (4 * kWideThreads) / (d > 0 ? d : 1);
+// to L + 1: the trials and the point after the last halving); nt threads
+// carry the start
+__host__ __device__ inline int wide_trials(int d, int L, int nt = kWideThreads) {
+    int W = (4 * nt) / (d > 0 ? d : 1);
     if (W < 1) W = 1;
     if (W > 64) W = 64;
     if (W > L + 1) W = L + 1;

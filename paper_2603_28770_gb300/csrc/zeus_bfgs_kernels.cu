@@ -56,6 +56,29 @@ __global__ void __launch_bounds__(kWideThreads)
     }
 }
 
+// One warp per start: four starts to a 128-thread block, each warp pulling
+// the next start for itself; the body is the block kernel's on 32 threads.
+template <int OBJ, int GRAD, class T>
+__global__ void __launch_bounds__(kWideThreads)
+    bfgs_warp_kernel(const zeus_problem p, const int W, const int slot, const double* x0,
+                     double* x_out, double* __restrict__ f_out, double* __restrict__ gnorm_out,
+                     int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
+                     Ctrl* __restrict__ ctrl) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ WideShared shw[kWideThreads / 32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const RunIO io{x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl};
+    unsigned char* mine = smem_raw + (size_t)w * slot;
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(&ctrl->q_head, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if ((long long)item >= p.n_starts) break;
+        wide_run<OBJ, GRAD, T, 32>(p, W, (long long)item, 0, 0, nullptr, nullptr, io, shw[w], mine,
+                                   lane);
+    }
+}
+
 // Narrow and wide in one cooperative launch.  Every block first takes lane
 // tiles (tile starts, one lane each, with the hand-over budget); once no
 // tile is left it serves the hand-over queue, so the starts handed over
@@ -236,6 +259,23 @@ static cudaError_t bfgs_go(const zeus_problem& p, const BfgsLaunch& L, const dou
                            double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
                            int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st) {
     cudaError_t e;
+    if (L.warp) {
+        auto kw = bfgs_warp_kernel<OBJ, GRAD, T>;
+        const size_t smem = 4 * L.warp_slot;
+        int dev = 0, sms = 0, per_sm = 0;
+        e = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kw, kWideThreads, smem);
+        if (e != cudaSuccess) return e;
+        long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
+        const long long need = (p.n_starts + 3) / 4;
+        if (blocks > need) blocks = need;
+        kw<<<(int)blocks, kWideThreads, smem, st>>>(p, L.W, (int)L.warp_slot, x0, x_out, f_out,
+                                                    gnorm_out, status_out, iters_out, ctrl);
+        return cudaGetLastError();
+    }
     if (L.narrow && L.budget > 0 && q.ready) {
         e = fused_go<OBJ, GRAD, T>(p, L, x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl,
                                    q, st);

@@ -25,7 +25,7 @@ namespace {
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-bool valid_lanes(int g) { return g == 0 || g == 1 || g == kWideThreads || g == 256; }
+bool valid_lanes(int g) { return g == 0 || g == 1 || g == 32 || g == kWideThreads || g == 256; }
 
 int validate(const zeus_problem* p) {
     if (!p) return ZEUS_EINVAL;
@@ -223,7 +223,8 @@ int zeus_plan_info(const zeus_problem* p, zeus_plan* plan) {
     plan->handover = L.budget > 0 ? 1 : 0;
     plan->lbfgs = L.lbfgs ? 1 : 0;
     plan->stream = (L.stream && !L.lbfgs) ? 1 : 0;
-    plan->block = (!L.narrow && !L.stream) ? 1 : 0;
+    plan->block = (!L.narrow && !L.stream && !L.warp) ? 1 : 0;
+    plan->warp = L.warp ? 1 : 0;
     plan->blocks = L.stream ? L.stream_blocks : L.wide_blocks;
     plan->h_bytes = L.lbfgs ? 0 : (int64_t)p->dim * p->dim * (p->precision == ZEUS_FP32_GUARDED ? 4 : 8);
     return ZEUS_OK;

@@ -105,6 +105,8 @@ struct BfgsLaunch {
     size_t stream_smem;   // its dynamic shared memory
     size_t hslot_bytes;   // bytes of all H slots
     bool lbfgs;           // L-BFGS: the streaming kernel's limited-memory variant (no H)
+    bool warp = false;    // one warp per start (threads_per_start 32), four per block
+    size_t warp_slot = 0; // dynamic shared memory of one warp's start
 };
 
 // Device tables of a batch (zeus_batch_*): per-problem parameters and
@@ -165,9 +167,9 @@ cudaError_t launch_batch_argmin(const BatchDev& bd, const double* f_out, zeus_re
 // counter `cls`; cls < 0: the hand-over queue
 // user: the batch holds user objectives (the kernel variant that has them)
 cudaError_t launch_batch_bfgs(const BatchDev& bd, int precision, int grad_mode, bool user, int cls,
-                              int first, int count, size_t smem, double* x_out, double* f_out,
-                              double* gnorm_out, int32_t* status_out, int32_t* iters_out,
-                              cudaStream_t st);
+                              int first, int count, size_t smem, bool warp_items, double* x_out,
+                              double* f_out, double* gnorm_out, int32_t* status_out,
+                              int32_t* iters_out, cudaStream_t st);
 
 // the kernels of one (gradient mode, precision) pair, compiled in a
 // translation unit of their own (zeus_bfgs_kernels.cu, zeus_batch_kernels.cu)
@@ -177,8 +179,8 @@ cudaError_t bfgs_launch_gt(const zeus_problem& p, const BfgsLaunch& L, const dou
                            int32_t* iters_out, Ctrl* ctrl, const Queue& q, cudaStream_t st);
 template <int GRAD, class T, bool U>
 cudaError_t batch_launch_gt(const BatchDev& bd, int cls, int first, int count, size_t smem,
-                            double* x_out, double* f_out, double* gnorm_out, int32_t* status_out,
-                            int32_t* iters_out, cudaStream_t st);
+                            bool warp_items, double* x_out, double* f_out, double* gnorm_out,
+                            int32_t* status_out, int32_t* iters_out, cudaStream_t st);
 
 cudaError_t launch_argmin(const double* f, long long n, Ctrl* ctrl, ArgPair* partials,
                           zeus_result* res, int mode, cudaStream_t st);

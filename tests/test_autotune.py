@@ -20,7 +20,7 @@ def test_buckets():
 
 def test_tuner_picks_fastest_and_caches(z, tmp_path):
     from paper_2603_28770_gb300.autotune import Autotuner
-    cost = {0: 3.0, 1: 2.0, 128: 5.0}
+    cost = {0: 3.0, 1: 2.0, 32: 4.0, 128: 5.0}
     calls = []
 
     def measure(probe):
@@ -33,12 +33,13 @@ def test_tuner_picks_fastest_and_caches(z, tmp_path):
     probs = [z.Problem(objective="rastrigin", dim=10, n_starts=500, seed=i) for i in range(5)]
     probs.append(z.Problem(objective="rastrigin", dim=30, n_starts=100))  # lanes do not fit in FP64
     probs.append(z.Problem(objective="ackley", dim=9, n_starts=100, threads_per_start=128))
-    t = Autotuner(str(path), probe_problems=3, probe_starts=64, measure=measure, device_name="dev")
+    t = Autotuner(str(path), probe_problems=3, probe_starts=64, measure=measure, device_name="dev",
+                  probe_total=0)
     out = t.apply(probs)
     assert [q.threads_per_start for q in out[:5]] == [1] * 5
     assert out[5].threads_per_start in (0, 128) and out[6].threads_per_start == 128
     k30 = t.key(probs[5].to_c())
-    assert set(t.table["dev"][k30]["ms"]) == {"0", "128"}  # the lane layout was not a candidate
+    assert set(t.table["dev"][k30]["ms"]) == {"0", "32", "128"}  # lanes were not a candidate
     assert t.key(probs[6].to_c()) not in t.table["dev"]    # explicit choices are not tuned
     saved = json.loads(path.read_text())
     assert saved["dev"][t.key(probs[0].to_c())]["threads_per_start"] == 1
@@ -48,7 +49,8 @@ def test_tuner_picks_fastest_and_caches(z, tmp_path):
     assert [q.threads_per_start for q in t2.apply(probs[:5])] == [1] * 5
     assert len(calls) == n
     # another device name is tuned separately
-    t3 = Autotuner(str(path), probe_problems=3, probe_starts=64, measure=measure, device_name="other")
+    t3 = Autotuner(str(path), probe_problems=3, probe_starts=64, measure=measure, device_name="other",
+                   probe_total=0)
     t3.apply(probs[:1])
     assert len(calls) > n and set(json.loads(path.read_text())) == {"dev", "other"}
 

@@ -78,7 +78,7 @@ def test_defaults(z):
     dict(n_starts=2**31), dict(pso_iters=-1), dict(bfgs_max_iters=-1), dict(ls_max_iters=0),
     dict(required_converged=-2), dict(grad_tol=-1.0), dict(grad_tol=float("nan")), dict(w=float("inf")),
     dict(armijo_c=0.0), dict(armijo_c=1.0), dict(backtrack=1.0), dict(backtrack=0.0), dict(grad_mode=2),
-    dict(start_from_pbest=2), dict(threads_per_start=3), dict(threads_per_start=32), dict(threads_per_start=512), dict(precision=5),
+    dict(start_from_pbest=2), dict(threads_per_start=3), dict(threads_per_start=64), dict(threads_per_start=512), dict(precision=5),
     dict(lbfgs_m=-1), dict(lbfgs_m=65),
 ])
 def test_validation_rejects(z, kw):
@@ -168,7 +168,7 @@ def test_batch_plan(z):
     # block-per-start classes first, then the lane-tile classes (which run
     # on the library's second stream with the hand-over launch)
     kinds = [pl.class_kind[c] for c in range(pl.n_classes)]
-    assert set(kinds) <= {0, 1} and kinds == sorted(kinds, reverse=True)
+    assert set(kinds) <= {0, 1, 2} and kinds == sorted(kinds, reverse=True)
     # work items: one per block-per-start start, one per lane tile of <= 128 starts
     lane = [p for p in probs if z.zeus_plan_info(p)["narrow"]]
     block = [p for p in probs if not z.zeus_plan_info(p)["narrow"]]

@@ -22,6 +22,7 @@ BOX = dict(workloads.BOXES, goldstein_price=(-2.0, 2.0), quadratic=(-3.0, 3.0))
 # (objective, d, N, PSO updates, BFGS cap, extra fields): lane tiles with
 # and without hand-over, block-per-start problems, ragged N (1, 129, 257),
 # no PSO update, start from the personal bests, forced kernel choices
+# (one lane, one block or one warp per start)
 CASES = [
     ("rosenbrock", 2, 130, 5, 200, {}),
     ("rastrigin", 10, 300, 3, 400, {}),
@@ -35,6 +36,9 @@ CASES = [
     ("rosenbrock", 16, 100, 2, 300, {}),
     ("rastrigin", 20, 50, 1, 40, {"threads_per_start": 1}),
     ("ackley", 5, 60, 2, 40, {"threads_per_start": 128}),
+    ("rosenbrock", 12, 70, 2, 200, {"threads_per_start": 32}),
+    ("ackley", 40, 30, 1, 50, {"threads_per_start": 32}),
+    ("rastrigin", 3, 101, 2, 100, {"threads_per_start": 32}),
 ]
 
 
@@ -160,7 +164,7 @@ def test_autotuned_batch_is_bitwise_the_same(z, tmp_path):
     probs = _problems(z)
     ref = z.Batch(probs)
     ref.solve()
-    t = Autotuner(str(tmp_path / "tune.json"), probe_problems=2, probe_starts=32, reps=1)
+    t = Autotuner(str(tmp_path / "tune.json"), probe_problems=2, probe_starts=32, reps=1, probe_total=256)
     b = z.Batch(probs, autotuner=t)
     assert t.table[t.device_name()]
     b.solve()

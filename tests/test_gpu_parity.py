@@ -152,9 +152,9 @@ def test_bfgs_first_20_iterations(z, ora, obj, d, n, lo, hi, mode):
     assert math.isnan(s["gbest_f"]) and s["gbest_index"] == -1
 
 
-@pytest.mark.parametrize("mode", [0, 1, 128])
+@pytest.mark.parametrize("mode", [0, 1, 32, 128])
 def test_kernel_choice_is_bitwise_neutral(z, ora, mode):
-    # one lane per start, one block per start, or the automatic hand-over:
+    # one lane, one warp or one block per start, or the automatic hand-over:
     # the same bits as the oracle (long cap so that starts get handed over)
     from parity import assert_bitwise
     d, n = 10, 600
@@ -277,8 +277,9 @@ BITWISE_WIDE_CASES = [("rastrigin", 40, 64, -5.12, 5.12), ("rosenbrock", 64, 32,
                       ("ackley", 100, 16, -5.0, 5.0), ("quadratic", 130, 8, -1.0, 1.0)]
 
 
-@pytest.mark.parametrize("obj,d,n,lo,hi,mode", [c + (m,) for c in BITWISE_CASES for m in (1, 128)]
-                         + [c + (128,) for c in BITWISE_WIDE_CASES])
+@pytest.mark.parametrize("obj,d,n,lo,hi,mode", [c + (m,) for c in BITWISE_CASES for m in (1, 32, 128)]
+                         + [c + (128,) for c in BITWISE_WIDE_CASES]
+                         + [c + (32,) for c in BITWISE_WIDE_CASES if c[1] <= 64])
 def test_bitwise_against_oracle(z, ora, obj, d, n, lo, hi, mode):
     # every sum runs in the oracle's order (one lane per start, or gathered
     # on one thread of the block), every elementary function follows the
@@ -327,7 +328,7 @@ def test_elementary_functions(z, ora):
 
 # -------------------------------------------------- FP32 form with FP64 guards
 
-@pytest.mark.parametrize("mode", [0, 1, 128])
+@pytest.mark.parametrize("mode", [0, 1, 32, 128])
 def test_fp32_form_kernel_choice_is_bitwise_neutral(z, mode):
     # the FP32 form performs the same operations in the same order in both
     # kernels, so where a start runs does not change a bit

@@ -44,16 +44,16 @@ def _reference(ora, key, fields, x0, **kw):
 
 
 # (objective, d, starts, box, kernel layouts, max excused fraction)
-# layouts: 1 one lane per start, 128 one block per start (H in shared
-# memory), 0 automatic (lane tiles and the hand-over in one cooperative
+# layouts: 1 one lane per start, 32 one warp per start, 128 one block per
+# start (H in shared memory), 0 automatic (lane tiles and the hand-over in one cooperative
 # launch at d <= 16), 256 one block per start with H streamed from HBM
 CASES = [
-    ("rastrigin", 10, 512, -5.12, 5.12, (1, 128, 0, 256), None),
-    ("ackley", 10, 512, -5.0, 5.0, (1, 128, 0, 256), None),
-    ("rosenbrock", 10, 512, -5.0, 5.0, (1, 128, 0, 256), None),
-    ("rastrigin", 40, 256, -5.12, 5.12, (128, 256), None),
-    ("ackley", 40, 256, -5.0, 5.0, (128, 256), None),
-    ("rosenbrock", 40, 256, -5.0, 5.0, (128, 256), 0.02),
+    ("rastrigin", 10, 512, -5.12, 5.12, (1, 32, 128, 0, 256), None),
+    ("ackley", 10, 512, -5.0, 5.0, (1, 32, 128, 0, 256), None),
+    ("rosenbrock", 10, 512, -5.0, 5.0, (1, 32, 128, 0, 256), None),
+    ("rastrigin", 40, 256, -5.12, 5.12, (32, 128, 256), None),
+    ("ackley", 40, 256, -5.0, 5.0, (32, 128, 256), None),
+    ("rosenbrock", 40, 256, -5.0, 5.0, (32, 128, 256), 0.02),
     ("rastrigin", 100, 128, -5.12, 5.12, (128, 256), None),
     ("ackley", 100, 128, -5.0, 5.0, (128, 256), None),
     ("rosenbrock", 100, 128, -5.0, 5.0, (128, 256), 0.02),
