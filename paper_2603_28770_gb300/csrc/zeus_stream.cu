@@ -471,10 +471,12 @@ struct StreamShared {
     double red[(kStreamWarps + 1) * 2 * kStreamTrials];
 };
 
-// LB = false: dense H streamed from its HBM slot (the pass above).
+// LB = false: dense H streamed from its HBM slot (the pass above; STG:
+// rows staged by bulk copies, compiled apart so that the direct pass keeps
+// its own registers).
 // LB = true: L-BFGS (the paper's future work, Section VI) with the m most
 // recent pairs in shared memory and the two-loop recursion for p; no H.
-template <int OBJ, int GRAD, class T, bool LB>
+template <int OBJ, int GRAD, class T, bool LB, bool STG = false>
 __global__ void __launch_bounds__(kStreamThreads, 4)
     bfgs_stream_kernel(const zeus_problem p, const double* x0, double* x_out,
                        double* __restrict__ f_out, double* __restrict__ gnorm_out,
@@ -505,7 +507,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     double* gam_m = rho_m + lm;  // s'y / y'y of each pair (the initial scaling)
     double* al_m = gam_m + lm;   // alpha of the first loop
     // staged pass (dense H only): chunks of rows in shared memory
-    const StagePlan sp = LB ? StagePlan{0, 0} : stage_plan(d, (int)sizeof(T));
+    const StagePlan sp = (LB || !STG) ? StagePlan{0, 0} : stage_plan(d, (int)sizeof(T));
     unsigned char* stage = smem_raw + stage_offset(d, sizeof(T));
     unsigned chunk_ctr = 0;
     if (sp.ns > 0) {
@@ -642,13 +644,16 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
                 for (int j = tid; j < d; j += NT) u[j] = gn[j];
                 __syncthreads();
             } else {
-                if (sp.ns > 0 && !ident) {
-                    if (!h_pass_staged<T>(Hs, d, corr, sv, hy, Av, Bv, gn, u, stage, stage_bar, sp,
-                                          chunk_ctr, spin_limit, ctrl))
-                        return;  // a chunk never arrived: the error word is set
-                } else {
-                    h_pass<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u);
+                bool staged = false;
+                if constexpr (STG) {
+                    if (sp.ns > 0 && !ident) {
+                        if (!h_pass_staged<T>(Hs, d, corr, sv, hy, Av, Bv, gn, u, stage, stage_bar,
+                                              sp, chunk_ctr, spin_limit, ctrl))
+                            return;  // a chunk never arrived: the error word is set
+                        staged = true;
+                    }
                 }
+                if (!staged) h_pass<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u);
                 n_read += ident ? 0 : 1;             // H_{k-1} read unless still I
                 n_write += (corr || ident) ? 1 : 0;  // H_k stored when it changed
                 ident = false;
@@ -773,7 +778,9 @@ static cudaError_t stream_go(const zeus_problem& p, const double* x0, double* x_
                                                          iters_out, ctrl, nullptr, wait_limit());
         return cudaGetLastError();
     }
-    auto kern = bfgs_stream_kernel<OBJ, GRAD, T, false>;
+    const bool stg = stage_plan(p.dim, (int)sizeof(T)).ns > 0;
+    auto kern = stg ? bfgs_stream_kernel<OBJ, GRAD, T, false, true>
+                    : bfgs_stream_kernel<OBJ, GRAD, T, false, false>;
     const size_t sm = stream_smem(p.dim, sizeof(T));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
