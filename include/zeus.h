@@ -23,6 +23,17 @@
  *    undefined afterwards.  Two calls in flight must not share a workspace.
  *  - Validation errors (ZEUS_EINVAL, ZEUS_EWORKSPACE, ZEUS_EUNSUPPORTED) are
  *    reported before any work is enqueued.
+ *  - Host threads: every entry point may be called from several host
+ *    threads at once, on one device or several, provided that no two calls
+ *    in flight share a workspace, a zeus_context, a batch plan's device
+ *    tables or an output buffer (one context per host thread for
+ *    zeus_solve_host).  The library's process-wide state is small and
+ *    guarded: the bounded-wait limit (an atomic, zeus_set_wait_limit), the
+ *    second stream of the batched form on each device (created once, under
+ *    a lock, by zeus_batch_prepare) and the scratch array of
+ *    zeus_solve_from_noalloc (its enqueue is serialised under a lock, but
+ *    overlapping calls share the array: see there).  Kernel attributes are
+ *    set before each launch, with the same value every time.
  */
 #ifndef ZEUS_H
 #define ZEUS_H

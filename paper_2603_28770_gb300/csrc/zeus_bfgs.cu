@@ -88,7 +88,9 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
         L->stream_smem = 0;
         L->hslot_bytes = 0;
         L->warp = true;
-        return 4 * L->warp_slot <= cap ? ZEUS_OK : ZEUS_EUNSUPPORTED;
+        // four slots of dynamic and four WideShared of static shared memory
+        return 4 * L->warp_slot + 4 * sizeof(WideShared) <= 227 * 1024 ? ZEUS_OK
+                                                                        : ZEUS_EUNSUPPORTED;
     }
     const size_t row = narrow_stride(d) * ts;
     const bool narrow_fits = row * 32 <= cap;
@@ -102,8 +104,14 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
     L->narrow_blocks = (int)((p.n_starts + nthreads - 1) / nthreads);
     L->W = wide_trials(d, p.ls_max_iters);
     L->wide_smem = wide_smem(d, L->W, p.ls_max_iters, ts);
-    // H streamed from HBM when the block-per-start kernel cannot hold it
-    L->stream = (req == 256) || (!L->narrow && L->wide_smem > cap);
+    // H streamed from HBM when the block-per-start kernel could not hold the
+    // full d x d matrix.  The packed triangle would fit up to about 1.4 times
+    // that d, but only one such block fits an SM, and the streamed kernel
+    // (four 256-thread blocks per SM) is faster there: 0.66 s against 2.48 s
+    // for the d = 256 chain in FP32.
+    const size_t full = wide_smem(d, L->W, p.ls_max_iters, ts) +
+                        ((size_t)d * d - (size_t)d * (d + 1) / 2) * ts;
+    L->stream = (req == 256) || (!L->narrow && full > cap);
     L->stream_blocks = stream_blocks(p);
     L->stream_smem = stream_smem(d, ts);
     L->hslot_bytes = L->stream ? (size_t)L->stream_blocks * d * d * ts : 0;

@@ -511,7 +511,7 @@ struct WideShared {
     int status;
     int accepted_m;
     int pad;
-    double red[4];
+    double red[8];
     AdjShared adj;
     int ok[64];
 };
@@ -553,8 +553,46 @@ __device__ __forceinline__ void wide_gradient(const T* x, T* g, int d, int tid, 
     for (int i = tid; i < d; i += NT) g[i] = grad_component<OBJ, GRAD>(x, d, i, a);
 }
 
+// The block- and warp-per-start forms hold the symmetric H as its upper
+// triangle, packed by rows: (r, c), r <= c, at tri_off(r) + c - r.  Every
+// element is the one the full matrix holds (the update keeps H exactly
+// symmetric), so rows read through tri_row_dot carry the same values in the
+// same column order; the packed form halves the shared memory of H.
+__host__ __device__ __forceinline__ int tri_off(int r, int d) { return r * d - (r * (r - 1)) / 2; }
+
+// Element t of the triangle in an order that balances threads: rows p and
+// d - 1 - p together hold d + 1 elements, so t = p (d + 1) + q numbers them
+// without gaps.
+__device__ __forceinline__ void tri_pair(int t, int d, int& r, int& c) {
+    const int pr = t / (d + 1), q = t - pr * (d + 1);
+    if (q < d - pr) {
+        r = pr;
+        c = pr + q;
+    } else {
+        r = d - 1 - pr;
+        c = r + (q - (d - pr));
+    }
+}
+
+// (H v)_r over the packed triangle, columns in order, one fused
+// multiply-add per term: (c, r) for c < r, then (r, c).  The element index
+// is selected per column, so the lanes of a warp never diverge.
+template <class T>
+__device__ __forceinline__ T tri_row_dot(const T* H, int d, int r, const T* v) {
+    int lo = r;                          // (c, r) while c < r
+    const int hi = tri_off(r, d) - r;    // (r, c) = hi + c for c >= r
+    T a = T(0);
+    for (int c = 0; c < d; ++c) {
+        const int e = c < r ? lo : hi + c;
+        a = mv_fma(H[e], v[c], a);
+        lo += d - c - 1;
+    }
+    return a;
+}
+
 __host__ __device__ __forceinline__ size_t wide_t_bytes(int d, size_t tsize) {
-    return (((size_t)d * d + 6 * (size_t)d) * tsize + 7) & ~size_t(7);
+    const size_t nu = (size_t)d * (d + 1) / 2;
+    return ((nu + 6 * (size_t)d) * tsize + 7) & ~size_t(7);
 }
 
 // Row r of a matrix-vector product goes to the thread of role
@@ -576,8 +614,9 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
     static_assert(NTW == 32 || NTW >= 96, "a warp, or a block of at least three warps");
     const int NT = NTW == 32 ? 32 : (int)blockDim.x;
     const int d = p.dim;
-    T* H = reinterpret_cast<T*>(smem_raw);
-    T* x = H + (size_t)d * d;
+    T* H = reinterpret_cast<T*>(smem_raw);  // packed upper triangle
+    const int nu = d * (d + 1) / 2;
+    T* x = H + nu;
     T* g = x + d;
     T* pv = g + d;
     T* xn = pv + d;
@@ -611,10 +650,12 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
     } else {
         for (int j = tid; j < d; j += NT) x[j] = T(io.x0[s * d + j]);
     }
-    if (Hq) {
-        for (int e = tid; e < d * d; e += NT) H[e] = peer ? __ldcg(Hq + e) : Hq[e];
-    } else {
-        for (int e = tid; e < d * d; e += NT) H[e] = (e / d == e % d) ? T(1) : T(0);
+    for (int t = tid; t < nu; t += NT) {  // Hq holds the full matrix, row-major
+        int r, c;
+        tri_pair(t, d, r, c);
+        const int e = tri_off(r, d) + c - r;
+        if (Hq) H[e] = peer ? __ldcg(Hq + (size_t)r * d + c) : Hq[(size_t)r * d + c];
+        else H[e] = r == c ? T(1) : T(0);
     }
     group_sync<NTW>();
     wide_gradient<OBJ, GRAD, T, NTW>(x, g, d, tid, sh);
@@ -631,12 +672,7 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         // if the start goes on)
         int b = 0;
         for (int j = tid; j < d; j += NT) b |= !isfinite(g[j]);
-        for (int r = row_of(tid, NT); r < d; r += NT) {
-            const T* Hr = H + r * d;
-            T a = T(0);
-            for (int c = 0; c < d; ++c) a = mv_fma(Hr[c], g[c], a);
-            pv[r] = -a;
-        }
+        for (int r = row_of(tid, NT); r < d; r += NT) pv[r] = -tri_row_dot(H, d, r, g);
         const int bad = group_sync_or<NTW>(b);
         // g'g and g'p on roles 0 and 1 (one warp, one instruction stream:
         // an FP64 warp instruction costs the same for one lane or two)
@@ -689,7 +725,11 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         double ddir = sh.red[0];
         if (!(ddir < 0.0)) {  // not a descent direction: restart from H = I
             group_sync<NTW>();
-            for (int e = tid; e < d * d; e += NT) H[e] = (e / d == e % d) ? T(1) : T(0);
+            for (int t = tid; t < nu; t += NT) {
+                int r, c;
+                tri_pair(t, d, r, c);
+                H[tri_off(r, d) + c - r] = r == c ? T(1) : T(0);
+            }
             for (int r = tid; r < d; r += NT) pv[r] = -g[r];
             group_sync<NTW>();
             if (d > kDotSplit) {
@@ -800,16 +840,26 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
         } else if (tid < 3) {  // on roles 0-2 (one warp, one instruction stream)
             sh.red[tid] = ordered_dot(tid == 1 ? sv : g, tid == 2 ? g : sv, d);
         }
-        for (int r = row_of(tid, NT); r < d; r += NT) {  // Hy into p (the direction is spent)
-            const T* Hr = H + r * d;
-            T a = T(0);
-            for (int c = 0; c < d; ++c) a = mv_fma(Hr[c], g[c], a);
-            pv[r] = a;
-        }
+        for (int r = row_of(tid, NT); r < d; r += NT)  // Hy into p (the direction is spent)
+            pv[r] = tri_row_dot(H, d, r, g);
         group_sync<NTW>();
-        const double sy = sh.red[0], ss = sh.red[1], yy = sh.red[2];
-        if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
-            const double rho = 1.0 / sy;
+        const double sy = sh.red[0];
+        bool pass;
+        double rho;
+        if constexpr (NTW == 32) {
+            pass = sy > 1e-12 * sqrt(sh.red[1]) * sqrt(sh.red[2]);
+            rho = 1.0 / sy;
+            if (pass) {
+                const double v = d > kDotSplit ? warp_split_dot(g, pv, d, tid)
+                                               : (tid == 0 ? ordered_dot(g, pv, d) : 0.0);
+                if (tid == 0) sh.red[3] = v;
+                group_sync<NTW>();
+            }
+        } else {
+            // the scalars of the test and the update on four sub-partitions
+            // at once, each formed by one thread: y'Hy on the warp of role 0
+            // (whether or not the pair passes), |s|, |y| and 1/y's on the
+            // warps of roles 32, 64 and NT - 32
             if (d > kDotSplit) {
                 if (tid < 32) {
                     const double v = warp_split_dot(g, pv, d, tid);
@@ -818,7 +868,14 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
             } else if (tid == 0) {
                 sh.red[3] = ordered_dot(g, pv, d);
             }
+            if (tid == 32) sh.red[4] = sqrt(sh.red[1]);
+            if (tid == 64) sh.red[5] = sqrt(sh.red[2]);
+            if (tid == NT - 32) sh.red[6] = 1.0 / sy;
             group_sync<NTW>();
+            pass = sy > 1e-12 * sh.red[4] * sh.red[5];
+            rho = sh.red[6];
+        }
+        if (pass) {
             const double b2 = rho * rho * sh.red[3] + rho;
             const T rt = T(rho), bt = T(b2);
             // A = b2 s - rho Hy and B = -rho s (in the spent scratch rows)
@@ -827,23 +884,12 @@ __device__ __forceinline__ void wide_run(const zeus_problem& p, const int W, con
                 sc1[r] = (double)(-(rt * sv[r]));
             }
             group_sync<NTW>();
-            // the elements r <= c, mirrored (H stays symmetric): rows r and
-            // d - 1 - r together hold d + 1 of them, so t = p (d + 1) + q
-            // numbers them without gaps
-            const int nu = d * (d + 1) / 2;
+            // the elements r <= c (H stays symmetric)
             for (int t = tid; t < nu; t += NT) {
-                const int pr = t / (d + 1), q = t - pr * (d + 1);
                 int r, c;
-                if (q < d - pr) {
-                    r = pr;
-                    c = pr + q;
-                } else {
-                    r = d - 1 - pr;
-                    c = r + (q - (d - pr));
-                }
-                const T v = mv_fma(sv[c], T(sc0[r]), mv_fma(pv[c], T(sc1[r]), H[r * d + c]));
-                H[r * d + c] = v;
-                H[c * d + r] = v;
+                tri_pair(t, d, r, c);
+                const int e = tri_off(r, d) + c - r;
+                H[e] = mv_fma(sv[c], T(sc0[r]), mv_fma(pv[c], T(sc1[r]), H[e]));
             }
         }
         // x, g <- x_new, g_new in the same phase (the update reads neither;

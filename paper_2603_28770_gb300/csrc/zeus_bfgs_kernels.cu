@@ -233,7 +233,7 @@ static cudaError_t fused_go(const zeus_problem& p, const BfgsLaunch& L, const do
     if (tile < 32) tile = 32;
     const size_t smem = (size_t)tile * row > L.wide_smem ? (size_t)tile * row : L.wide_smem;
     auto kf = bfgs_fused_kernel<OBJ, GRAD, T>;
-    e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_smem(kf, smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, kWideThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorNotSupported;
@@ -263,7 +263,7 @@ static cudaError_t bfgs_go(const zeus_problem& p, const BfgsLaunch& L, const dou
         auto kw = bfgs_warp_kernel<OBJ, GRAD, T>;
         const size_t smem = 4 * L.warp_slot;
         int dev = 0, sms = 0, per_sm = 0;
-        e = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_smem(kw, smem);
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
@@ -284,8 +284,7 @@ static cudaError_t bfgs_go(const zeus_problem& p, const BfgsLaunch& L, const dou
     }
     if (L.narrow) {
         auto kn = bfgs_narrow_kernel<OBJ, GRAD, T>;
-        e = cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.narrow_smem);
+        e = allow_smem(kn, L.narrow_smem);
         if (e != cudaSuccess) return e;
         kn<<<L.narrow_blocks, L.narrow_threads, L.narrow_smem, st>>>(
             p, L.stride, L.budget, x0, x_out, f_out, gnorm_out, status_out, iters_out, ctrl, q);
@@ -294,7 +293,7 @@ static cudaError_t bfgs_go(const zeus_problem& p, const BfgsLaunch& L, const dou
         if (L.budget == 0) return cudaSuccess;
     }
     auto kw = bfgs_wide_kernel<OBJ, GRAD, T>;
-    e = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.wide_smem);
+    e = allow_smem(kw, L.wide_smem);
     if (e != cudaSuccess) return e;
     kw<<<L.wide_blocks, kWideThreads, L.wide_smem, st>>>(p, L.W, x0, x_out, f_out, gnorm_out,
                                                          status_out, iters_out, ctrl, q,

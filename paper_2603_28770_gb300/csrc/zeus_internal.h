@@ -50,6 +50,23 @@ unsigned wait_limit();
 
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Raises a kernel's dynamic shared-memory limit to the most the device
+// allows beside the kernel's static shared memory: the same value on every
+// call, so that calls from several host threads never lower it under one
+// another's launch.  Fails (cudaErrorInvalidValue) if `need` does not fit.
+template <class K>
+inline cudaError_t allow_smem(K* kernel, size_t need) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const int maxdyn = optin - (int)fa.sharedSizeBytes;
+    if ((long long)need > (long long)maxdyn) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn);
+}
+
 // Workspace carve-up (offsets in bytes from the workspace base).
 constexpr int kMaxSMs = 1024;  // size of the per-SM table of the fused kernel
 

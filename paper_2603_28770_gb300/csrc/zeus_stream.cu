@@ -20,6 +20,8 @@
 // path is compared with the oracle within tolerance, not bit for bit.
 // T = float is the FP32 form (FP64 for y's, |s|, |y|, g'p, y'Hy, rho, the
 // Armijo sums and the final value); T = double is the FP64 method.
+#include <type_traits>
+
 #include "zeus_device.cuh"
 #include "zeus_internal.h"
 #include "zeus_tma.cuh"
@@ -37,12 +39,19 @@ __device__ __forceinline__ T warp_sum_t(T v) {
     return v;
 }
 
+struct NoPost {
+    __device__ void operator()(const double*) const {}
+};
+
 // Sum N doubles over the block; every thread gets the totals.  Warp
 // shuffles first, then warp 0 adds the per-warp partials of each value over
 // groups of kStreamWarps lanes (three shuffle levels instead of one thread
-// adding eight partials per value).
-template <int N>
-__device__ __forceinline__ void block_sum(double (&v)[N], double* red) {
+// adding eight partials per value).  `post`, if given, runs on thread 0
+// with the N totals before the barrier that publishes them: scalars that
+// every thread needs and one thread can form (square roots, quotients)
+// are written there once instead of on every warp.
+template <int N, class Post = NoPost>
+__device__ __forceinline__ void block_sum(double (&v)[N], double* red, Post post = Post()) {
     static_assert(kStreamWarps == 8, "second stage assumes 8 warps");
     static_assert(N >= 1 && N <= 8, "up to eight sums");
     constexpr int P = N <= 1 ? 1 : (N <= 2 ? 2 : (N <= 4 ? 4 : 8));  // N rounded up
@@ -82,6 +91,10 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double* red) {
             b += __shfl_xor_sync(0xffffffffu, b, 2);
             b += __shfl_xor_sync(0xffffffffu, b, 1);
             if ((lane & 7) == 0 && i < N) red[8 * N + i] = b;
+        }
+        if constexpr (!std::is_same<Post, NoPost>::value) {
+            __syncwarp();
+            if (lane == 0) post(red + 8 * N);
         }
     }
     __syncthreads();
@@ -136,7 +149,8 @@ __device__ __forceinline__ double finish_parts(double s0, double s1, int d) {
     return s0;
 }
 
-// Trial values f(x + a_m p), m = 0..n-1 (n <= kStreamTrials), all threads
+// Trial values f(x + a_m p), m = 0..n-1 (n <= kStreamTrials) into out,
+// formed by thread 0 and visible to all threads on return
 template <int OBJ, class T>
 __device__ __forceinline__ void block_values(const T* x, const T* p, const double* alpha, int n,
                                              int d, double* out, double* red) {
@@ -154,10 +168,9 @@ __device__ __forceinline__ void block_values(const T* x, const T* p, const doubl
             }
         }
     }
-    block_sum<2 * kStreamTrials>(s, red);
-#pragma unroll
-    for (int m = 0; m < kStreamTrials; ++m)
-        if (m < n) out[m] = finish_parts<OBJ, T>(s[2 * m], s[2 * m + 1], d);
+    block_sum<2 * kStreamTrials>(s, red, [=](const double* t) {
+        for (int m = 0; m < n; ++m) out[m] = finish_parts<OBJ, T>(t[2 * m], t[2 * m + 1], d);
+    });
 }
 
 template <int OBJ, int GRAD, class T>
@@ -552,17 +565,19 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
                 v3[2] += (double)(g[j] * pv[j]);
             }
             block_sum<3>(v3, sh.red);
-            gnorm = sqrt(v3[0]);
-            int st = -1;
-            if (k >= K) st = ZEUS_RUN_MAX_ITER;
-            else if (use_stop && *((volatile int*)&ctrl->stop)) st = ZEUS_RUN_STOPPED;
-            else if (!isfinite(f0) || v3[1] != 0.0) st = ZEUS_RUN_NONFINITE;
-            else if (gnorm < tol) st = ZEUS_RUN_CONVERGED;
-            else if (use_target && f0 <= p.target_f) st = ZEUS_RUN_CONVERGED;
-            else if (stalled) st = ZEUS_RUN_STALLED;
-            if (tid == 0) sh.status = st;
+            if (tid == 0) {  // the tests on one thread; |g| is its output alone
+                gnorm = sqrt(v3[0]);
+                int t = -1;
+                if (k >= K) t = ZEUS_RUN_MAX_ITER;
+                else if (use_stop && *((volatile int*)&ctrl->stop)) t = ZEUS_RUN_STOPPED;
+                else if (!isfinite(f0) || v3[1] != 0.0) t = ZEUS_RUN_NONFINITE;
+                else if (gnorm < tol) t = ZEUS_RUN_CONVERGED;
+                else if (use_target && f0 <= p.target_f) t = ZEUS_RUN_CONVERGED;
+                else if (stalled) t = ZEUS_RUN_STALLED;
+                sh.status = t;
+            }
             __syncthreads();
-            st = sh.status;
+            const int st = sh.status;
             if (st >= 0) {
                 if (tid == 0 && st == ZEUS_RUN_CONVERGED && use_stop) {
                     const unsigned long long c = atomicAdd(&ctrl->n_conv, 1ull) + 1ull;
@@ -671,11 +686,18 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
                 v6[4] += (double)(sj * gn[j]);
                 v6[5] += (double)(hyj * gn[j]);
             }
-            block_sum<6>(v6, sh.red);
-            const double sy = v6[0];
-            if (sy > 1e-12 * sqrt(v6[1]) * sqrt(v6[2])) {
+            // the curvature test, rho and b2 formed once, on thread 0
+            block_sum<6>(v6, sh.red, [](double* t) {
+                const double sy = t[0];
+                t[6] = sy > 1e-12 * sqrt(t[1]) * sqrt(t[2]) ? 1.0 : 0.0;
                 const double rho = 1.0 / sy;
-                const double b2 = rho * rho * v6[3] + rho;
+                t[7] = rho;
+                t[8] = rho * rho * t[3] + rho;
+            });
+            const double* cs = sh.red + 8 * 6 + 6;  // pass, rho, b2 (until the next sum)
+            if (cs[0] != 0.0) {
+                const double rho = cs[1];
+                const double b2 = cs[2];
                 const T sg = T(v6[4]), hg = T(v6[5]), rt = T(rho), bt = T(b2);
                 for (int j = tid; j < d; j += NT) {
                     const T sj = xn[j] - x[j];
@@ -772,7 +794,7 @@ static cudaError_t stream_go(const zeus_problem& p, const double* x0, double* x_
     if (p.lbfgs_m > 0) {
         auto kl = bfgs_stream_kernel<OBJ, GRAD, T, true>;
         const size_t sl = lbfgs_smem(p.dim, p.lbfgs_m, sizeof(T));
-        cudaError_t e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+        cudaError_t e = allow_smem(kl, sl);
         if (e != cudaSuccess) return e;
         kl<<<stream_blocks(p), kStreamThreads, sl, st>>>(p, x0, x_out, f_out, gnorm_out, status_out,
                                                          iters_out, ctrl, nullptr, wait_limit());
@@ -782,7 +804,7 @@ static cudaError_t stream_go(const zeus_problem& p, const double* x0, double* x_
     auto kern = stg ? bfgs_stream_kernel<OBJ, GRAD, T, false, true>
                     : bfgs_stream_kernel<OBJ, GRAD, T, false, false>;
     const size_t sm = stream_smem(p.dim, sizeof(T));
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = allow_smem(kern, sm);
     if (e != cudaSuccess) return e;
     kern<<<stream_blocks(p), kStreamThreads, sm, st>>>(p, x0, x_out, f_out, gnorm_out, status_out,
                                                        iters_out, ctrl, static_cast<T*>(hslots),
