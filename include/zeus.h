@@ -305,8 +305,10 @@ int zeus_math_eval(int32_t fn, int64_t n, const double *x, double *y0, double *y
  * equal those of zeus_solve(&probs[P]) bit for bit.
  *
  * Every problem of a batch shares `precision` and `grad_mode`; problems
- * whose H must stream from HBM (zeus_plan_info().stream) are not batched
- * (ZEUS_EUNSUPPORTED).  A problem's n_starts must be below 2^30.
+ * whose dense H must stream from HBM (zeus_plan_info().stream) are not
+ * batched (ZEUS_EUNSUPPORTED); L-BFGS problems (lbfgs_m > 0) are, one
+ * 256-thread block per start in classes of their own, beside dense ones.
+ * A problem's n_starts must be below 2^30.
  *
  * Outputs are the problems' arrays concatenated in problem order:
  *   x_out      device double [sum_P N_P * dim_P]   final BFGS points (required)
@@ -336,7 +338,8 @@ typedef struct {
     int32_t class_count[ZEUS_BATCH_MAX_CLASSES];  /* shared memory of each BFGS */
     int32_t class_smem[ZEUS_BATCH_MAX_CLASSES];   /* launch */
     int32_t class_kind[ZEUS_BATCH_MAX_CLASSES];   /* 0: lane tiles, 1: one block per start,
-                                                     2: one warp per start */
+                                                     2: one warp per start, 3: L-BFGS, one
+                                                     256-thread block per start */
     int64_t total_starts;     /* sum_P N_P */
     int64_t total_coords;     /* sum_P N_P * dim_P */
     int64_t total_g;          /* sum_P dim_P */

@@ -16,7 +16,8 @@ problems of that key (at most `probe_problems` of them, truncated to
 once are compared at throughput rather than at the latency of a few
 starts), and keeps the fastest.  Choices persist in a
 JSON file keyed also by the device name, so a key is measured once per GPU
-model.
+model.  L-BFGS problems have one layout (a 256-thread block per start) and
+are not tuned.
 """
 from __future__ import annotations
 
@@ -184,11 +185,11 @@ class Autotuner:
         from . import _capi, _prob
         problems = [_prob(p) for p in problems]
         if tune:
-            self.tune([p for p in problems if p.threads_per_start == 0])
+            self.tune([p for p in problems if p.threads_per_start == 0 and p.lbfgs_m == 0])
         out = []
         for p in problems:
             q = _capi.zeus_problem.from_buffer_copy(bytes(p))
-            if q.threads_per_start == 0:
+            if q.threads_per_start == 0 and q.lbfgs_m == 0:  # L-BFGS has one layout
                 c = self.choice(q)
                 if c is not None:
                     q.threads_per_start = c

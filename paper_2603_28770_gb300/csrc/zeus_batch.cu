@@ -112,7 +112,7 @@ int build_host(const zeus_problem* probs, int n, BatchHost& B) {
         BfgsLaunch L;
         const int r = plan_bfgs(p, &L);
         if (r != ZEUS_OK) return r;
-        if (L.stream) return ZEUS_EUNSUPPORTED;  // H on chip (and no L-BFGS) in a batch
+        if (L.stream && !L.lbfgs) return ZEUS_EUNSUPPORTED;  // dense H on chip in a batch
         if (p.objective >= ZEUS_OBJ_USER) ++B.n_user;
         const int d = p.dim;
         const int G = lanes_for_dim(d);
@@ -131,7 +131,10 @@ int build_host(const zeus_problem* probs, int n, BatchHost& B) {
         B.pso_iters_max = std::max(B.pso_iters_max, (int)p.pso_iters);
         B.stride.push_back(L.stride);
         B.budget.push_back(L.budget);
-        if (L.narrow) {
+        if (L.lbfgs) {  // one 256-thread block per start, the pairs in shared memory
+            for (long long s = 0; s < p.n_starts; ++s)
+                work.push_back({make_int4(P, (int)s, 0, 3), L.stream_smem, d});
+        } else if (L.narrow) {
             const size_t row = (size_t)L.stride * ts;
             const int tile = (int)std::min<size_t>(kWideThreads, kSmemCap / row);
             for (long long s = 0; s < p.n_starts; s += tile) {
@@ -152,10 +155,10 @@ int build_host(const zeus_problem* probs, int n, BatchHost& B) {
         }
     }
     if (work.size() >= (size_t)1 << 31) return ZEUS_EINVAL;
-    // classes by kind (warp-per-start and block-per-start items, then lane
-    // tiles, which feed the hand-over queue) and occupancy (fewest blocks
-    // per SM first); within
-    // a class larger d first (long work starts early)
+    // classes by kind (L-BFGS, warp-per-start and block-per-start items,
+    // then lane tiles, which feed the hand-over queue) and occupancy (fewest
+    // blocks per SM first); within a class larger d first (long work starts
+    // early)
     std::stable_sort(work.begin(), work.end(), [](const Work& a, const Work& b) {
         if (a.item.w != b.item.w) return a.item.w > b.item.w;
         const int ca = per_sm(a.smem), cb = per_sm(b.smem);
@@ -361,7 +364,7 @@ bool plan_sane(const zeus_batch_plan& p) {
     for (int c = 0; c < p.n_classes; ++c) {
         if (p.class_first[c] != next || p.class_count[c] < 1) return false;
         if (p.class_smem[c] < 0 || p.class_smem[c] > (int)kSmemCap) return false;
-        if (p.class_kind[c] < 0 || p.class_kind[c] > 2) return false;
+        if (p.class_kind[c] < 0 || p.class_kind[c] > 3) return false;
         next += p.class_count[c];
     }
     if (next != p.items) return false;
@@ -453,12 +456,19 @@ int zeus_batch_solve(const zeus_batch_plan* plan, void* workspace, size_t worksp
         e = aux_for_device(&a);
         if (e == cudaSuccess) e = cudaEventRecord(a->fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(a->stream, a->fork, 0);
-        for (int c = 0; c < plan->n_classes && e == cudaSuccess; ++c)
-            e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, c,
-                                  plan->class_first[c], plan->class_count[c],
-                                  (size_t)plan->class_smem[c], plan->class_kind[c] == 2, x_out,
-                                  f_out, gnorm_out, status_out, iters_out,
-                                  plan->class_kind[c] == 0 ? a->stream : st);
+        for (int c = 0; c < plan->n_classes && e == cudaSuccess; ++c) {
+            const int kind = plan->class_kind[c];
+            if (kind == 3)
+                e = launch_batch_lbfgs(bd, plan->precision, plan->grad_mode, c,
+                                       plan->class_first[c], plan->class_count[c],
+                                       (size_t)plan->class_smem[c], x_out, f_out, gnorm_out,
+                                       status_out, iters_out, st);
+            else
+                e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, c,
+                                      plan->class_first[c], plan->class_count[c],
+                                      (size_t)plan->class_smem[c], kind == 2, x_out, f_out,
+                                      gnorm_out, status_out, iters_out, kind == 0 ? a->stream : st);
+        }
         if (e == cudaSuccess && plan->q_cap > 0)
             e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, -1, 0, 0,
                                   (size_t)plan->handover_smem, false, x_out, f_out, gnorm_out,

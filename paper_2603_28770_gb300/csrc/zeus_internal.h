@@ -139,7 +139,8 @@ struct BatchDev {
     const int* pblk;         // its number of PSO blocks
     const int* plane;        // PSO lanes per particle
     const int* pso_table;    // problem of each PSO block
-    const int4* items;       // BFGS work: (problem, first start, count or W, mode 0 lane/1 block)
+    const int4* items;       // BFGS work: (problem, first start, count or W, kind: 0 lane
+                             // tile, 1 block, 2 warp, 3 L-BFGS block per start)
     const int* stride;       // one-lane layout stride per problem
     const int* budget;       // hand-over budget per problem (0 = none)
     Ctrl* pctrl;             // [n] per-problem counters, stop flag, global best
@@ -187,6 +188,12 @@ cudaError_t launch_batch_bfgs(const BatchDev& bd, int precision, int grad_mode, 
                               int first, int count, size_t smem, bool warp_items, double* x_out,
                               double* f_out, double* gnorm_out, int32_t* status_out,
                               int32_t* iters_out, cudaStream_t st);
+// one persistent launch over the L-BFGS items [first, first + count) of
+// class `cls` (zeus_stream.cu: the body of the single-problem L-BFGS kernel)
+cudaError_t launch_batch_lbfgs(const BatchDev& bd, int precision, int grad_mode, int cls,
+                               int first, int count, size_t smem, double* x_out, double* f_out,
+                               double* gnorm_out, int32_t* status_out, int32_t* iters_out,
+                               cudaStream_t st);
 
 // the kernels of one (gradient mode, precision) pair, compiled in a
 // translation unit of their own (zeus_bfgs_kernels.cu, zeus_batch_kernels.cu)

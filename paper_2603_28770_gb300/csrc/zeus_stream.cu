@@ -484,20 +484,21 @@ struct StreamShared {
     double red[(kStreamWarps + 1) * 2 * kStreamTrials];
 };
 
-// LB = false: dense H streamed from its HBM slot (the pass above; STG:
-// rows staged by bulk copies, compiled apart so that the direct pass keeps
-// its own registers).
-// LB = true: L-BFGS (the paper's future work, Section VI) with the m most
-// recent pairs in shared memory and the two-loop recursion for p; no H.
-template <int OBJ, int GRAD, class T, bool LB, bool STG = false>
-__global__ void __launch_bounds__(kStreamThreads, 4)
-    bfgs_stream_kernel(const zeus_problem p, const double* x0, double* x_out,
-                       double* __restrict__ f_out, double* __restrict__ gnorm_out,
-                       int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
-                       Ctrl* __restrict__ ctrl, T* __restrict__ hslots, const unsigned spin_limit) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ StreamShared sh;
-    __shared__ __align__(8) uint64_t stage_bar[4];
+// One start on the block: x from row s of x0, the results to row s of the
+// outputs, the counters to *ctrl.  LB = false: dense H streamed from the
+// block's HBM slot Hs (the pass above; STG: rows staged by bulk copies,
+// compiled apart so that the direct pass keeps its own registers).  LB =
+// true: L-BFGS (the paper's future work, Section VI) with the m most recent
+// pairs in shared memory and the two-loop recursion for p; no H.  Returns
+// false if a staged chunk never arrived (the error word is set).
+template <int OBJ, int GRAD, class T, bool LB, bool STG>
+__device__ __forceinline__ bool stream_start(const zeus_problem& p, const long long s,
+                                             const double* x0, double* x_out, double* f_out,
+                                             double* gnorm_out, int32_t* status_out,
+                                             int32_t* iters_out, Ctrl* ctrl, T* Hs,
+                                             const unsigned spin_limit, StreamShared& sh,
+                                             unsigned char* smem_raw, uint64_t* stage_bar,
+                                             unsigned& chunk_ctr) {
     const int tid = threadIdx.x, NT = blockDim.x;
     const int d = p.dim;
     T* x = reinterpret_cast<T*>(smem_raw);
@@ -510,7 +511,6 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     T* Av = hy + d;
     T* Bv = Av + d;
     T* u = Bv + d;
-    T* Hs = LB ? nullptr : hslots + (size_t)blockIdx.x * d * d;
     // L-BFGS history: m pairs (ring, slot of the i-th oldest = (head + i) % m)
     const int lm = LB ? p.lbfgs_m : 0;
     T* Sm = u + d;
@@ -522,198 +522,114 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     // staged pass (dense H only): chunks of rows in shared memory
     const StagePlan sp = (LB || !STG) ? StagePlan{0, 0} : stage_plan(d, (int)sizeof(T));
     unsigned char* stage = smem_raw + stage_offset(d, sizeof(T));
-    unsigned chunk_ctr = 0;
-    if (sp.ns > 0) {
-        if (tid == 0) {
-            for (int i = 0; i < sp.ns; ++i) mbar_init(stage_bar + i, 1);
-            fence_async_shared();
-        }
-        __syncthreads();
-    }
 
     const bool use_target = !isnan(p.target_f);
     const bool use_stop = use_target || p.required_converged > 0;
     const double tol = p.grad_tol, cA = p.armijo_c, beta = p.backtrack;
     const int K = p.bfgs_max_iters, L = p.ls_max_iters;
 
+    for (int j = tid; j < d; j += NT) x[j] = T(x0[s * d + j]);
+    __syncthreads();
+    block_gradient<OBJ, GRAD>(x, g, d, sh.red);
+    double a0 = 0.0;
+    block_values<OBJ, T>(x, pv, &a0, 1, d, sh.vals, sh.red);  // p unused at a = 0
+    double f0 = sh.vals[0];
+    for (int j = tid; j < d; j += NT) pv[j] = -g[j];  // H_0 = I
+    bool ident = true, corr = false;
+    int npair = 0, head = 0;  // L-BFGS pairs stored, oldest slot
+    int k = 0, feval = 0, status = ZEUS_RUN_MAX_ITER;
+    bool stalled = false;  // FP32 form: the previous decrease was below FP32 resolution
+    unsigned long long n_read = 0, n_write = 0;  // H passes through HBM
+    double gnorm = 0.0;
+    __syncthreads();
     for (;;) {
+        // ---- tests at the top of iteration k, and g'p, in one reduction
+        double v3[3] = {0.0, 0.0, 0.0};
+        for (int j = tid; j < d; j += NT) {
+            v3[0] += (double)(g[j] * g[j]);
+            v3[1] += isfinite(g[j]) ? 0.0 : 1.0;
+            v3[2] += (double)(g[j] * pv[j]);
+        }
+        block_sum<3>(v3, sh.red);
+        if (tid == 0) {  // the tests on one thread; |g| is its output alone
+            gnorm = sqrt(v3[0]);
+            int t = -1;
+            if (k >= K) t = ZEUS_RUN_MAX_ITER;
+            else if (use_stop && *((volatile int*)&ctrl->stop)) t = ZEUS_RUN_STOPPED;
+            else if (!isfinite(f0) || v3[1] != 0.0) t = ZEUS_RUN_NONFINITE;
+            else if (gnorm < tol) t = ZEUS_RUN_CONVERGED;
+            else if (use_target && f0 <= p.target_f) t = ZEUS_RUN_CONVERGED;
+            else if (stalled) t = ZEUS_RUN_STALLED;
+            sh.status = t;
+        }
         __syncthreads();
-        if (tid == 0) sh.item = (int)atomicAdd(&ctrl->q_head, 1u);
-        __syncthreads();
-        const long long s = sh.item;
-        if (s >= p.n_starts) break;
-        for (int j = tid; j < d; j += NT) x[j] = T(x0[s * d + j]);
-        __syncthreads();
-        block_gradient<OBJ, GRAD>(x, g, d, sh.red);
-        double a0 = 0.0;
-        block_values<OBJ, T>(x, pv, &a0, 1, d, sh.vals, sh.red);  // p unused at a = 0
-        double f0 = sh.vals[0];
-        for (int j = tid; j < d; j += NT) pv[j] = -g[j];  // H_0 = I
-        bool ident = true, corr = false;
-        int npair = 0, head = 0;  // L-BFGS pairs stored, oldest slot
-        int k = 0, feval = 0, status = ZEUS_RUN_MAX_ITER;
-        bool stalled = false;  // FP32 form: the previous decrease was below FP32 resolution
-        unsigned long long n_read = 0, n_write = 0;  // H passes through HBM
-        double gnorm = 0.0;
-        __syncthreads();
-        for (;;) {
-            // ---- tests at the top of iteration k, and g'p, in one reduction
-            double v3[3] = {0.0, 0.0, 0.0};
+        const int st = sh.status;
+        if (st >= 0) {
+            if (tid == 0 && st == ZEUS_RUN_CONVERGED && use_stop) {
+                const unsigned long long c = atomicAdd(&ctrl->n_conv, 1ull) + 1ull;
+                if ((use_target && f0 <= p.target_f) ||
+                    (p.required_converged > 0 && c >= (unsigned long long)p.required_converged))
+                    atomicExch(&ctrl->stop, 1);
+            }
+            status = st;
+            break;
+        }
+        // ---- descent check
+        double ddir = v3[2];
+        if (!(ddir < 0.0)) {  // restart from H = I
+            ident = true;
+            corr = false;
+            npair = 0;
+            head = 0;
+            double v1[1] = {0.0};
             for (int j = tid; j < d; j += NT) {
-                v3[0] += (double)(g[j] * g[j]);
-                v3[1] += isfinite(g[j]) ? 0.0 : 1.0;
-                v3[2] += (double)(g[j] * pv[j]);
+                pv[j] = -g[j];
+                v1[0] += (double)(g[j] * -g[j]);
             }
-            block_sum<3>(v3, sh.red);
-            if (tid == 0) {  // the tests on one thread; |g| is its output alone
-                gnorm = sqrt(v3[0]);
-                int t = -1;
-                if (k >= K) t = ZEUS_RUN_MAX_ITER;
-                else if (use_stop && *((volatile int*)&ctrl->stop)) t = ZEUS_RUN_STOPPED;
-                else if (!isfinite(f0) || v3[1] != 0.0) t = ZEUS_RUN_NONFINITE;
-                else if (gnorm < tol) t = ZEUS_RUN_CONVERGED;
-                else if (use_target && f0 <= p.target_f) t = ZEUS_RUN_CONVERGED;
-                else if (stalled) t = ZEUS_RUN_STALLED;
-                sh.status = t;
-            }
-            __syncthreads();
-            const int st = sh.status;
-            if (st >= 0) {
-                if (tid == 0 && st == ZEUS_RUN_CONVERGED && use_stop) {
-                    const unsigned long long c = atomicAdd(&ctrl->n_conv, 1ull) + 1ull;
-                    if ((use_target && f0 <= p.target_f) ||
-                        (p.required_converged > 0 && c >= (unsigned long long)p.required_converged))
-                        atomicExch(&ctrl->stop, 1);
-                }
-                status = st;
-                break;
-            }
-            // ---- descent check
-            double ddir = v3[2];
-            if (!(ddir < 0.0)) {  // restart from H = I
-                ident = true;
-                corr = false;
-                npair = 0;
-                head = 0;
-                double v1[1] = {0.0};
-                for (int j = tid; j < d; j += NT) {
-                    pv[j] = -g[j];
-                    v1[0] += (double)(g[j] * -g[j]);
-                }
-                block_sum<1>(v1, sh.red);
-                ddir = v1[0];
-            }
-            // ---- backtracking Armijo line search, kStreamTrials trials at once
-            double alpha_acc = 0.0, fn = 0.0;
-            int acc = -1;
-            double a_m = 1.0;
-            for (int m0 = 0; m0 < L && acc < 0;) {
-                // the first trial alone (usually accepted), then several at once
-                const int nw = min(m0 == 0 ? 1 : kStreamTrials, L - m0);
-                double al[kStreamTrials];
-                double a = a_m;
+            block_sum<1>(v1, sh.red);
+            ddir = v1[0];
+        }
+        // ---- backtracking Armijo line search, kStreamTrials trials at once
+        double alpha_acc = 0.0, fn = 0.0;
+        int acc = -1;
+        double a_m = 1.0;
+        for (int m0 = 0; m0 < L && acc < 0;) {
+            // the first trial alone (usually accepted), then several at once
+            const int nw = min(m0 == 0 ? 1 : kStreamTrials, L - m0);
+            double al[kStreamTrials];
+            double a = a_m;
 #pragma unroll
-                for (int i = 0; i < kStreamTrials; ++i) {
-                    al[i] = a;
-                    a = beta * a;
-                }
-                block_values<OBJ, T>(x, pv, al, nw, d, sh.vals, sh.red);
-                for (int i = 0; i < nw; ++i) {
-                    if (sh.vals[i] <= f0 + cA * al[i] * ddir) {
-                        acc = m0 + i;
-                        alpha_acc = al[i];
-                        fn = sh.vals[i];
-                        break;
-                    }
-                }
-                feval += acc >= 0 ? acc - m0 + 1 : nw;
-                a_m = al[nw - 1] * beta;
-                m0 += nw;
-                __syncthreads();
+            for (int i = 0; i < kStreamTrials; ++i) {
+                al[i] = a;
+                a = beta * a;
             }
-            if (acc < 0) alpha_acc = a_m;  // the step after the last halving
-            const T at = T(alpha_acc);
-            for (int j = tid; j < d; j += NT) xn[j] = x[j] + at * pv[j];
+            block_values<OBJ, T>(x, pv, al, nw, d, sh.vals, sh.red);
+            for (int i = 0; i < nw; ++i) {
+                if (sh.vals[i] <= f0 + cA * al[i] * ddir) {
+                    acc = m0 + i;
+                    alpha_acc = al[i];
+                    fn = sh.vals[i];
+                    break;
+                }
+            }
+            feval += acc >= 0 ? acc - m0 + 1 : nw;
+            a_m = al[nw - 1] * beta;
+            m0 += nw;
             __syncthreads();
-            if (acc < 0) {
-                double z = 0.0;
-                block_values<OBJ, T>(xn, pv, &z, 1, d, sh.vals, sh.red);
-                fn = sh.vals[0];
-            }
-            block_gradient<OBJ, GRAD>(xn, gn, d, sh.red);
-            if (LB) {
-                lbfgs_step<T>(x, xn, g, gn, pv, u, Sm, Ym, rho_m, gam_m, al_m, lm, npair, head, d,
-                              sh.red);
-                for (int j = tid; j < d; j += NT) {
-                    x[j] = xn[j];
-                    g[j] = gn[j];
-                }
-                stalled = stalled_step<T>(f0, fn);
-                f0 = fn;
-                ++k;
-                __syncthreads();
-                continue;
-            }
-            // ---- the pass: H_k = H_{k-1} + C_{k-1}, u = H_k g_{k+1}
-            if (ident && !corr) {
-                for (int j = tid; j < d; j += NT) u[j] = gn[j];
-                __syncthreads();
-            } else {
-                bool staged = false;
-                if constexpr (STG) {
-                    if (sp.ns > 0 && !ident) {
-                        if (!h_pass_staged<T>(Hs, d, corr, sv, hy, Av, Bv, gn, u, stage, stage_bar,
-                                              sp, chunk_ctr, spin_limit, ctrl))
-                            return;  // a chunk never arrived: the error word is set
-                        staged = true;
-                    }
-                }
-                if (!staged) h_pass<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u);
-                n_read += ident ? 0 : 1;             // H_{k-1} read unless still I
-                n_write += (corr || ident) ? 1 : 0;  // H_k stored when it changed
-                ident = false;
-            }
-            // ---- curvature pair and the correction C_k: one reduction for
-            //      y's, |s|^2, |y|^2, y'Hy, s'g_new, Hy'g_new
-            double v6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-            for (int j = tid; j < d; j += NT) {
-                const T sj = xn[j] - x[j], yj = gn[j] - g[j];
-                const T hyj = u[j] + pv[j];  // H_k y_k = H_k g_{k+1} + p_k
-                v6[0] += (double)(yj * sj);
-                v6[1] += (double)(sj * sj);
-                v6[2] += (double)(yj * yj);
-                v6[3] += (double)(yj * hyj);
-                v6[4] += (double)(sj * gn[j]);
-                v6[5] += (double)(hyj * gn[j]);
-            }
-            // the curvature test, rho and b2 formed once, on thread 0
-            block_sum<6>(v6, sh.red, [](double* t) {
-                const double sy = t[0];
-                t[6] = sy > 1e-12 * sqrt(t[1]) * sqrt(t[2]) ? 1.0 : 0.0;
-                const double rho = 1.0 / sy;
-                t[7] = rho;
-                t[8] = rho * rho * t[3] + rho;
-            });
-            const double* cs = sh.red + 8 * 6 + 6;  // pass, rho, b2 (until the next sum)
-            if (cs[0] != 0.0) {
-                const double rho = cs[1];
-                const double b2 = cs[2];
-                const T sg = T(v6[4]), hg = T(v6[5]), rt = T(rho), bt = T(b2);
-                for (int j = tid; j < d; j += NT) {
-                    const T sj = xn[j] - x[j];
-                    const T hyj = u[j] + pv[j];
-                    sv[j] = sj;
-                    hy[j] = hyj;
-                    const T a = bt * sj - rt * hyj, b = -rt * sj;
-                    Av[j] = a;
-                    Bv[j] = b;
-                    pv[j] = -(u[j] + a * sg + b * hg);
-                }
-                corr = true;
-            } else {
-                for (int j = tid; j < d; j += NT) pv[j] = -u[j];
-                corr = false;
-            }
+        }
+        if (acc < 0) alpha_acc = a_m;  // the step after the last halving
+        const T at = T(alpha_acc);
+        for (int j = tid; j < d; j += NT) xn[j] = x[j] + at * pv[j];
+        __syncthreads();
+        if (acc < 0) {
+            double z = 0.0;
+            block_values<OBJ, T>(xn, pv, &z, 1, d, sh.vals, sh.red);
+            fn = sh.vals[0];
+        }
+        block_gradient<OBJ, GRAD>(xn, gn, d, sh.red);
+        if (LB) {
+            lbfgs_step<T>(x, xn, g, gn, pv, u, Sm, Ym, rho_m, gam_m, al_m, lm, npair, head, d,
+                          sh.red);
             for (int j = tid; j < d; j += NT) {
                 x[j] = xn[j];
                 g[j] = gn[j];
@@ -722,48 +638,242 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
             f0 = fn;
             ++k;
             __syncthreads();
+            continue;
         }
-        // final value in FP64 at the final point
-        double vf[2] = {0.0, 0.0};
-        for (int j = tid; j < d; j += NT) {
-            double t0, t1;
-            const double xj = (double)x[j];
-            if (OBJ == ZEUS_OBJ_ROSENBROCK) {
-                t1 = 0.0;
-                t0 = 0.0;
-                if (j + 1 < d) {
-                    const double xk = (double)x[j + 1];
-                    const double a = 1.0 - xj, b = xk - xj * xj;
-                    t0 = a * a + 100.0 * (b * b);
+        // ---- the pass: H_k = H_{k-1} + C_{k-1}, u = H_k g_{k+1}
+        if (ident && !corr) {
+            for (int j = tid; j < d; j += NT) u[j] = gn[j];
+            __syncthreads();
+        } else {
+            bool staged = false;
+            if constexpr (STG) {
+                if (sp.ns > 0 && !ident) {
+                    if (!h_pass_staged<T>(Hs, d, corr, sv, hy, Av, Bv, gn, u, stage, stage_bar,
+                                          sp, chunk_ctr, spin_limit, ctrl))
+                        return false;  // a chunk never arrived: the error word is set
+                    staged = true;
                 }
-            } else if (OBJ == ZEUS_OBJ_RASTRIGIN) {
-                t0 = (xj * xj - 10.0 * c_2pi(xj)) + 10.0;
-                t1 = 0.0;
-            } else if (OBJ == ZEUS_OBJ_ACKLEY) {
-                t0 = xj * xj;
-                t1 = c_2pi(xj);
-            } else {
-                t0 = (0.5 * (double)(j + 1)) * (xj * xj);
-                t1 = 0.0;
             }
-            vf[0] += t0;
-            vf[1] += t1;
+            if (!staged) h_pass<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u);
+            n_read += ident ? 0 : 1;             // H_{k-1} read unless still I
+            n_write += (corr || ident) ? 1 : 0;  // H_k stored when it changed
+            ident = false;
         }
-        block_sum<2>(vf, sh.red);
-        const double ffin = finish_parts<OBJ, double>(vf[0], vf[1], d);
-        for (int j = tid; j < d; j += NT) x_out[s * d + j] = (double)x[j];
-        if (tid == 0) {
-            if (f_out) f_out[s] = ffin;
-            if (gnorm_out) gnorm_out[s] = gnorm;
-            if (status_out) status_out[s] = status;
-            if (iters_out) iters_out[s] = k;
-            atomicAdd(&ctrl->total_iters, (unsigned long long)k);
-            atomicAdd(&ctrl->total_feval, (unsigned long long)feval);
-            atomicAdd(&ctrl->h_reads, n_read);
-            atomicAdd(&ctrl->h_writes, n_write);
-            if (!use_stop && status == ZEUS_RUN_CONVERGED) atomicAdd(&ctrl->n_conv, 1ull);
+        // ---- curvature pair and the correction C_k: one reduction for
+        //      y's, |s|^2, |y|^2, y'Hy, s'g_new, Hy'g_new
+        double v6[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int j = tid; j < d; j += NT) {
+            const T sj = xn[j] - x[j], yj = gn[j] - g[j];
+            const T hyj = u[j] + pv[j];  // H_k y_k = H_k g_{k+1} + p_k
+            v6[0] += (double)(yj * sj);
+            v6[1] += (double)(sj * sj);
+            v6[2] += (double)(yj * yj);
+            v6[3] += (double)(yj * hyj);
+            v6[4] += (double)(sj * gn[j]);
+            v6[5] += (double)(hyj * gn[j]);
         }
+        // the curvature test, rho and b2 formed once, on thread 0
+        block_sum<6>(v6, sh.red, [](double* t) {
+            const double sy = t[0];
+            t[6] = sy > 1e-12 * sqrt(t[1]) * sqrt(t[2]) ? 1.0 : 0.0;
+            const double rho = 1.0 / sy;
+            t[7] = rho;
+            t[8] = rho * rho * t[3] + rho;
+        });
+        const double* cs = sh.red + 8 * 6 + 6;  // pass, rho, b2 (until the next sum)
+        if (cs[0] != 0.0) {
+            const double rho = cs[1];
+            const double b2 = cs[2];
+            const T sg = T(v6[4]), hg = T(v6[5]), rt = T(rho), bt = T(b2);
+            for (int j = tid; j < d; j += NT) {
+                const T sj = xn[j] - x[j];
+                const T hyj = u[j] + pv[j];
+                sv[j] = sj;
+                hy[j] = hyj;
+                const T a = bt * sj - rt * hyj, b = -rt * sj;
+                Av[j] = a;
+                Bv[j] = b;
+                pv[j] = -(u[j] + a * sg + b * hg);
+            }
+            corr = true;
+        } else {
+            for (int j = tid; j < d; j += NT) pv[j] = -u[j];
+            corr = false;
+        }
+        for (int j = tid; j < d; j += NT) {
+            x[j] = xn[j];
+            g[j] = gn[j];
+        }
+        stalled = stalled_step<T>(f0, fn);
+        f0 = fn;
+        ++k;
+        __syncthreads();
     }
+    // final value in FP64 at the final point
+    double vf[2] = {0.0, 0.0};
+    for (int j = tid; j < d; j += NT) {
+        double t0, t1;
+        const double xj = (double)x[j];
+        if (OBJ == ZEUS_OBJ_ROSENBROCK) {
+            t1 = 0.0;
+            t0 = 0.0;
+            if (j + 1 < d) {
+                const double xk = (double)x[j + 1];
+                const double a = 1.0 - xj, b = xk - xj * xj;
+                t0 = a * a + 100.0 * (b * b);
+            }
+        } else if (OBJ == ZEUS_OBJ_RASTRIGIN) {
+            t0 = (xj * xj - 10.0 * c_2pi(xj)) + 10.0;
+            t1 = 0.0;
+        } else if (OBJ == ZEUS_OBJ_ACKLEY) {
+            t0 = xj * xj;
+            t1 = c_2pi(xj);
+        } else {
+            t0 = (0.5 * (double)(j + 1)) * (xj * xj);
+            t1 = 0.0;
+        }
+        vf[0] += t0;
+        vf[1] += t1;
+    }
+    block_sum<2>(vf, sh.red);
+    const double ffin = finish_parts<OBJ, double>(vf[0], vf[1], d);
+    for (int j = tid; j < d; j += NT) x_out[s * d + j] = (double)x[j];
+    if (tid == 0) {
+        if (f_out) f_out[s] = ffin;
+        if (gnorm_out) gnorm_out[s] = gnorm;
+        if (status_out) status_out[s] = status;
+        if (iters_out) iters_out[s] = k;
+        atomicAdd(&ctrl->total_iters, (unsigned long long)k);
+        atomicAdd(&ctrl->total_feval, (unsigned long long)feval);
+        atomicAdd(&ctrl->h_reads, n_read);
+        atomicAdd(&ctrl->h_writes, n_write);
+        if (!use_stop && status == ZEUS_RUN_CONVERGED) atomicAdd(&ctrl->n_conv, 1ull);
+    }
+    return true;
+}
+
+// Persistent blocks over the starts of one problem (a start per block at a
+// time, taken from ctrl->q_head).
+template <int OBJ, int GRAD, class T, bool LB, bool STG = false>
+__global__ void __launch_bounds__(kStreamThreads, 4)
+    bfgs_stream_kernel(const zeus_problem p, const double* x0, double* x_out,
+                       double* __restrict__ f_out, double* __restrict__ gnorm_out,
+                       int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
+                       Ctrl* __restrict__ ctrl, T* __restrict__ hslots, const unsigned spin_limit) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ StreamShared sh;
+    __shared__ __align__(8) uint64_t stage_bar[4];
+    const int d = p.dim;
+    T* Hs = LB ? nullptr : hslots + (size_t)blockIdx.x * d * d;
+    const StagePlan sp = (LB || !STG) ? StagePlan{0, 0} : stage_plan(d, (int)sizeof(T));
+    if (sp.ns > 0) {
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < sp.ns; ++i) mbar_init(stage_bar + i, 1);
+            fence_async_shared();
+        }
+        __syncthreads();
+    }
+    unsigned chunk_ctr = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) sh.item = (int)atomicAdd(&ctrl->q_head, 1u);
+        __syncthreads();
+        const long long s = sh.item;
+        if (s >= p.n_starts) break;
+        if (!stream_start<OBJ, GRAD, T, LB, STG>(p, s, x0, x_out, f_out, gnorm_out, status_out,
+                                                 iters_out, ctrl, Hs, spin_limit, sh, smem_raw,
+                                                 stage_bar, chunk_ctr))
+            return;
+    }
+}
+
+// L-BFGS items (P, s, 0, 3) of a batch class: persistent blocks over the
+// class's items, each start run by the body of the single-problem L-BFGS
+// kernel, so that its results are those of zeus_solve bit for bit.
+template <int GRAD, class T>
+__global__ void __launch_bounds__(kStreamThreads, 4)
+    batch_lbfgs_kernel(const BatchDev bd, const int cls, const int first, const int count,
+                       double* x_out, double* __restrict__ f_out, double* __restrict__ gnorm_out,
+                       int32_t* __restrict__ status_out, int32_t* __restrict__ iters_out,
+                       const unsigned spin_limit) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ StreamShared sh;
+    unsigned chunk_ctr = 0;
+    unsigned* head = bd.heads + cls;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) sh.item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int item = sh.item;
+        if (item >= count) break;
+        const int4 w = bd.items[first + item];
+        const int P = w.x;
+        const zeus_problem p = bd.probs[P];
+        const long long xo = bd.xoff[P], so = bd.soff[P];
+        const double* x0 = p.start_from_pbest ? bd.px + xo : x_out + xo;
+        double* go = gnorm_out ? gnorm_out + so : nullptr;
+        int32_t* sto = status_out ? status_out + so : nullptr;
+        int32_t* ito = iters_out ? iters_out + so : nullptr;
+#define ZEUS_LBCASE(O)                                                                        \
+    stream_start<O, GRAD, T, true, false>(p, (long long)w.y, x0, x_out + xo, f_out + so, go, \
+                                          sto, ito, bd.pctrl + P, nullptr, spin_limit, sh,   \
+                                          smem_raw, nullptr, chunk_ctr)
+        switch (p.objective) {
+            case ZEUS_OBJ_ROSENBROCK:
+                ZEUS_LBCASE(ZEUS_OBJ_ROSENBROCK);
+                break;
+            case ZEUS_OBJ_RASTRIGIN:
+                ZEUS_LBCASE(ZEUS_OBJ_RASTRIGIN);
+                break;
+            case ZEUS_OBJ_ACKLEY:
+                ZEUS_LBCASE(ZEUS_OBJ_ACKLEY);
+                break;
+            default:
+                ZEUS_LBCASE(ZEUS_OBJ_QUADRATIC);
+                break;
+        }
+#undef ZEUS_LBCASE
+    }
+}
+
+template <int GRAD, class T>
+static cudaError_t batch_lbfgs_go(const BatchDev& bd, int cls, int first, int count, size_t smem,
+                                  double* x_out, double* f_out, double* gnorm_out,
+                                  int32_t* status_out, int32_t* iters_out, cudaStream_t st) {
+    auto k = batch_lbfgs_kernel<GRAD, T>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = allow_smem(k, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStreamThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long blocks = (long long)sms * per_sm;
+    if (blocks > count) blocks = count;  // no block without an item
+    if (blocks < 1) return cudaSuccess;
+    k<<<(int)blocks, kStreamThreads, smem, st>>>(bd, cls, first, count, x_out, f_out, gnorm_out,
+                                                 status_out, iters_out, wait_limit());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_lbfgs(const BatchDev& bd, int precision, int grad_mode, int cls,
+                               int first, int count, size_t smem, double* x_out, double* f_out,
+                               double* gnorm_out, int32_t* status_out, int32_t* iters_out,
+                               cudaStream_t st) {
+    const bool f32 = precision == ZEUS_FP32_GUARDED;
+    if (grad_mode == ZEUS_GRAD_ADJOINT)
+        return f32 ? batch_lbfgs_go<ZEUS_GRAD_ADJOINT, float>(bd, cls, first, count, smem, x_out,
+                                                               f_out, gnorm_out, status_out,
+                                                               iters_out, st)
+                   : batch_lbfgs_go<ZEUS_GRAD_ADJOINT, double>(bd, cls, first, count, smem, x_out,
+                                                                f_out, gnorm_out, status_out,
+                                                                iters_out, st);
+    return f32 ? batch_lbfgs_go<ZEUS_GRAD_FORWARD, float>(bd, cls, first, count, smem, x_out, f_out,
+                                                           gnorm_out, status_out, iters_out, st)
+               : batch_lbfgs_go<ZEUS_GRAD_FORWARD, double>(bd, cls, first, count, smem, x_out,
+                                                            f_out, gnorm_out, status_out, iters_out,
+                                                            st);
 }
 
 size_t stream_smem(int d, size_t tsize) {

@@ -179,6 +179,22 @@ def test_batch_plan(z):
     assert bytes(z.zeus_batch_plan_make(probs)) == bytes(pl)
 
 
+def test_batch_plan_with_lbfgs(z):
+    # L-BFGS problems (also at a d whose dense H would stream) join a batch
+    # as one 256-thread-block item per start, in classes of kind 3 that come
+    # first
+    probs = _mixed(z, 6)
+    lb = [z.Problem(objective="rosenbrock", dim=300, n_starts=5, lbfgs_m=4, seed=1),
+          z.Problem(objective="ackley", dim=20, n_starts=9, lbfgs_m=7, seed=2)]
+    pl = z.zeus_batch_plan_make(probs + lb)
+    kinds = [pl.class_kind[c] for c in range(pl.n_classes)]
+    assert kinds[0] == 3 and set(kinds) <= {0, 1, 2, 3} and kinds == sorted(kinds, reverse=True)
+    n3 = sum(pl.class_count[c] for c in range(pl.n_classes) if pl.class_kind[c] == 3)
+    assert n3 == sum(p.n_starts for p in lb)
+    assert all(pl.class_smem[c] > 0 for c in range(pl.n_classes) if pl.class_kind[c] == 3)
+    assert pl.total_starts == sum(p.n_starts for p in probs + lb)
+
+
 def test_batch_rejects(z):
     L = z.lib()
     EINVAL, EUNS, EWS = z._capi.ZEUS_EINVAL, z._capi.ZEUS_EUNSUPPORTED, z._capi.ZEUS_EWORKSPACE
@@ -199,9 +215,13 @@ def test_batch_rejects(z):
     # an invalid member problem
     with pytest.raises(z.ZeusError):
         z.zeus_batch_plan_make(probs[:3] + [probs[3].replace(dim=0)])
-    # H streamed from HBM is not batched
+    # dense H streamed from HBM is not batched, nor L-BFGS on Goldstein-Price
     with pytest.raises(z.ZeusError) as e:
         z.zeus_batch_plan_make(probs[:3] + [z.Problem(objective="rosenbrock", dim=256, n_starts=8)])
+    assert e.value.code == EUNS
+    with pytest.raises(z.ZeusError) as e:
+        z.zeus_batch_plan_make(probs[:3] + [z.Problem(objective="goldstein_price", dim=2,
+                                                      n_starts=8, lbfgs_m=3)])
     assert e.value.code == EUNS
     assert L.zeus_batch_plan_make(arr, 4, C.byref(pl)) == 0
     # prepare: missing or small workspace, and a plan of another batch, fail on the host
@@ -237,8 +257,9 @@ def test_lbfgs_plan(z):
             z.zeus_plan_info(p.replace(**bad))
         assert e.value.code == z._capi.ZEUS_EUNSUPPORTED
     assert z.zeus_plan_info(p.replace(threads_per_start=256))["lbfgs"] == 1
-    with pytest.raises(z.ZeusError):  # not batched
-        z.zeus_batch_plan_make([z.Problem(), p.replace(precision="fp64", dim=20, n_starts=8)])
+    # batched beside a dense problem: one item per start, a class of kind 3
+    pl = z.zeus_batch_plan_make([z.Problem(), p.replace(precision="fp64", dim=20, n_starts=8)])
+    assert pl.class_kind[0] == 3 and pl.class_count[0] == 8
 
 
 def test_user_objectives_of_the_default_plugin(z):

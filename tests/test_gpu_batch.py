@@ -90,6 +90,34 @@ def test_batch_equals_single_solves(z, precision, grad_mode):
         _check_against_single(z, b, probs, P)
 
 
+# L-BFGS problems (one 256-thread block per start, classes of their own)
+LBFGS_CASES = [
+    ("rosenbrock", 12, 70, 2, 100, {"lbfgs_m": 5}),
+    ("ackley", 40, 20, 1, 60, {"lbfgs_m": 3}),
+    ("rastrigin", 10, 33, 2, 80, {"lbfgs_m": 7}),
+    ("quadratic", 200, 5, 0, 40, {"lbfgs_m": 9}),
+    ("rosenbrock", 300, 3, 1, 30, {"lbfgs_m": 2, "start_from_pbest": 1}),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_guarded"])
+@pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
+def test_batch_with_lbfgs_problems(z, precision, grad_mode):
+    # L-BFGS problems beside dense ones in one batch: each problem equals
+    # its own zeus_solve bit for bit (the batch runs the single-problem
+    # L-BFGS body per start)
+    kw = dict(precision=precision, grad_mode=grad_mode)
+    probs = _problems(z, **kw)[:7]
+    probs += [z.Problem(**_fields(*c, seed=301 + i), **kw) for i, c in enumerate(LBFGS_CASES)]
+    b = z.Batch(probs)
+    kinds = list(b.plan.class_kind[: b.plan.n_classes])
+    assert kinds[0] == 3 and kinds == sorted(kinds, reverse=True)
+    b.solve()
+    torch.cuda.synchronize()
+    for P in range(len(probs)):
+        _check_against_single(z, b, probs, P)
+
+
 def test_batch_against_oracle(z, ora):
     # the oracle runs the whole method of each small problem of the batch
     probs = _problems(z)
