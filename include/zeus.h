@@ -29,7 +29,7 @@
  *    tables or an output buffer (one context per host thread for
  *    zeus_solve_host).  The library's process-wide state is small and
  *    guarded: the bounded-wait limit (an atomic, zeus_set_wait_limit), the
- *    second stream of the batched form on each device (created once, under
+ *    two streams of the batched form on each device (created once, under
  *    a lock, by zeus_batch_prepare) and the scratch array of
  *    zeus_solve_from_noalloc (its enqueue is serialised under a lock, but
  *    overlapping calls share the array: see there).  Kernel attributes are
@@ -299,10 +299,11 @@ int zeus_math_eval(int32_t fn, int64_t n, const double *x, double *y0, double *y
  * (persistent blocks; one launch per class of items that share a layout
  * and an occupancy), the hand-over launch, and one best-of-swarm reduction
  * per problem.  The lane-tile classes and the hand-over launch run on a
- * stream of the library's own, concurrently with the block-per-start
- * classes on `stream` (forked from and joined back to `stream`, so the
- * call stays stream-ordered and graph-capturable).  Problem P's results
- * equal those of zeus_solve(&probs[P]) bit for bit.
+ * stream of the library's own, concurrently with the other classes, which
+ * alternate between `stream` and a second stream of the library's own
+ * (both forked from and joined back to `stream`, so the call stays
+ * stream-ordered and graph-capturable).  Problem P's results equal those
+ * of zeus_solve(&probs[P]) bit for bit.
  *
  * Every problem of a batch shares `precision` and `grad_mode`; problems
  * whose dense H must stream from HBM (zeus_plan_info().stream) are not
@@ -353,8 +354,9 @@ int zeus_batch_plan_make(const zeus_problem *probs, int32_t n, zeus_batch_plan *
 /* Writes the batch's tables (problem parameters, offsets, work list) into
  * the workspace: one host-to-device copy on `stream`, then synchronizes
  * `stream`.  On its first call on a device it also creates the library's
- * second stream and two events for that device (kept until exit), so call
- * it before any stream capture of zeus_batch_solve.  probs and plan must be those given to zeus_batch_plan_make;
+ * two streams and three events for that device (kept until exit), so call
+ * it before any stream capture of zeus_batch_solve.  probs and plan must
+ * be those given to zeus_batch_plan_make;
  * workspace: device, plan->workspace_bytes, 256-byte aligned.  The tables
  * stay valid for any number of zeus_batch_solve calls on this workspace. */
 int zeus_batch_prepare(const zeus_problem *probs, int32_t n, const zeus_batch_plan *plan,

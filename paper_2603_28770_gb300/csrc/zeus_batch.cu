@@ -321,15 +321,17 @@ int check_ws(void* ws, size_t have, size_t need) {
     return ZEUS_OK;
 }
 
-// The library's second stream of each device (the lane-tile classes and the
-// hand-over launch run there, concurrently with the block-per-start
-// classes) and the two events that fork it from and join it to the
-// caller's stream.  Created once per device, kept until exit; the mutex
-// also keeps one call's fork and join from interleaving with another's.
+// The library's own streams of each device: `stream` carries the lane-tile
+// classes and the hand-over launch, `stream2` every other block-, warp- or
+// L-BFGS class (the rest run on the caller's stream), so that one class's
+// tail (its last long runs, on a few SMs) overlaps the next class's start;
+// and the events that fork them from and join them to the caller's stream.
+// Created once per device, kept until exit; the mutex also keeps one
+// call's fork and join from interleaving with another's.
 constexpr int kMaxDevices = 64;
 struct Aux {
-    cudaStream_t stream = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t stream = nullptr, stream2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
 };
 std::mutex g_aux_mu;
 Aux g_aux[kMaxDevices];
@@ -343,8 +345,10 @@ cudaError_t aux_for_device(Aux** out) {
     Aux& a = g_aux[dev];
     if (!a.stream) {
         e = cudaStreamCreateWithFlags(&a.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&a.stream2, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&a.join2, cudaEventDisableTiming);
         if (e != cudaSuccess) {
             a = Aux();
             return e;
@@ -447,27 +451,31 @@ int zeus_batch_solve(const zeus_batch_plan* plan, void* workspace, size_t worksp
         e = launch_batch_pso(bd, t, x_out, st);
     if (e != cudaSuccess) return ZEUS_ECUDA;
     {
-        // fork: lane-tile classes then the hand-over launch on the second
-        // stream, block-per-start classes on `stream`; join before the
-        // reduction.  The two sets touch disjoint problems (a problem's
-        // starts are all lane tiles or all blocks).
+        // fork: lane-tile classes then the hand-over launch on the library's
+        // stream, the other classes alternately on `stream` and the
+        // library's second stream; join before the reduction.  Classes
+        // touch disjoint starts, and the lane-tile set disjoint problems (a
+        // problem's starts are all lane tiles or all of one other kind).
         std::lock_guard<std::mutex> lock(g_aux_mu);
         Aux* a = nullptr;
         e = aux_for_device(&a);
         if (e == cudaSuccess) e = cudaEventRecord(a->fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(a->stream, a->fork, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(a->stream2, a->fork, 0);
+        int n_other = 0;
         for (int c = 0; c < plan->n_classes && e == cudaSuccess; ++c) {
             const int kind = plan->class_kind[c];
+            const cudaStream_t cs = kind == 0 ? a->stream : ((n_other++ & 1) ? a->stream2 : st);
             if (kind == 3)
                 e = launch_batch_lbfgs(bd, plan->precision, plan->grad_mode, c,
                                        plan->class_first[c], plan->class_count[c],
                                        (size_t)plan->class_smem[c], x_out, f_out, gnorm_out,
-                                       status_out, iters_out, st);
+                                       status_out, iters_out, cs);
             else
                 e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, c,
                                       plan->class_first[c], plan->class_count[c],
                                       (size_t)plan->class_smem[c], kind == 2, x_out, f_out,
-                                      gnorm_out, status_out, iters_out, kind == 0 ? a->stream : st);
+                                      gnorm_out, status_out, iters_out, cs);
         }
         if (e == cudaSuccess && plan->q_cap > 0)
             e = launch_batch_bfgs(bd, plan->precision, plan->grad_mode, plan->n_user > 0, -1, 0, 0,
@@ -476,9 +484,11 @@ int zeus_batch_solve(const zeus_batch_plan* plan, void* workspace, size_t worksp
         // join whatever was enqueued, also after a failed launch, so that a
         // capture never ends with the second stream still forked
         if (a) {
-            const cudaError_t e1 = cudaEventRecord(a->join, a->stream);
-            const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(st, a->join, 0) : e1;
-            if (e == cudaSuccess) e = e2;
+            cudaError_t e1 = cudaEventRecord(a->join, a->stream);
+            if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(st, a->join, 0);
+            if (e1 == cudaSuccess) e1 = cudaEventRecord(a->join2, a->stream2);
+            if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(st, a->join2, 0);
+            if (e == cudaSuccess) e = e1;
         }
     }
     if (e == cudaSuccess) e = launch_batch_argmin(bd, f_out, results, st);
