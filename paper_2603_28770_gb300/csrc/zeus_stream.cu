@@ -173,6 +173,38 @@ __device__ __forceinline__ void block_values(const T* x, const T* p, const doubl
     });
 }
 
+// The trial values of block_values and, on the same thread, the Armijo
+// test of each in order: *accepted = the first trial m with
+// f(x + a_m p) <= f0 + cA a_m ddir, or -1; visible to all threads on return.
+template <int OBJ, class T>
+__device__ __forceinline__ void block_trials(const T* x, const T* p, const double (&alpha)[kStreamTrials],
+                                             int n, int d, double f0, double cA, double ddir,
+                                             double* out, int* accepted, double* red) {
+    double s[2 * kStreamTrials];
+#pragma unroll
+    for (int m = 0; m < 2 * kStreamTrials; ++m) s[m] = 0.0;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+#pragma unroll
+        for (int m = 0; m < kStreamTrials; ++m) {
+            if (m < n) {
+                double t0, t1;
+                term_parts<OBJ>(x, p, T(alpha[m]), d, j, t0, t1);
+                s[2 * m] += t0;
+                s[2 * m + 1] += t1;
+            }
+        }
+    }
+    block_sum<2 * kStreamTrials>(s, red, [=](const double* t) {
+        int acc = -1;
+        for (int m = 0; m < n; ++m) {
+            const double fm = finish_parts<OBJ, T>(t[2 * m], t[2 * m + 1], d);
+            out[m] = fm;
+            if (acc < 0 && fm <= f0 + cA * alpha[m] * ddir) acc = m;
+        }
+        *accepted = acc;
+    });
+}
+
 template <int OBJ, int GRAD, class T>
 __device__ __forceinline__ void block_gradient(const T* x, T* g, int d, double* red) {
     AdjShared a;
@@ -601,16 +633,15 @@ __device__ __forceinline__ bool stream_start(const zeus_problem& p, const long l
 #pragma unroll
             for (int i = 0; i < kStreamTrials; ++i) {
                 al[i] = a;
-                a = beta * a;
+                if (i + 1 < nw) a = beta * a;
             }
-            block_values<OBJ, T>(x, pv, al, nw, d, sh.vals, sh.red);
-            for (int i = 0; i < nw; ++i) {
-                if (sh.vals[i] <= f0 + cA * al[i] * ddir) {
-                    acc = m0 + i;
-                    alpha_acc = al[i];
-                    fn = sh.vals[i];
-                    break;
-                }
+            // values and tests on thread 0 (the first accepted trial wins)
+            block_trials<OBJ, T>(x, pv, al, nw, d, f0, cA, ddir, sh.vals, &sh.accepted, sh.red);
+            const int ia = sh.accepted;
+            if (ia >= 0) {
+                acc = m0 + ia;
+                alpha_acc = al[ia];
+                fn = sh.vals[ia];
             }
             feval += acc >= 0 ? acc - m0 + 1 : nw;
             a_m = al[nw - 1] * beta;
@@ -634,7 +665,7 @@ __device__ __forceinline__ bool stream_start(const zeus_problem& p, const long l
                 x[j] = xn[j];
                 g[j] = gn[j];
             }
-            stalled = stalled_step<T>(f0, fn);
+            if (tid == 0) stalled = stalled_step<T>(f0, fn);  // read by the tests alone
             f0 = fn;
             ++k;
             __syncthreads();
@@ -704,7 +735,7 @@ __device__ __forceinline__ bool stream_start(const zeus_problem& p, const long l
             x[j] = xn[j];
             g[j] = gn[j];
         }
-        stalled = stalled_step<T>(f0, fn);
+        if (tid == 0) stalled = stalled_step<T>(f0, fn);  // read by the tests alone
         f0 = fn;
         ++k;
         __syncthreads();
