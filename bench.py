@@ -256,6 +256,18 @@ def _problem(z, fields):
     return z.Problem(**{k: v for k, v in fields.items() if k in z.Problem.__dataclass_fields__})
 
 
+# DRAM traffic of the streamed-H kernel per algorithmic byte of its H
+# passes, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
+# over the launch) of the current build on a small case of each workload:
+# Rosenbrock chain d = 256 FP32, forward, 8192 starts, K = 50: 209.35 GB for
+# 208.31 GB of passes; d = 1024 FP32, adjoint, 608 starts, K = 40: 195.42 GB
+# for 194.75 GB.  Traffic grows with the passes, so a full launch's traffic
+# is its algorithmic bytes times the ratio.  Keyed by (objective, d,
+# precision, gradient mode); other cases report null.
+STREAM_TRAFFIC_RATIO = {("rosenbrock", 256, "fp32_guarded", "forward"): 209.35 / 208.31,
+                        ("rosenbrock", 1024, "fp32_guarded", "adjoint"): 195.42 / 194.75}
+
+
 def single_roofline(z, pc, d, iters, fevals, summary, bfgs_s, fields, lbfgs_m, precision):
     """Roofline of the BFGS phase (the dominant launch sequence), timed by the
     events around zeus_solve_from on its stream."""
@@ -284,9 +296,11 @@ def single_roofline(z, pc, d, iters, fevals, summary, bfgs_s, fields, lbfgs_m, p
         nbytes = float(plan["h_bytes"]) * (reads + writes)
         achieved = nbytes / bfgs_s / 1e9
         peak, src = hbm_peak()
+        ratio = STREAM_TRAFFIC_RATIO.get((fields["objective"], d, precision, grad_mode))
         roof = {"kernel": "bfgs_stream_kernel (+ argmin)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src,
+                "frac": round(achieved / peak, 4),
+                "traffic": round(nbytes * ratio) if ratio else None, "peak_source": src,
                 "bytes_per_launch": nbytes, "launch_ms": round(bfgs_s * 1e3, 3),
                 "h_passes": {"reads": reads, "writes": writes, "bytes_per_pass": plan["h_bytes"]}}
         if precision == "fp64":
