@@ -164,14 +164,15 @@ __device__ __forceinline__ Dual<T> operator*(T s, Dual<T> x) { return dmk(s * x.
 //  e^x: Cody & Waite reduction x = k ln2 + r, k = rint(x / ln2),
 //    ln2 = L1 + L2 with a 32-bit head L1 (k L1 exact), Taylor series of e^r
 //    through r^13 in Horner form, exact scaling by 2^k.
-// Cost: sincos 2 rint + 3 add/mul + 16 FMA + 2 mul; e^x 1 rint + 4 +
-// 13 FMA.  FP32 uses CUDA's sincospif / expf.
+// Cost: sincos 2 rint + 2 add/mul + 17 FMA + 2 mul; e^x 1 rint + 3 +
+// 14 FMA (the products by q/4 and by k L1 are exact, so each joins its
+// subtraction in one FMA without changing a bit).  FP32 uses CUDA's sincospif / expf.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void sincos2pi(double x, double* sp, double* cp) {
     const double n = rint(x);
     const double r = x - n;
     const double qf = rint(4.0 * r);
-    const double s = r - 0.25 * qf;
+    const double s = fma(-0.25, qf, r);  // 0.25 qf is exact: r - qf/4 rounded once, as written
     const int q = ((int)qf) & 3;
     const double z = s * s;
     double ps = 0x1.aaec32af93359p-4, pc = 0x1.20c62c2f2d7f5p-2;
@@ -215,7 +216,8 @@ __device__ __forceinline__ double exp_cw(double x) {
     if (x > 709.78) return CUDART_INF;
     if (x < -745.2) return 0.0;
     const double k = rint(x * 0x1.71547652b82fep+0);
-    const double r = (x - k * 0x1.62e42fee00000p-1) - k * 0x1.a39ef35793c76p-33;
+    // k L1 is exact (a 32-bit head times |k| < 2^11), so x - k L1 is one rounding
+    const double r = fma(-k, 0x1.62e42fee00000p-1, x) - k * 0x1.a39ef35793c76p-33;
     double p = 0x1.6124613a86d09p-33;  // 1/13!
     p = fma(p, r, 0x1.1eed8eff8d898p-29);
     p = fma(p, r, 0x1.ae64567f544e4p-26);
@@ -241,7 +243,7 @@ __device__ __forceinline__ double cos2pi(double x) {
     const double n = rint(x);
     const double r = x - n;
     const double qf = rint(4.0 * r);
-    const double s = r - 0.25 * qf;
+    const double s = fma(-0.25, qf, r);  // 0.25 qf is exact: r - qf/4 rounded once, as written
     const int q = ((int)qf) & 3;
     const bool odd = (q & 1) != 0;
     const double z = s * s;
