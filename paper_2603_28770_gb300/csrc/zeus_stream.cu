@@ -149,60 +149,69 @@ __device__ __forceinline__ double finish_parts(double s0, double s1, int d) {
     return s0;
 }
 
-// Trial values f(x + a_m p), m = 0..n-1 (n <= kStreamTrials) into out,
-// formed by thread 0 and visible to all threads on return
+// f(x + a p) into *out, formed by thread 0 and visible to all threads on
+// return (one sum, two for Ackley)
 template <int OBJ, class T>
-__device__ __forceinline__ void block_values(const T* x, const T* p, const double* alpha, int n,
-                                             int d, double* out, double* red) {
-    double s[2 * kStreamTrials];
+__device__ __forceinline__ void block_value(const T* x, const T* p, const double a, int d,
+                                            double* out, double* red) {
+    constexpr int NP = OBJ == ZEUS_OBJ_ACKLEY ? 2 : 1;
+    double s[NP];
 #pragma unroll
-    for (int m = 0; m < 2 * kStreamTrials; ++m) s[m] = 0.0;
+    for (int m = 0; m < NP; ++m) s[m] = 0.0;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
-#pragma unroll
-        for (int m = 0; m < kStreamTrials; ++m) {
-            if (m < n) {
-                double t0, t1;
-                term_parts<OBJ>(x, p, T(alpha[m]), d, j, t0, t1);
-                s[2 * m] += t0;
-                s[2 * m + 1] += t1;
-            }
-        }
+        double t0, t1;
+        term_parts<OBJ>(x, p, T(a), d, j, t0, t1);
+        s[0] += t0;
+        if (NP == 2) s[NP - 1] += t1;
     }
-    block_sum<2 * kStreamTrials>(s, red, [=](const double* t) {
-        for (int m = 0; m < n; ++m) out[m] = finish_parts<OBJ, T>(t[2 * m], t[2 * m + 1], d);
+    block_sum<NP>(s, red, [=](const double* t) {
+        *out = finish_parts<OBJ, T>(t[0], NP == 2 ? t[NP - 1] : 0.0, d);
     });
 }
 
-// The trial values of block_values and, on the same thread, the Armijo
+// The trial values f(x + a_m p), m < n <= kStreamTrials, into out and, on
+// the thread that forms them (thread 0), the Armijo
 // test of each in order: *accepted = the first trial m with
 // f(x + a_m p) <= f0 + cA a_m ddir, or -1; visible to all threads on return.
 template <int OBJ, class T>
 __device__ __forceinline__ void block_trials(const T* x, const T* p, const double (&alpha)[kStreamTrials],
                                              int n, int d, double f0, double cA, double ddir,
                                              double* out, int* accepted, double* red) {
-    double s[2 * kStreamTrials];
+    // one sum per trial (two for Ackley); a chunk of one trial (the first
+    // of each search) reduces only its own: the block sum's butterfly is the
+    // same for any number of values, so the totals are the same bits
+    constexpr int NP = OBJ == ZEUS_OBJ_ACKLEY ? 2 : 1;
+    double s[NP * kStreamTrials];
 #pragma unroll
-    for (int m = 0; m < 2 * kStreamTrials; ++m) s[m] = 0.0;
+    for (int m = 0; m < NP * kStreamTrials; ++m) s[m] = 0.0;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
 #pragma unroll
         for (int m = 0; m < kStreamTrials; ++m) {
             if (m < n) {
                 double t0, t1;
                 term_parts<OBJ>(x, p, T(alpha[m]), d, j, t0, t1);
-                s[2 * m] += t0;
-                s[2 * m + 1] += t1;
+                s[NP * m] += t0;
+                if (NP == 2) s[NP * m + 1] += t1;
             }
         }
     }
-    block_sum<2 * kStreamTrials>(s, red, [=](const double* t) {
+    auto post = [=](const double* t) {
         int acc = -1;
         for (int m = 0; m < n; ++m) {
-            const double fm = finish_parts<OBJ, T>(t[2 * m], t[2 * m + 1], d);
+            const double fm = finish_parts<OBJ, T>(t[NP * m], NP == 2 ? t[NP * m + 1] : 0.0, d);
             out[m] = fm;
             if (acc < 0 && fm <= f0 + cA * alpha[m] * ddir) acc = m;
         }
         *accepted = acc;
-    });
+    };
+    if (n == 1) {
+        double s1[NP];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) s1[m] = s[m];
+        block_sum<NP>(s1, red, post);
+    } else {
+        block_sum<NP * kStreamTrials>(s, red, post);
+    }
 }
 
 template <int OBJ, int GRAD, class T>
@@ -564,7 +573,7 @@ __device__ __forceinline__ bool stream_start(const zeus_problem& p, const long l
     __syncthreads();
     block_gradient<OBJ, GRAD>(x, g, d, sh.red);
     double a0 = 0.0;
-    block_values<OBJ, T>(x, pv, &a0, 1, d, sh.vals, sh.red);  // p unused at a = 0
+    block_value<OBJ, T>(x, pv, a0, d, sh.vals, sh.red);  // p unused at a = 0
     double f0 = sh.vals[0];
     for (int j = tid; j < d; j += NT) pv[j] = -g[j];  // H_0 = I
     bool ident = true, corr = false;
@@ -654,7 +663,7 @@ __device__ __forceinline__ bool stream_start(const zeus_problem& p, const long l
         __syncthreads();
         if (acc < 0) {
             double z = 0.0;
-            block_values<OBJ, T>(xn, pv, &z, 1, d, sh.vals, sh.red);
+            block_value<OBJ, T>(xn, pv, z, d, sh.vals, sh.red);
             fn = sh.vals[0];
         }
         block_gradient<OBJ, GRAD>(xn, gn, d, sh.red);
