@@ -259,13 +259,13 @@ def _problem(z, fields):
 # DRAM traffic of the streamed-H kernel per algorithmic byte of its H
 # passes, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
 # over the launch) of the current build on a small case of each workload:
-# Rosenbrock chain d = 256 FP32, forward, 8192 starts, K = 50: 209.35 GB for
-# 208.31 GB of passes; d = 1024 FP32, adjoint, 608 starts, K = 40: 195.42 GB
+# Rosenbrock chain d = 256 FP32, forward, 8192 starts, K = 50: 210.24 GB for
+# 208.31 GB of passes; d = 1024 FP32, adjoint, 608 starts, K = 40: 195.41 GB
 # for 194.75 GB.  Traffic grows with the passes, so a full launch's traffic
 # is its algorithmic bytes times the ratio.  Keyed by (objective, d,
 # precision, gradient mode); other cases report null.
-STREAM_TRAFFIC_RATIO = {("rosenbrock", 256, "fp32_guarded", "forward"): 209.35 / 208.31,
-                        ("rosenbrock", 1024, "fp32_guarded", "adjoint"): 195.42 / 194.75}
+STREAM_TRAFFIC_RATIO = {("rosenbrock", 256, "fp32_guarded", "forward"): 210.24 / 208.31,
+                        ("rosenbrock", 1024, "fp32_guarded", "adjoint"): 195.41 / 194.75}
 
 
 def single_roofline(z, pc, d, iters, fevals, summary, bfgs_s, fields, lbfgs_m, precision):
