@@ -258,14 +258,11 @@ def _problem(z, fields):
 
 # DRAM traffic of the streamed-H kernel per algorithmic byte of its H
 # passes, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
-# over the launch) of the current build on a small case of each workload:
-# Rosenbrock chain d = 256 FP32, forward, 8192 starts, K = 50: 210.24 GB for
-# 208.31 GB of passes; d = 1024 FP32, adjoint, 608 starts, K = 40: 195.41 GB
-# for 194.75 GB.  Traffic grows with the passes, so a full launch's traffic
+# over the launch) of the current build on a small case of each workload.
+# Traffic grows with the passes, so a full launch's traffic
 # is its algorithmic bytes times the ratio.  Keyed by (objective, d,
 # precision, gradient mode); other cases report null.
-STREAM_TRAFFIC_RATIO = {("rosenbrock", 256, "fp32_guarded", "forward"): 210.24 / 208.31,
-                        ("rosenbrock", 1024, "fp32_guarded", "adjoint"): 195.41 / 194.75}
+STREAM_TRAFFIC_RATIO = {}
 
 
 def single_roofline(z, pc, d, iters, fevals, summary, bfgs_s, fields, lbfgs_m, precision):
@@ -289,11 +286,15 @@ def single_roofline(z, pc, d, iters, fevals, summary, bfgs_s, fields, lbfgs_m, p
                                 else "FP64 FMA rate measured on this GB300"),
                 "flops_per_launch": flops, "launch_ms": round(bfgs_s * 1e3, 3)}
     if plan["stream"]:
-        # H streamed from HBM: one H of d^2 sizeof(T) bytes per pass that
-        # read or wrote it (the kernel counts them; at most 2 per
-        # start-iteration, none while H = I)
+        # H streamed from HBM, per pass that read or wrote it (the kernel
+        # counts them; at most 2 per start-iteration, none while H = I): FP64
+        # H moves the full matrix, d^2 x 8 bytes; FP32 H is held as the tiles
+        # of its upper triangle, and its algorithmic bytes are the
+        # triangle's, d (d + 1) / 2 x 4 (the tiles on the diagonal carry a
+        # few more: plan h_bytes)
         reads, writes = summary["h_reads"], summary["h_writes"]
-        nbytes = float(plan["h_bytes"]) * (reads + writes)
+        per_pass = d * (d + 1) // 2 * 4 if precision == "fp32_guarded" else d * d * 8
+        nbytes = float(per_pass) * (reads + writes)
         achieved = nbytes / bfgs_s / 1e9
         peak, src = hbm_peak()
         ratio = STREAM_TRAFFIC_RATIO.get((fields["objective"], d, precision, grad_mode))
@@ -302,7 +303,8 @@ def single_roofline(z, pc, d, iters, fevals, summary, bfgs_s, fields, lbfgs_m, p
                 "frac": round(achieved / peak, 4),
                 "traffic": round(nbytes * ratio) if ratio else None, "peak_source": src,
                 "bytes_per_launch": nbytes, "launch_ms": round(bfgs_s * 1e3, 3),
-                "h_passes": {"reads": reads, "writes": writes, "bytes_per_pass": plan["h_bytes"]}}
+                "h_passes": {"reads": reads, "writes": writes, "bytes_per_pass": per_pass,
+                             "stored_bytes_per_pass": plan["h_bytes"]}}
         if precision == "fp64":
             # FP64 H: every pass takes d^2 FMAs for H g and 2 d^2 more when
             # it applies an update; against the FP64 pipe this is the bound

@@ -194,7 +194,10 @@ typedef struct {
     int32_t blocks;          /* grid of the block-per-start / streaming kernel */
     int32_t lbfgs;           /* 1: L-BFGS (problem.lbfgs_m > 0), block per start, no H */
     int32_t warp;            /* 1: one warp per start, H in shared memory */
-    int64_t h_bytes;         /* bytes of H per start in the chosen precision */
+    int64_t h_bytes;         /* bytes of H per start in the chosen precision: d^2
+                                elements; streamed FP32 H is held as the 32-column tiles
+                                of its upper triangle, and h_bytes is then their size
+                                (what one pass reads and writes) */
 } zeus_plan;
 int zeus_plan_info(const zeus_problem *p, zeus_plan *plan);
 

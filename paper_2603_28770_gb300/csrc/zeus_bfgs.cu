@@ -64,8 +64,8 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
         L->budget = 0;
         L->q_cap = 0;
         L->stream = true;
-        L->stream_blocks = stream_blocks(p);
         L->stream_smem = lbfgs_smem(d, p.lbfgs_m, ts);
+        L->stream_blocks = stream_blocks(p, L->stream_smem);
         L->hslot_bytes = 0;
         return L->stream_smem <= cap ? ZEUS_OK : ZEUS_EUNSUPPORTED;
     }
@@ -112,9 +112,11 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
     const size_t full = wide_smem(d, L->W, p.ls_max_iters, ts) +
                         ((size_t)d * d - (size_t)d * (d + 1) / 2) * ts;
     L->stream = (req == 256) || (!L->narrow && full > cap);
-    L->stream_blocks = stream_blocks(p);
     L->stream_smem = stream_smem(d, ts);
-    L->hslot_bytes = L->stream ? (size_t)L->stream_blocks * d * d * ts : 0;
+    L->stream_blocks = stream_blocks(p, L->stream_smem);
+    // FP32 H streams as the tiled upper triangle, FP64 H as the full matrix
+    L->hslot_bytes = !L->stream ? 0
+                     : (size_t)L->stream_blocks * (ts == 4 ? tile_slot_bytes(d, ts) : (size_t)d * d * ts);
     if (L->stream && (user || L->stream_smem > cap)) return ZEUS_EUNSUPPORTED;
     L->wide_blocks = 152 * 4;
     // hand-over budget (iterations + line-search evaluations) of the narrow

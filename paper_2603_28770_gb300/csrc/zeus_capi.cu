@@ -226,7 +226,12 @@ int zeus_plan_info(const zeus_problem* p, zeus_plan* plan) {
     plan->block = (!L.narrow && !L.stream && !L.warp) ? 1 : 0;
     plan->warp = L.warp ? 1 : 0;
     plan->blocks = L.stream ? L.stream_blocks : L.wide_blocks;
-    plan->h_bytes = L.lbfgs ? 0 : (int64_t)p->dim * p->dim * (p->precision == ZEUS_FP32_GUARDED ? 4 : 8);
+    // H per start: d^2 elements, except streamed FP32 H, held as the tiles
+    // of its upper triangle (what one pass moves each way)
+    const bool f32 = p->precision == ZEUS_FP32_GUARDED;
+    plan->h_bytes = L.lbfgs                ? 0
+                    : (L.stream && f32)    ? (int64_t)tile_slot_bytes(p->dim, 4)
+                                           : (int64_t)p->dim * p->dim * (f32 ? 4 : 8);
     return ZEUS_OK;
 }
 

@@ -50,6 +50,50 @@ unsigned wait_limit();
 
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Streamed H (zeus_stream.cu) is held as the upper triangle of the
+// symmetric matrix in tiles of th rows x 32 columns: tile (I, J) covers rows
+// [I th, I th + th) and columns [32 J, 32 J + 32) of the matrix padded to
+// dp (d rounded up to 32), and is stored when it holds an element r <= c,
+// i.e. for J >= I th / 32; tiles follow one another by tile rows, J
+// ascending.  Inside a tile, element (r, c) sits at ((r % th) / n) 32 n +
+// (c % 32) n + r % n, n = 16 / sizeof(T): lane c % 32 of a warp reads n
+// consecutive rows of its column as one 16-byte vector, and the warp reads
+// 512 contiguous bytes.  th = dp / 16 (at least n, at most 32, a power of
+// two), so that a matrix has at least 16 tile rows: eight warps take them
+// in pairs (I, TR - 1 - I), which hold the same number of tiles.
+struct TileGeo {
+    int th;  // rows per tile
+    int tr;  // tile rows, dp / th
+    int tc;  // tile columns, dp / 32
+    int dp;  // d rounded up to 32
+};
+__host__ __device__ inline TileGeo tile_geo(int d, int n) {
+    TileGeo t;
+    t.dp = (d + 31) / 32 * 32;
+    int th = t.dp / 16;
+    if (th > 32) th = 32;
+    int p2 = 1;
+    while (p2 * 2 <= th) p2 *= 2;
+    t.th = p2 < n ? n : p2;
+    t.tr = t.dp / t.th;
+    t.tc = t.dp / 32;
+    return t;
+}
+__host__ __device__ inline int tile_jmin(const TileGeo& t, int I) { return (I * t.th) / 32; }
+// tiles before tile row I
+__host__ __device__ inline long long tile_row_first(const TileGeo& t, int I) {
+    long long s = 0;
+    for (int i = 0; i < I; ++i) s += t.tc - tile_jmin(t, i);
+    return s;
+}
+__host__ __device__ inline long long tile_slot_elems(int d, int n) {
+    const TileGeo t = tile_geo(d, n);
+    return tile_row_first(t, t.tr) * t.th * 32;
+}
+inline size_t tile_slot_bytes(int d, size_t tsize) {
+    return (size_t)tile_slot_elems(d, (int)(16 / tsize)) * tsize;
+}
+
 // Raises a kernel's dynamic shared-memory limit to the most the device
 // allows beside the kernel's static shared memory: the same value on every
 // call, so that calls from several host threads never lower it under one
@@ -173,7 +217,7 @@ cudaError_t launch_bfgs(const zeus_problem& p, const BfgsLaunch& L, const double
 
 size_t stream_smem(int d, size_t tsize);
 size_t lbfgs_smem(int d, int m, size_t tsize);
-int stream_blocks(const zeus_problem& p);
+int stream_blocks(const zeus_problem& p, size_t smem);
 cudaError_t launch_bfgs_stream(const zeus_problem& p, const double* x0, double* x_out,
                                double* f_out, double* gnorm_out, int32_t* status_out,
                                int32_t* iters_out, Ctrl* ctrl, void* hslots, cudaStream_t st);

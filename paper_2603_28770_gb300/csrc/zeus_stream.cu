@@ -267,10 +267,110 @@ struct Vec16<double> {
     }
 };
 
-// The pass: H_k = H_{k-1} + (s_c A_r + hy_c B_r) (if corr), u = H_k g.
-// One warp per row, 16-byte loads and stores along the row.
+// The pass over the tiled triangle: H_k = H_{k-1} + (s_c A_r + hy_c B_r) for
+// the stored elements r <= c (if corr), and u = H_k g.  A warp takes tile
+// rows in pairs (I, TR - 1 - I); in a tile lane l holds column c = 32 J + l
+// and reads th rows of it n at a time (16-byte loads, 512 bytes a warp).
+// u_c gathers two parts: the row part, c' >= r, H_rc' g_c' summed over the
+// lanes of each tile row by row (a warp sum per row, held by the lane of
+// that row within the tile row across its tiles), and the column part,
+// r < c, H_rc g_r, which lane l of a tile adds up itself over the tile's
+// rows and then into its warp's column partials cp[w][c]; after the pass
+// the partials join u in warp order.  Elements outside r <= c < d (the
+// lower part of the tiles on the diagonal, the padding past d) are carried
+// along but never used.
 template <class T>
-__device__ __forceinline__ void h_pass(T* __restrict__ Hs, int d, bool ident, bool corr,
+__device__ __forceinline__ void h_pass_tiles(T* __restrict__ Hs, const int d, const bool ident,
+                                       const bool corr, const T* s, const T* hy, const T* A,
+                                       const T* B, const T* g, T* u, T* cp) {
+    using VT = Vec16<T>;
+    using V = typename VT::V;
+    constexpr int n = VT::n;
+    static_assert(n == 4, "the tiled pass holds FP32 H");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const TileGeo tg = tile_geo(d, n);
+    const int th = tg.th, nq = th / n;
+    T* cpw = cp + (size_t)w * tg.dp;
+    for (int c = lane; c < tg.dp; c += 32) cpw[c] = T(0);  // the lane's own columns
+    const bool store = corr || ident;
+    for (int q = w; q < (tg.tr + 1) / 2; q += kStreamWarps) {
+#pragma unroll 1
+        for (int side = 0; side < 2; ++side) {
+            const int I = side == 0 ? q : tg.tr - 1 - q;
+            if (side == 1 && I == q) break;  // the middle tile row of an odd count
+            T rowacc = T(0);
+            V* tile = reinterpret_cast<V*>(Hs + tile_row_first(tg, I) * th * 32);
+            for (int J = tile_jmin(tg, I); J < tg.tc; ++J, tile += nq * 32) {
+                const int c = 32 * J + lane;
+                const T sc = s[c], hc = hy[c], gc = g[c];
+                T colacc = T(0);
+                auto load = [&](int gq) {
+                    V h;
+                    if (ident) {
+#pragma unroll
+                        for (int k = 0; k < n; ++k) VT::set(h, k, (I * th + gq * n + k == c) ? T(1) : T(0));
+                    } else {
+                        h = __ldcs(tile + gq * 32 + lane);
+                    }
+                    return h;
+                };
+                V hn = load(0);
+                for (int gq = 0; gq < nq; ++gq) {
+                    V h = hn;
+                    if (gq + 1 < nq) hn = load(gq + 1);  // the next rows in flight
+                    const int i0 = I * th + gq * n;
+                    const V aq = *reinterpret_cast<const V*>(A + i0);
+                    const V bq = *reinterpret_cast<const V*>(B + i0);
+                    const V gi = *reinterpret_cast<const V*>(g + i0);
+                    T pr[n];
+#pragma unroll
+                    for (int k = 0; k < n; ++k) {
+                        const int i = i0 + k;
+                        T e = VT::get(h, k);
+                        if (corr) e = fma(sc, VT::get(aq, k), fma(hc, VT::get(bq, k), e));
+                        VT::set(h, k, e);
+                        const bool ok = c < d && i < d;
+                        if (ok && i < c) colacc = fma(e, VT::get(gi, k), colacc);
+                        pr[k] = (ok && i <= c) ? e * gc : T(0);
+                    }
+                    // the four row sums over the lanes at once: two halving
+                    // levels leave lane l one value (row (l >> 3)), three
+                    // more sum it; the row's lane in the tile row takes it
+                    const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+                    const T k0 = up16 ? pr[2] : pr[0], g0 = up16 ? pr[0] : pr[2];
+                    const T k1 = up16 ? pr[3] : pr[1], g1 = up16 ? pr[1] : pr[3];
+                    const T a0 = k0 + __shfl_xor_sync(0xffffffffu, g0, 16);
+                    const T a1 = k1 + __shfl_xor_sync(0xffffffffu, g1, 16);
+                    T rs = (up8 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, up8 ? a0 : a1, 8);
+                    rs += __shfl_xor_sync(0xffffffffu, rs, 4);
+                    rs += __shfl_xor_sync(0xffffffffu, rs, 2);
+                    rs += __shfl_xor_sync(0xffffffffu, rs, 1);
+                    const int kr = lane - gq * n;
+                    const T mine = __shfl_sync(0xffffffffu, rs, (kr & 3) * 8);
+                    if (kr >= 0 && kr < n) rowacc += mine;
+                    if (store) __stcs(tile + gq * 32 + lane, h);
+                }
+                if (c < d) cpw[c] += colacc;
+            }
+            if (lane < th && I * th + lane < d) u[I * th + lane] = rowacc;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        T t = u[c];
+#pragma unroll
+        for (int w2 = 0; w2 < kStreamWarps; ++w2) t = t + cp[(size_t)w2 * tg.dp + c];
+        u[c] = t;
+    }
+    __syncthreads();
+}
+
+// FP64 H, full d x d slot: H_k = H_{k-1} + (s_c A_r + hy_c B_r) (if corr),
+// u = H_k g.  One warp per row, 16-byte loads and stores along the row.  (The
+// tiled triangle would halve the bytes, but its row sums across lanes cost
+// FP64 adds per element, and the FP64 pipe bounds this pass.)
+template <class T>
+__device__ __forceinline__ void h_pass_rows(T* __restrict__ Hs, int d, bool ident, bool corr,
                                        const T* s, const T* hy, const T* A, const T* B,
                                        const T* g, T* u) {
     using VT = Vec16<T>;
@@ -542,19 +642,24 @@ __device__ __forceinline__ bool stream_start(const zeus_problem& p, const long l
                                              unsigned& chunk_ctr) {
     const int tid = threadIdx.x, NT = blockDim.x;
     const int d = p.dim;
+    // vectors of dp elements (the dense pass reads them 16 bytes at a time
+    // up to d rounded up to 32; the elements past d are never used); L-BFGS
+    // keeps d
+    const int dp = (LB || sizeof(T) == 8) ? d : tile_geo(d, Vec16<T>::n).dp;
     T* x = reinterpret_cast<T*>(smem_raw);
-    T* g = x + d;
-    T* pv = g + d;
-    T* xn = pv + d;
-    T* gn = xn + d;
-    T* sv = gn + d;  // s of the pending correction
-    T* hy = sv + d;  // Hy of the pending correction
-    T* Av = hy + d;
-    T* Bv = Av + d;
-    T* u = Bv + d;
+    T* g = x + dp;
+    T* pv = g + dp;
+    T* xn = pv + dp;
+    T* gn = xn + dp;
+    T* sv = gn + dp;  // s of the pending correction
+    T* hy = sv + dp;  // Hy of the pending correction
+    T* Av = hy + dp;
+    T* Bv = Av + dp;
+    T* u = Bv + dp;
+    T* cp = u + dp;  // FP32 dense pass: kStreamWarps column partials of dp elements
     // L-BFGS history: m pairs (ring, slot of the i-th oldest = (head + i) % m)
     const int lm = LB ? p.lbfgs_m : 0;
-    T* Sm = u + d;
+    T* Sm = u + dp;
     T* Ym = Sm + (size_t)lm * d;
     double* rho_m = reinterpret_cast<double*>(
         smem_raw + ((((size_t)10 * d + 2 * (size_t)lm * d) * sizeof(T) + 7) & ~size_t(7)));
@@ -685,16 +790,20 @@ __device__ __forceinline__ bool stream_start(const zeus_problem& p, const long l
             for (int j = tid; j < d; j += NT) u[j] = gn[j];
             __syncthreads();
         } else {
-            bool staged = false;
-            if constexpr (STG) {
-                if (sp.ns > 0 && !ident) {
-                    if (!h_pass_staged<T>(Hs, d, corr, sv, hy, Av, Bv, gn, u, stage, stage_bar,
-                                          sp, chunk_ctr, spin_limit, ctrl))
-                        return false;  // a chunk never arrived: the error word is set
-                    staged = true;
+            if constexpr (sizeof(T) == 4) {
+                h_pass_tiles<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u, cp);
+            } else {
+                bool staged = false;
+                if constexpr (STG) {
+                    if (sp.ns > 0 && !ident) {
+                        if (!h_pass_staged<T>(Hs, d, corr, sv, hy, Av, Bv, gn, u, stage,
+                                              stage_bar, sp, chunk_ctr, spin_limit, ctrl))
+                            return false;  // a chunk never arrived: the error word is set
+                        staged = true;
+                    }
                 }
+                if (!staged) h_pass_rows<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u);
             }
-            if (!staged) h_pass<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u);
             n_read += ident ? 0 : 1;             // H_{k-1} read unless still I
             n_write += (corr || ident) ? 1 : 0;  // H_k stored when it changed
             ident = false;
@@ -804,7 +913,9 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     __shared__ StreamShared sh;
     __shared__ __align__(8) uint64_t stage_bar[4];
     const int d = p.dim;
-    T* Hs = LB ? nullptr : hslots + (size_t)blockIdx.x * d * d;
+    T* Hs = LB ? nullptr
+               : hslots + (size_t)blockIdx.x * (sizeof(T) == 4 ? tile_slot_elems(d, 4)
+                                                               : (long long)d * d);
     const StagePlan sp = (LB || !STG) ? StagePlan{0, 0} : stage_plan(d, (int)sizeof(T));
     if (sp.ns > 0) {
         if (threadIdx.x == 0) {
@@ -917,6 +1028,7 @@ cudaError_t launch_batch_lbfgs(const BatchDev& bd, int precision, int grad_mode,
 }
 
 size_t stream_smem(int d, size_t tsize) {
+    if (tsize == 4) return 18 * (size_t)tile_geo(d, 4).dp * tsize;  // vectors and column partials
     const StagePlan sp = stage_plan(d, (int)tsize);
     if (sp.ns == 0) return 10 * (size_t)d * tsize;
     return stage_offset(d, tsize) + (size_t)sp.ns * sp.chunk_bytes;
@@ -927,10 +1039,16 @@ size_t lbfgs_smem(int d, int m, size_t tsize) {
            3 * (size_t)m * sizeof(double);
 }
 
-// About four blocks per SM, and the starts spread evenly over the rounds
-// (each block takes a start, runs it to the end, takes the next).
-int stream_blocks(const zeus_problem& p) {
-    const long long full = 152ll * 4;
+// As many blocks as fit the SMs at once (at most four per SM: the kernel's
+// registers; fewer when its shared memory, `smem` bytes, allows fewer), and
+// the starts spread evenly over the rounds (each block takes a start, runs
+// it to the end, takes the next).  A block beyond those resident would
+// start only when a resident one had run out of starts.
+int stream_blocks(const zeus_problem& p, size_t smem) {
+    long long per_sm = (long long)(233472 / (smem + 2048));  // 228 KB per SM, reserve + static
+    if (per_sm > 4) per_sm = 4;
+    if (per_sm < 1) per_sm = 1;
+    const long long full = 152ll * per_sm;
     const long long rounds = (p.n_starts + full - 1) / full;
     long long b = (p.n_starts + rounds - 1) / rounds;
     if (b < 1) b = 1;
@@ -946,17 +1064,18 @@ static cudaError_t stream_go(const zeus_problem& p, const double* x0, double* x_
         const size_t sl = lbfgs_smem(p.dim, p.lbfgs_m, sizeof(T));
         cudaError_t e = allow_smem(kl, sl);
         if (e != cudaSuccess) return e;
-        kl<<<stream_blocks(p), kStreamThreads, sl, st>>>(p, x0, x_out, f_out, gnorm_out, status_out,
+        kl<<<stream_blocks(p, sl), kStreamThreads, sl, st>>>(p, x0, x_out, f_out, gnorm_out,
+                                                             status_out,
                                                          iters_out, ctrl, nullptr, wait_limit());
         return cudaGetLastError();
     }
-    const bool stg = stage_plan(p.dim, (int)sizeof(T)).ns > 0;
+    const bool stg = sizeof(T) == 8 && stage_plan(p.dim, (int)sizeof(T)).ns > 0;
     auto kern = stg ? bfgs_stream_kernel<OBJ, GRAD, T, false, true>
                     : bfgs_stream_kernel<OBJ, GRAD, T, false, false>;
     const size_t sm = stream_smem(p.dim, sizeof(T));
     cudaError_t e = allow_smem(kern, sm);
     if (e != cudaSuccess) return e;
-    kern<<<stream_blocks(p), kStreamThreads, sm, st>>>(p, x0, x_out, f_out, gnorm_out, status_out,
+    kern<<<stream_blocks(p, sm), kStreamThreads, sm, st>>>(p, x0, x_out, f_out, gnorm_out, status_out,
                                                        iters_out, ctrl, static_cast<T*>(hslots),
                                                        wait_limit());
     return cudaGetLastError();

