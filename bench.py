@@ -258,11 +258,16 @@ def _problem(z, fields):
 
 # DRAM traffic of the streamed-H kernel per algorithmic byte of its H
 # passes, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
-# over the launch) of the current build on a small case of each workload.
-# Traffic grows with the passes, so a full launch's traffic
-# is its algorithmic bytes times the ratio.  Keyed by (objective, d,
-# precision, gradient mode); other cases report null.
-STREAM_TRAFFIC_RATIO = {}
+# over the launch) of the current build on a small case of each workload:
+# Rosenbrock chain d = 256 FP32, forward, 8192 starts, K = 50: 102.90 GB for
+# 104.56 GB of triangle passes (the 86 MB of tiles partly stay in L2);
+# d = 1024 FP32, adjoint, 608 starts, K = 40: 100.69 GB for 97.47 GB (the
+# tiles on the diagonal carry their lower elements too).  Traffic grows
+# with the passes, so a full launch's traffic is its algorithmic bytes
+# times the ratio.  Keyed by (objective, d, precision, gradient mode);
+# other cases report null.
+STREAM_TRAFFIC_RATIO = {("rosenbrock", 256, "fp32_guarded", "forward"): 102.90 / 104.56,
+                        ("rosenbrock", 1024, "fp32_guarded", "adjoint"): 100.69 / 97.47}
 
 
 def single_roofline(z, pc, d, iters, fevals, summary, bfgs_s, fields, lbfgs_m, precision):
