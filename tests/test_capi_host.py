@@ -145,6 +145,37 @@ def test_plan_choice(z):
                                            precision="fp32_guarded")) >= 300 * tiles * 16 * 32 * 4
 
 
+def _tiles_fp32(d):
+    # the tiled triangle of streamed FP32 H: d padded to 32, tiles of th
+    # rows x 32 columns, th = dp / 16 rounded down to a power of two within
+    # [4, 32], tile (I, J) stored when J >= I th / 32
+    dp = (d + 31) // 32 * 32
+    th = min(32, dp // 16)
+    p2 = 1
+    while p2 * 2 <= th:
+        p2 *= 2
+    th = max(p2, 4)
+    tiles = sum(dp // 32 - (I * th) // 32 for I in range(dp // th))
+    return tiles * th * 32, dp
+
+
+@pytest.mark.parametrize("d", [2, 10, 33, 64, 100, 200, 256, 300, 1024])
+def test_streamed_fp32_slot_is_the_tiled_triangle(z, d):
+    p = z.Problem(objective="rosenbrock", dim=d, n_starts=16, precision="fp32_guarded",
+                  threads_per_start=256)
+    info = z.zeus_plan_info(p)
+    elems, dp = _tiles_fp32(d)
+    assert info["stream"] == 1 and info["h_bytes"] == elems * 4
+    # every element r <= c < d is in some stored tile, and the slot holds at
+    # most the padded matrix
+    assert d * (d + 1) // 2 <= elems <= dp * dp
+    # the workspace holds one slot per block
+    assert z.zeus_workspace_size(p) >= info["blocks"] * elems * 4
+    # FP64 H streams whole
+    info64 = z.zeus_plan_info(p.replace(precision="fp64"))
+    assert info64["h_bytes"] == d * d * 8
+
+
 # ---------------------------------------------------------------- batched form
 
 def _mixed(z, n=12, **kw):
