@@ -409,6 +409,27 @@ def test_stream_counts_its_h_passes(z):
     assert s2["h_reads"] == 0 and s2["h_writes"] == 0
 
 
+@pytest.mark.parametrize("obj,d", [("quadratic", 33), ("quadratic", 100), ("rosenbrock", 100),
+                                   ("rosenbrock", 200), ("quadratic", 300), ("ackley", 70)])
+def test_stream_fp32_tiles_first_iterations(z, ora, obj, d):
+    # FP32 H streamed as the tiled triangle at d that leave ragged tiles
+    # (padding past d, 4, 8 and 16 rows a tile): the first 8 iterates'
+    # values agree with the FP64 oracle's to FP32 accuracy start by start
+    n = 16
+    lo, hi = {"quadratic": (-1.0, 1.0), "rosenbrock": (-2.0, 2.0), "ackley": (-0.5, 0.5)}[obj]
+    x0 = workloads.start_points(n, d, lo, hi, seed=5 * d + 3)
+    fields = dict(objective=obj, dim=d, lower=lo, upper=hi, n_starts=n, bfgs_max_iters=8,
+                  grad_tol=1e-30, threads_per_start=256)
+    pz = zeus_problem(z, fields, precision="fp32_guarded")
+    assert z.zeus_plan_info(pz)["stream"] == 1
+    g = to_np(z.solve_from(pz, torch.from_numpy(x0).cuda()))
+    o = ora.bfgs_many(oracle_problem(ora, fields), x0)
+    err = np.abs(g["f"] - o["f"]) / np.maximum(1.0, np.abs(o["f"]))
+    assert (g["iters"] == 8).all() and np.isfinite(g["f"]).all()
+    assert (err <= 1e-4).mean() >= 0.9, np.sort(err)[-4:]
+    assert g["summary"]["h_writes"] > 0
+
+
 @pytest.mark.parametrize("obj,d,n,lo,hi,fmin", [("rosenbrock", 64, 32, -2.0, 2.0, 0.0),
                                                 ("rastrigin", 12, 256, -5.12, 5.12, 0.0),
                                                 ("rosenbrock", 256, 8, -2.0, 2.0, 0.0)])
