@@ -298,7 +298,9 @@ def single_roofline(z, pc, d, iters, fevals, summary, bfgs_s, fields, lbfgs_m, p
         # triangle's, d (d + 1) / 2 x 4 (the tiles on the diagonal carry a
         # few more: plan h_bytes)
         reads, writes = summary["h_reads"], summary["h_writes"]
-        per_pass = d * (d + 1) // 2 * 4 if precision == "fp32_guarded" else d * d * 8
+        b = 4 if precision == "fp32_guarded" else 8
+        tiled = b == 4 and plan["h_bytes"] < d * d * 4  # past d ~ 3200 FP32 H streams whole
+        per_pass = d * (d + 1) // 2 * 4 if tiled else d * d * b
         nbytes = float(per_pass) * (reads + writes)
         achieved = nbytes / bfgs_s / 1e9
         peak, src = hbm_peak()

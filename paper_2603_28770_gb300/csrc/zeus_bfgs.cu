@@ -115,8 +115,7 @@ int plan_bfgs(const zeus_problem& p, BfgsLaunch* L) {
     L->stream_smem = stream_smem(d, ts);
     L->stream_blocks = stream_blocks(p, L->stream_smem);
     // FP32 H streams as the tiled upper triangle, FP64 H as the full matrix
-    L->hslot_bytes = !L->stream ? 0
-                     : (size_t)L->stream_blocks * (ts == 4 ? tile_slot_bytes(d, ts) : (size_t)d * d * ts);
+    L->hslot_bytes = !L->stream ? 0 : (size_t)L->stream_blocks * stream_slot_elems(d, ts) * ts;
     if (L->stream && (user || L->stream_smem > cap)) return ZEUS_EUNSUPPORTED;
     L->wide_blocks = 152 * 4;
     // hand-over budget (iterations + line-search evaluations) of the narrow

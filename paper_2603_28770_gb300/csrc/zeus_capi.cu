@@ -229,9 +229,9 @@ int zeus_plan_info(const zeus_problem* p, zeus_plan* plan) {
     // H per start: d^2 elements, except streamed FP32 H, held as the tiles
     // of its upper triangle (what one pass moves each way)
     const bool f32 = p->precision == ZEUS_FP32_GUARDED;
-    plan->h_bytes = L.lbfgs                ? 0
-                    : (L.stream && f32)    ? (int64_t)tile_slot_bytes(p->dim, 4)
-                                           : (int64_t)p->dim * p->dim * (f32 ? 4 : 8);
+    plan->h_bytes = L.lbfgs    ? 0
+                    : L.stream ? stream_slot_elems(p->dim, f32 ? 4 : 8) * (f32 ? 4 : 8)
+                               : (int64_t)p->dim * p->dim * (f32 ? 4 : 8);
     return ZEUS_OK;
 }
 

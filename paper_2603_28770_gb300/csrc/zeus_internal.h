@@ -93,6 +93,16 @@ __host__ __device__ inline long long tile_slot_elems(int d, int n) {
 inline size_t tile_slot_bytes(int d, size_t tsize) {
     return (size_t)tile_slot_elems(d, (int)(16 / tsize)) * tsize;
 }
+// FP32 H streams as the tiled triangle where the pass's shared memory (ten
+// vectors and eight warps' column partials of dp elements) fits a block;
+// FP64 H, and FP32 H beyond that d (about 3200), stream as the full matrix
+__host__ __device__ inline bool stream_tiled(int d, size_t tsize) {
+    return tsize == 4 && (size_t)18 * tile_geo(d, 4).dp * 4 <= (size_t)226 * 1024;
+}
+// elements of one block's H slot
+__host__ __device__ inline long long stream_slot_elems(int d, size_t tsize) {
+    return stream_tiled(d, tsize) ? tile_slot_elems(d, 4) : (long long)d * d;
+}
 
 // Raises a kernel's dynamic shared-memory limit to the most the device
 // allows beside the kernel's static shared memory: the same value on every

@@ -645,7 +645,8 @@ __device__ __forceinline__ bool stream_start(const zeus_problem& p, const long l
     // vectors of dp elements (the dense pass reads them 16 bytes at a time
     // up to d rounded up to 32; the elements past d are never used); L-BFGS
     // keeps d
-    const int dp = (LB || sizeof(T) == 8) ? d : tile_geo(d, Vec16<T>::n).dp;
+    const bool tiled = !LB && stream_tiled(d, sizeof(T));
+    const int dp = tiled ? (int)tile_geo(d, Vec16<T>::n).dp : d;
     T* x = reinterpret_cast<T*>(smem_raw);
     T* g = x + dp;
     T* pv = g + dp;
@@ -656,7 +657,7 @@ __device__ __forceinline__ bool stream_start(const zeus_problem& p, const long l
     T* Av = hy + dp;
     T* Bv = Av + dp;
     T* u = Bv + dp;
-    T* cp = u + dp;  // FP32 dense pass: kStreamWarps column partials of dp elements
+    T* cp = u + dp;  // tiled pass: kStreamWarps column partials of dp elements
     // L-BFGS history: m pairs (ring, slot of the i-th oldest = (head + i) % m)
     const int lm = LB ? p.lbfgs_m : 0;
     T* Sm = u + dp;
@@ -790,9 +791,14 @@ __device__ __forceinline__ bool stream_start(const zeus_problem& p, const long l
             for (int j = tid; j < d; j += NT) u[j] = gn[j];
             __syncthreads();
         } else {
+            bool done = false;
             if constexpr (sizeof(T) == 4) {
-                h_pass_tiles<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u, cp);
-            } else {
+                if (tiled) {
+                    h_pass_tiles<T>(Hs, d, ident, corr, sv, hy, Av, Bv, gn, u, cp);
+                    done = true;
+                }
+            }
+            if (!done) {
                 bool staged = false;
                 if constexpr (STG) {
                     if (sp.ns > 0 && !ident) {
@@ -913,9 +919,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     __shared__ StreamShared sh;
     __shared__ __align__(8) uint64_t stage_bar[4];
     const int d = p.dim;
-    T* Hs = LB ? nullptr
-               : hslots + (size_t)blockIdx.x * (sizeof(T) == 4 ? tile_slot_elems(d, 4)
-                                                               : (long long)d * d);
+    T* Hs = LB ? nullptr : hslots + (size_t)blockIdx.x * stream_slot_elems(d, sizeof(T));
     const StagePlan sp = (LB || !STG) ? StagePlan{0, 0} : stage_plan(d, (int)sizeof(T));
     if (sp.ns > 0) {
         if (threadIdx.x == 0) {
@@ -1028,7 +1032,7 @@ cudaError_t launch_batch_lbfgs(const BatchDev& bd, int precision, int grad_mode,
 }
 
 size_t stream_smem(int d, size_t tsize) {
-    if (tsize == 4) return 18 * (size_t)tile_geo(d, 4).dp * tsize;  // vectors and column partials
+    if (stream_tiled(d, tsize)) return 18 * (size_t)tile_geo(d, 4).dp * tsize;  // vectors, partials
     const StagePlan sp = stage_plan(d, (int)tsize);
     if (sp.ns == 0) return 10 * (size_t)d * tsize;
     return stage_offset(d, tsize) + (size_t)sp.ns * sp.chunk_bytes;
@@ -1069,7 +1073,7 @@ static cudaError_t stream_go(const zeus_problem& p, const double* x0, double* x_
                                                          iters_out, ctrl, nullptr, wait_limit());
         return cudaGetLastError();
     }
-    const bool stg = sizeof(T) == 8 && stage_plan(p.dim, (int)sizeof(T)).ns > 0;
+    const bool stg = !stream_tiled(p.dim, sizeof(T)) && stage_plan(p.dim, (int)sizeof(T)).ns > 0;
     auto kern = stg ? bfgs_stream_kernel<OBJ, GRAD, T, false, true>
                     : bfgs_stream_kernel<OBJ, GRAD, T, false, false>;
     const size_t sm = stream_smem(p.dim, sizeof(T));

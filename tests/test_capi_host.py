@@ -176,6 +176,14 @@ def test_streamed_fp32_slot_is_the_tiled_triangle(z, d):
     assert info64["h_bytes"] == d * d * 8
 
 
+def test_streamed_fp32_whole_matrix_past_the_tiles(z):
+    # past d ~ 3200 the tiled pass's shared memory would not fit a block:
+    # FP32 H streams as the full matrix there (up to the largest d)
+    p = z.Problem(objective="rosenbrock", dim=4000, n_starts=4, precision="fp32_guarded")
+    info = z.zeus_plan_info(p)
+    assert info["stream"] == 1 and info["h_bytes"] == 4000 * 4000 * 4
+
+
 # ---------------------------------------------------------------- batched form
 
 def _mixed(z, n=12, **kw):
